@@ -1,0 +1,222 @@
+/*
+ * pdhcg.h — C ABI of the B300 (sm_103a) PDHCG-II solver library (libpdhcg.so).
+ *
+ * Problem (Sec. 2, Eq. QP):
+ *     minimize   1/2 x^T Q x + c^T x
+ *     subject to lc <= A x <= uc,   lv <= x <= uv
+ * with Q symmetric positive semidefinite (full symmetric CSR storage, or NULL
+ * for Q = 0), A an m x n CSR matrix, and +-INFINITY marking an absent bound
+ * (an equality row has lc == uc).
+ *
+ * Method: the PDHCG-II iteration — the PDHG step of Sec. 2.1 (Eq. pdhcg_update)
+ * with the primal subproblem solved by the diagonal closed form, conjugate
+ * gradients or projected gradient with Barzilai-Borwein steps (Sec. 2.2), the
+ * reflected Halpern scheme (Sec. 3.1), step sizes tau = eta/omega,
+ * sigma = eta*omega with eta = 0.998/||A|| and the PID primal weight (Sec. 3.2,
+ * Eq. pid), the adaptive inner tolerance (Sec. 3.3), the KKT stopping rule
+ * (Sec. 4.2) and the infeasibility tests (Sec. 5.1, 5.2).  Every floating-point
+ * step of the method runs in CUDA kernels on the device.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PDHCG_OK (0) on success, a negative PDHCG_E_* code on
+ *     failure (pdhcg_strerror() names it; pdhcg_last_error() gives a detail
+ *     message for the calling thread).  No C++ exception crosses the ABI.
+ *   - Host pointers unless the name ends in _dev (then device pointers on the
+ *     handle's device).  The library copies every input it keeps; the caller
+ *     keeps ownership of its buffers.  Output arrays are caller-allocated.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ *   - CSR: 0-based, rowptr has nrows+1 entries, rowptr[0] = 0, nondecreasing;
+ *     column indices in [0, ncols); duplicates are rejected; nnz < 2^31.
+ */
+#ifndef PDHCG_H
+#define PDHCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDHCG_API_VERSION 1
+
+/* ---- return codes ---- */
+#define PDHCG_OK 0
+#define PDHCG_PENDING 1          /* pdhcg_poll: request not finished yet          */
+#define PDHCG_E_INVALID (-1)     /* bad argument or malformed problem data        */
+#define PDHCG_E_OOM (-2)         /* device allocation failed / over HBM budget    */
+#define PDHCG_E_CUDA (-3)        /* a CUDA runtime call failed                    */
+#define PDHCG_E_BUSY (-4)        /* server queue full; retry later                */
+#define PDHCG_E_NOT_FOUND (-5)   /* unknown ticket                                */
+#define PDHCG_E_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up          */
+
+/* ---- solver outcome (pdhcg_result.status) ---- */
+#define PDHCG_UNSOLVED 0
+#define PDHCG_OPTIMAL 1            /* max(r_primal, r_dual, r_gap) <= eps_tol (Sec. 4.2) */
+#define PDHCG_PRIMAL_INFEASIBLE 2  /* Farkas ray found (Sec. 5.1); y_out holds it         */
+#define PDHCG_DUAL_INFEASIBLE 3    /* unbounded direction found (Sec. 5.2); x_out holds it */
+#define PDHCG_ITERATION_LIMIT 4
+#define PDHCG_TIME_LIMIT 5
+#define PDHCG_NUMERICAL_ERROR 6
+
+/* ---- arithmetic of the iteration ---- */
+#define PDHCG_FP64 0   /* matrix values, vectors and reductions in double                  */
+#define PDHCG_FP32 1   /* FP32 matrix values, vectors and SpMV accumulation; FP64 inner
+                          products, KKT norms, restart/PID decisions and certificates       */
+#define PDHCG_MIXED 2  /* FP32 matrix values, FP64 vectors and accumulation                 */
+
+/* ---- primal subproblem solver (Sec. 2.2) ---- */
+#define PDHCG_INNER_AUTO 0  /* diagonal Q: closed form; else finite bounds: BB; else CG */
+#define PDHCG_INNER_DIAG 1  /* closed form; only valid for diagonal Q                    */
+#define PDHCG_INNER_CG 2    /* conjugate gradients; only valid when no bound is finite   */
+#define PDHCG_INNER_BB 3    /* projected gradient with Barzilai-Borwein steps            */
+
+typedef struct {
+  int32_t nrows, ncols;
+  int64_t nnz;
+  const int64_t* rowptr; /* nrows + 1 */
+  const int32_t* col;    /* nnz       */
+  const double* val;     /* nnz       */
+} pdhcg_csr;
+
+/* Solver parameters.  Fill with pdhcg_default_params() first; struct_size is
+ * checked so that older callers keep working when fields are appended. */
+typedef struct {
+  uint32_t struct_size;
+  int32_t precision;          /* PDHCG_FP64 (default) / PDHCG_FP32 / PDHCG_MIXED            */
+  double eps_tol;             /* KKT tolerance, Sec. 4.2 (1e-6)                              */
+  double eps_inf;             /* infeasibility tolerance eps_inf, Sec. 5 (1e-8)              */
+  double time_limit_s;        /* wall-clock limit measured on the device timer (3600)        */
+  int64_t max_iter;           /* outer PDHG steps (1e6)                                      */
+  double theta;               /* Halpern reflection parameter, Sec. 3.1 (1.0)                */
+  double kp, ki, kd;          /* PID gains, Eq. pid (0.99, 0.01, 0.0)                        */
+  double gamma_inner;         /* gamma of the adaptive inner tolerance, Sec. 3.3 (5e-4)      */
+  double eps_inner_min;       /* eps_min, Sec. 3.3 (1e-9)                                    */
+  double eps_inner_first;     /* first inner tolerance = this * max(1, ||b||) (1e-2)         */
+  int32_t k_eval;             /* KKT / infeasibility / restart check period (64)             */
+  int32_t inner;              /* PDHCG_INNER_*                                               */
+  int32_t max_inner_iter;     /* cap on CG / BB steps per outer step (1000)                  */
+  int32_t ruiz_iters;         /* Ruiz equilibration passes, 0 = no scaling (10)              */
+  double restart_sufficient;  /* restart if FPR <= this * FPR(anchor) (0.2)                  */
+  double restart_necessary;   /* ... or FPR <= this * FPR(anchor) and FPR grew (0.8)         */
+  double restart_artificial;  /* ... or round length >= this * total steps (0.36)            */
+  int32_t power_max_iter;     /* power iteration for ||A||_2 (1000)                          */
+  int32_t lanes_override;     /* force lanes per CSR row (1..32, power of 2); 0 = tuned      */
+  double power_tol;           /* relative change stopping the power iteration (1e-8)         */
+  double eta_override;        /* > 0: use this eta instead of 0.998/||A||                    */
+  double omega0_override;     /* > 0: use this initial primal weight                         */
+  double omega_clamp;         /* omega kept within [omega0/c, omega0*c] (1e5)                */
+  int32_t group_blocks;       /* CTAs per instance in pdhcg_solve: 0 = auto                  */
+  int32_t device_timeout_ms;  /* bound on any device-side wait (8000)                        */
+} pdhcg_params;
+
+typedef struct {
+  int32_t status;             /* PDHCG_OPTIMAL, ... (see above)                              */
+  int32_t inner_method;       /* the PDHCG_INNER_* actually used                             */
+  int64_t iterations;         /* outer PDHG steps                                            */
+  int64_t inner_iterations;   /* CG / BB steps summed over all outer steps                   */
+  int64_t restarts;
+  double r_primal, r_dual, r_gap; /* Sec. 4.2 residuals at the returned point (unscaled data)*/
+  double primal_obj, dual_obj;
+  double eta, omega, norm_A;  /* step size, final primal weight, ||A||_2 estimate (scaled) */
+  double solve_seconds;       /* device-timer duration of the solve                          */
+  int32_t power_iters;
+  int32_t precision;
+} pdhcg_result;
+
+typedef struct pdhcg_problem pdhcg_t;
+typedef struct pdhcg_server pdhcg_server_t;
+
+/* Fill p with the defaults listed above.  Returns PDHCG_E_INVALID for NULL. */
+int pdhcg_default_params(pdhcg_params* p);
+
+/* Validate the problem, copy it to the device and run the setup of the method
+ * on the device: Ruiz equilibration of [Q A^T; A 0] (reading of the paper's
+ * "system scaling"), the power-iteration estimate of ||A||_2 for
+ * eta = 0.998/||A|| (Sec. 3.2), Gershgorin bound of Q for the BB step range,
+ * and the initial primal weight.  Q may be NULL (LP).  A must be given even
+ * when m = 0 (nrows = 0).  lc, uc: m entries; c, lv, uv: n entries.
+ * cuda_stream: a cudaStream_t (NULL = the default stream) used for all work on
+ * this handle.  On success *out owns device memory released by pdhcg_destroy.
+ * Errors: E_INVALID (shape, NaN, lc > uc, lv > uv, lc = +inf, non-symmetric Q,
+ * duplicate entries), E_OOM, E_CUDA. */
+int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
+                 const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
+                 void* cuda_stream, pdhcg_t** out);
+
+/* Solve from host buffers (blocking).  x0 (n) / y0 (m) are optional warm
+ * starts (NULL = x = proj_X(0), y = 0).  x_out (n) / y_out (m) may be NULL.
+ * Host<->device copies of the warm start and of the result are part of the call.
+ * For PDHCG_PRIMAL_INFEASIBLE y_out holds the ray (infinity norm 1); for
+ * PDHCG_DUAL_INFEASIBLE x_out holds the ray. */
+int pdhcg_solve(pdhcg_t* prob, const double* x0, const double* y0, pdhcg_result* res,
+                double* x_out, double* y_out);
+
+/* Same with device-resident buffers (double, on the handle's device); the
+ * result struct is still returned in host memory.  Blocking. */
+int pdhcg_solve_dev(pdhcg_t* prob, const double* x0_dev, const double* y0_dev, pdhcg_result* res,
+                    double* x_out_dev, double* y_out_dev);
+
+/* Solve count independent problems in one persistent launch: every CTA takes
+ * the next unsolved instance from a device work queue and solves it alone
+ * (instances whose size calls for it run on groups of CTAs).  All handles must
+ * share precision and stream.  x_out / y_out: arrays of count host pointers
+ * (each may be NULL), or NULL.  res: count results. */
+int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result* res, double* const* x_out,
+                      double* const* y_out);
+
+/* eta used by the iteration and the ||A||_2 estimate of the scaled A (Sec. 3.2). */
+int pdhcg_get_eta(const pdhcg_t* prob, double* eta, double* norm_A);
+
+/* Scaling vectors: x_original = D .* x_scaled, y_original = E .* y_scaled. */
+int pdhcg_get_scaling(const pdhcg_t* prob, double* D, double* E);
+
+/* Sizes of a handle: n, m, device bytes held. */
+int pdhcg_get_info(const pdhcg_t* prob, int32_t* n, int32_t* m, size_t* device_bytes);
+
+/* Profiling aid: device-timer seconds of the last pdhcg_solve / pdhcg_solve_dev
+ * on this handle, as seen by one thread of the first CTA, split into 8
+ * categories: [0] Phase I (A^T y, subproblem start), [1] inner-solver row phases
+ * (Q p), [2] inner-solver elementwise phases, [3] Phase II (A xbar, dual step,
+ * Halpern), [4] KKT / infeasibility checks, [5] group barriers and reductions,
+ * [6] restarts and output, [7] unused. */
+int pdhcg_get_phase_times(const pdhcg_t* prob, double* seconds8);
+
+void pdhcg_destroy(pdhcg_t* prob);
+
+/* ---- serving loop (continuous batching) ----
+ * A host scheduler thread admits submitted problems while their device
+ * footprint fits hbm_budget_bytes and a slot (max_slots) is free, keeps every
+ * live solve's iterates and restart state resident on the device, and packs
+ * all live solves into shared persistent launches that each advance every live
+ * solve by a bounded slice of iterations; finished solves free their slot and
+ * memory at the next slice boundary, where waiting requests are admitted. */
+typedef struct {
+  uint64_t submitted, admitted, completed, rejected;
+  uint64_t launches;
+  int32_t live, queued;
+  size_t hbm_in_use;
+} pdhcg_server_stats;
+
+int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_params* params,
+                        void* cuda_stream, pdhcg_server_t** out);
+/* Copy the problem into the server's queue (non-blocking).  Returns
+ * PDHCG_E_BUSY if the queue holds max_queue requests already, PDHCG_E_OOM if
+ * the problem alone can never fit the budget.  *ticket identifies it. */
+int pdhcg_submit(pdhcg_server_t* srv, const pdhcg_csr* Q, const pdhcg_csr* A, const double* c,
+                 const double* lc, const double* uc, const double* lv, const double* uv,
+                 uint64_t* ticket);
+/* PDHCG_PENDING while queued or running; PDHCG_OK once finished, filling res
+ * and (optionally) x_out / y_out; the ticket is then forgotten. */
+int pdhcg_poll(pdhcg_server_t* srv, uint64_t ticket, pdhcg_result* res, double* x_out,
+               double* y_out);
+int pdhcg_server_get_stats(pdhcg_server_t* srv, pdhcg_server_stats* stats);
+void pdhcg_server_destroy(pdhcg_server_t* srv);
+
+const char* pdhcg_strerror(int code);
+const char* pdhcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDHCG_H */

@@ -1,0 +1,858 @@
+// device_common.cuh — CTA-group machinery shared by the setup and solve kernels.
+//
+// A "group" is the set of CTAs that work on one instance: either one CTA
+// (batched small instances) or several co-resident CTAs of a cooperative
+// launch (one large instance).  The same phase code runs on both: rows of a
+// phase are split over the group's CTAs, and every phase ends in
+// group_reduce(), which is both the group barrier and a deterministic
+// reduction of up to kSlots FP64 values.  Every CTA sums the per-CTA partials
+// in the same fixed order, so every CTA holds bitwise identical totals and
+// takes identical scalar decisions without further communication.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "pdhcg_internal.h"
+
+namespace pdhcg {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- mbarrier + bulk-copy (TMA) helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Bulk copy global -> shared, completing `bytes` of transaction on `bar`.
+// src, dst 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase `parity` of `bar`; false after timeout_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns);
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Streaming loads of matrix data that is read-only for the whole kernel: keep it
+// out of L1 and mark it evict-first in L2 so the (re-read) vectors stay resident.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int ld_stream(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+               : "=r"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+               : "=f"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
+               : "=d"(v) : "l"(p), "l"(l2_evict_first_policy()));
+  return v;
+}
+
+// Read-only loads through L1 (small instances solved by one CTA re-read their
+// whole matrix every step; it stays in L1).
+template <bool kStream, class T>
+__device__ __forceinline__ T ld_mat(const T* p) {
+  if constexpr (kStream) return ld_stream(p);
+  else return __ldg(p);
+}
+
+template <class T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Sign cone Y_i of the dual (Sec. 2): {0} free row, R+ upper-only, R- lower-only, R boxed.
+__device__ __forceinline__ double proj_Y(double v, int8_t t) {
+  switch (t) {
+    case kFree: return 0.0;
+    case kUpOnly: return fmax(v, 0.0);
+    case kLowOnly: return fmin(v, 0.0);
+    default: return v;
+  }
+}
+// Sign cone R_j of the reduced cost (Sec. 2): {0} free, R- upper-only, R+ lower-only, R boxed.
+__device__ __forceinline__ double proj_R(double v, int8_t t) {
+  switch (t) {
+    case kFree: return 0.0;
+    case kUpOnly: return fmin(v, 0.0);
+    case kLowOnly: return fmax(v, 0.0);
+    default: return v;
+  }
+}
+// Recession cone of a box (Sec. 5.2): {0} boxed, R+ lower-only, R- upper-only, R free.
+__device__ __forceinline__ double proj_recc(double d, int8_t t) {
+  switch (t) {
+    case kBoxed: return 0.0;
+    case kLowOnly: return fmax(d, 0.0);
+    case kUpOnly: return fmin(d, 0.0);
+    default: return d;
+  }
+}
+// One term of p(z; l, u) = u^T z^+ - l^T z^- (Sec. 2); zero z contributes 0.
+__device__ __forceinline__ double support_term(double z, double lo, double hi) {
+  if (z > 0.0) return hi * z;
+  if (z < 0.0) return lo * z;
+  return 0.0;
+}
+
+template <int BS>
+struct Group {
+  static constexpr int kWarps = BS / 32;
+  int nblk;                     // CTAs in the group
+  int rank;                     // this CTA's rank
+  unsigned* bar32;              // hierarchical barrier block (multi-CTA only, kBarWords)
+  unsigned long long epoch;     // barriers passed
+  double* part;                 // 2 * kSlots * nblk partials (multi-CTA only)
+  double* sm_warp;              // shared [2][kWarps][kSlots]
+  double* sm_tot;               // shared [2][kSlots]
+  int* sm_flag;                 // shared
+  int* err;
+  uint64_t timeout_ns;
+  bool failed;
+
+  // Row range of this CTA in a space whose partition table is `part`
+  // (nblk+1 offsets), or the whole space for a single-CTA group.
+  __device__ __forceinline__ void range(const int32_t* part_tab, int nrows, int& lo,
+                                        int& hi) const {
+    if (nblk == 1 || part_tab == nullptr) {
+      lo = 0;
+      hi = nrows;
+    } else {
+      lo = part_tab[rank];
+      hi = part_tab[rank + 1];
+    }
+  }
+};
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
+  uint32_t done = 0;
+  uint64_t t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63u) == 63u) {
+      const uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > timeout_ns) return false;
+    }
+  }
+}
+
+// Bounded spin until *addr >= target.  Returns false after timeout_ns or when
+// another CTA reported an error.
+__device__ __forceinline__ bool spin_geq(const unsigned long long* addr, unsigned long long target,
+                                         uint64_t timeout_ns, const int* err) {
+  uint64_t t0 = 0;
+  unsigned it = 0;
+  while (ld_acquire_u64(addr) < target) {
+    if ((++it & 255u) == 0u) {
+      uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      if (t - t0 > timeout_ns) return false;
+      if (ld_relaxed_s32(err) != 0) return false;
+    }
+  }
+  return true;
+}
+
+// ---- hierarchical group barrier ----
+// Layout of a group's barrier block (zeroed before the launch), 128-byte lines:
+// line k < kBarSub: arrival counter of sub-group k (CTAs with rank % nsub == k);
+// line kBarSub: top-level counter; line kBarSub + 1: generation (epochs completed).
+constexpr int kBarSub = 32;
+constexpr int kBarLineWords = 32;  // 128 bytes of unsigned
+constexpr int kBarWords = (kBarSub + 2) * kBarLineWords;
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrive (thread 0 of each CTA) and wait until all nblk CTAs arrived at epoch
+// `epoch` (0-based).  acq_rel atomics chain every CTA's prior writes to the last
+// arriver, whose release of the generation word publishes them to all waiters.
+__device__ __forceinline__ bool group_arrive_wait(unsigned* bar, int rank, int nblk,
+                                                  unsigned long long epoch, uint64_t timeout_ns,
+                                                  const int* err) {
+  const int nsub = nblk < kBarSub ? nblk : kBarSub;
+  const int sub = rank % nsub;
+  const unsigned sub_size = unsigned((nblk - sub + nsub - 1) / nsub);
+  unsigned* cnt = bar + sub * kBarLineWords;
+  unsigned* top = bar + kBarSub * kBarLineWords;
+  unsigned* gen = bar + (kBarSub + 1) * kBarLineWords;
+  const unsigned target = unsigned(epoch + 1ull);
+  if (atom_add_acq_rel(cnt, 1u) == sub_size - 1u) {
+    *cnt = 0u;  // ordered before the release below; reused only after the next generation
+    if (atom_add_acq_rel(top, 1u) == unsigned(nsub) - 1u) {
+      *top = 0u;
+      st_release_u32(gen, target);
+      return true;
+    }
+  }
+  uint64_t t0 = 0;
+  unsigned ns = 32;
+  for (unsigned it = 0;; ++it) {
+    if (int(ld_acquire_u32(gen) - target) >= 0) return true;
+    if ((it & 15u) == 15u) {
+      const uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > timeout_ns) return false;
+      if (ld_relaxed_s32(err) != 0) return false;
+    }
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+}
+
+// End of a phase: barrier over the group plus a reduction of NV values.  Bit j
+// of maxmask selects max (values must be >= 0) instead of sum for v[j].
+// On return every thread of every CTA of the group holds the totals in v.
+// Returns false if a bounded wait gave up (the caller must leave the solve).
+//
+// Per-warp partials go to shared memory (double-buffered by barrier parity).  A
+// single CTA then reduces them in every warp after one __syncthreads.  With
+// several CTAs, warp 0 publishes the CTA partial and thread 0 passes the
+// hierarchical barrier; warp 0 then sums all CTAs' partials in a fixed order and
+// shares the totals through shared memory.
+template <int BS, int NV>
+__device__ __noinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsigned maxmask) {
+  static_assert(NV <= kSlots, "too many reduction slots");
+  constexpr int W = BS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* sw = g.sm_warp + (g.epoch & 1ull) * (W * kSlots);
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double t = v[j];
+    const bool mx = (maxmask >> j) & 1u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_xor_sync(kFull, t, off);
+      t = mx ? fmax(t, o) : t + o;
+    }
+    if (lane == 0) sw[warp * kSlots + j] = t;
+  }
+  __syncthreads();
+  if (*g.sm_flag) {
+    g.failed = true;
+    return false;
+  }
+  if (g.nblk == 1) {
+    // every warp reduces the warp partials in the same order (lane j <-> slot j)
+    double tot = 0.0;
+    if (lane < NV) {
+      const bool mx = (maxmask >> lane) & 1u;
+      for (int w = 0; w < W; ++w) {
+        const double o = sw[w * kSlots + lane];
+        tot = mx ? fmax(tot, o) : tot + o;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = __shfl_sync(kFull, tot, j);
+    g.epoch++;
+    return true;
+  }
+  double* buf = g.part + (size_t)(g.epoch & 1ull) * kSlots * g.nblk;
+  double* tot_sm = g.sm_tot + (g.epoch & 1ull) * kSlots;
+  if (warp == 0) {
+    if (lane < NV) {
+      const bool mx = (maxmask >> lane) & 1u;
+      double bp = 0.0;
+      for (int w = 0; w < W; ++w) {
+        const double o = sw[w * kSlots + lane];
+        bp = mx ? fmax(bp, o) : bp + o;
+      }
+      buf[lane * g.nblk + g.rank] = bp;
+    }
+    __syncwarp();
+    bool ok = true;
+    if (lane == 0) {
+      ok = group_arrive_wait(g.bar32, g.rank, g.nblk, g.epoch, g.timeout_ns, g.err);
+      if (!ok) {
+        atomicExch(g.err, 1);
+        *g.sm_flag = 1;
+      }
+    }
+    ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+    if (ok) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const bool mx = (maxmask >> j) & 1u;
+        double t = 0.0;
+        const double* src = buf + (size_t)j * g.nblk;
+        for (int b = lane; b < g.nblk; b += 32) {
+          const double o = __ldcg(src + b);
+          t = mx ? fmax(t, o) : t + o;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const double o = __shfl_xor_sync(kFull, t, off);
+          t = mx ? fmax(t, o) : t + o;
+        }
+        if (lane == 0) tot_sm[j] = t;
+      }
+    }
+  }
+  __syncthreads();
+  if (*g.sm_flag) {
+    g.failed = true;
+    return false;
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = tot_sm[j];
+  g.epoch++;
+  return true;
+}
+
+// Plain group barrier (no values).
+template <int BS>
+__device__ __forceinline__ bool group_sync(Group<BS>& g) {
+  double v[1] = {0.0};
+  return group_reduce<BS, 1>(g, v, 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Row engine over a SELL-C-sigma row space.
+//
+// Regular rows live in 32-row slices; warp w of a CTA takes slices w, w+NW, ...
+// of the CTA's range and lane l sums the row in slot l sequentially in column
+// order (coalesced 128-byte loads of column indices and values, independent
+// gathers).  Long rows are summed by one warp each (CSR, lane-strided, then a
+// shuffle tree), huge rows by the whole CTA.  The phase epilogue runs once per
+// row with the row sums.  Warps never wait for each other inside a phase, and
+// every sum is taken in a fixed order.
+// ---------------------------------------------------------------------------
+enum class Ld { Stream, Cached, Generic };
+
+template <Ld LM, class T>
+__device__ __forceinline__ T ldm(const T* p) {
+  if constexpr (LM == Ld::Stream) return ld_stream(p);
+  else if constexpr (LM == Ld::Cached) return __ldg(p);
+  else return *p;
+}
+template <Ld LM>
+__device__ __forceinline__ int64_t ldm64(const int64_t* p) {
+  if constexpr (LM == Ld::Generic) return *p;
+  else return __ldg(reinterpret_cast<const long long*>(p));
+}
+
+// Columns per TMA chunk of a slice (chunk = 32 rows x kChunkCols columns).
+constexpr int kChunkCols = 8;
+constexpr int kChunkElems = kChunkCols * 32;
+
+// Per-warp double-buffered shared-memory staging of slice chunks for two sources.
+// Values are stored in 8-byte slots so one layout serves FP32 and FP64 matrices.
+struct WarpStages {
+  int colA_[2][kChunkElems];
+  int colB_[2][kChunkElems];
+  double valA_[2][kChunkElems];
+  double valB_[2][kChunkElems];
+  uint64_t bar[2];
+  unsigned parity[2];
+  int next;
+  __device__ __forceinline__ int* colA(int st) { return colA_[st]; }
+  __device__ __forceinline__ int* colB(int st) { return colB_[st]; }
+  __device__ __forceinline__ void* valA(int st) { return valA_[st]; }
+  __device__ __forceinline__ void* valB(int st) { return valB_[st]; }
+};
+
+// Shared context of the row engine for one CTA.
+struct RowCtx {
+  WarpStages* stages;  // one per warp (TMA staging only)
+  double* red;         // BS/32 * 4 doubles
+  int* err;
+  int* fail_flag;      // shared: set when a bounded wait of this CTA gave up
+  uint64_t timeout_ns;
+};
+
+// Initialise the warps' stage barriers (once per kernel, before any phase).
+template <int BS>
+__device__ __forceinline__ void init_stages(WarpStages* st) {
+  if (threadIdx.x < BS / 32) {
+    mbar_init(&st[threadIdx.x].bar[0], 1);
+    mbar_init(&st[threadIdx.x].bar[1], 1);
+    st[threadIdx.x].parity[0] = 0;
+    st[threadIdx.x].parity[1] = 0;
+    st[threadIdx.x].next = 0;
+  }
+  fence_mbar_init();
+  __syncthreads();
+}
+
+// A product source: matrix in SELL form (regular rows) and CSR form (long and
+// huge rows), with NG gathers (0, 1 or 2) of the column index.
+struct NoGather {
+  __device__ __forceinline__ float operator()(int) const { return 0.f; }
+};
+template <class MatT, int NGv, class G1, class G2>
+struct RowSrc {
+  static constexpr int NG = NGv;
+  using mat_type = MatT;
+  Sell<MatT> S;
+  Csr<MatT> M;
+  G1 g1;
+  G2 g2;
+  bool on;
+};
+template <class MatT, class G1>
+__device__ __forceinline__ RowSrc<MatT, 1, G1, NoGather> src(const Sell<MatT>& S, const Csr<MatT>& M,
+                                                             G1 g1, bool on = true) {
+  return RowSrc<MatT, 1, G1, NoGather>{S, M, g1, NoGather{}, on};
+}
+template <class MatT, class G1, class G2>
+__device__ __forceinline__ RowSrc<MatT, 2, G1, G2> src2(const Sell<MatT>& S, const Csr<MatT>& M, G1 g1,
+                                                        G2 g2, bool on = true) {
+  return RowSrc<MatT, 2, G1, G2>{S, M, g1, g2, on};
+}
+template <class MatT>
+__device__ __forceinline__ RowSrc<MatT, 0, NoGather, NoGather> nosrc() {
+  return RowSrc<MatT, 0, NoGather, NoGather>{Sell<MatT>{}, Csr<MatT>{}, NoGather{}, NoGather{}, false};
+}
+
+// First CH column/value pairs of slot `lane` of slice s of source X, loaded
+// ahead of use (software pipelining across the slices of a warp).
+template <class MatT, int CH>
+struct SlicePre {
+  int64_t b;
+  int W;
+  int c[CH];
+  MatT v[CH];
+};
+
+template <Ld LM, int CH, class X, class MatT>
+__device__ __forceinline__ void slice_prefetch(const X& x, int s, int lane, SlicePre<MatT, CH>& p) {
+  p.W = 0;
+  if constexpr (X::NG > 0) {
+    if (!x.on) return;
+    p.b = ldm64<LM>(x.S.ptr + s);
+    p.W = int((ldm64<LM>(x.S.ptr + s + 1) - p.b) >> 5);
+    const int* cp = x.S.col + p.b + lane;
+    const MatT* vp = x.S.val + p.b + lane;
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (u < p.W) {
+        p.c[u] = ldm<LM>(cp + 32 * u);
+        p.v[u] = ldm<LM>(vp + 32 * u);
+      }
+  }
+}
+
+// Finish slot `lane` of a prefetched slice: gathers and multiply-adds of the
+// prefetched chunk, then the rest of the row in chunks, all in column order.
+template <Ld LM, int CH, class Acc, class X, class MatT>
+__device__ __forceinline__ void slice_finish(const X& x, int lane, const SlicePre<MatT, CH>& p, Acc* sums) {
+  if constexpr (X::NG > 0) {
+    if (p.W == 0) return;
+    {
+      Acc g1v[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (u < p.W) g1v[u] = Acc(x.g1(p.c[u]));
+      if constexpr (X::NG == 2) {
+        Acc g2v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+          if (u < p.W) g2v[u] = Acc(x.g2(p.c[u]));
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+          if (u < p.W) sums[1] += Acc(p.v[u]) * g2v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (u < p.W) sums[0] += Acc(p.v[u]) * g1v[u];
+    }
+    const int* cp = x.S.col + p.b + lane;
+    const MatT* vp = x.S.val + p.b + lane;
+    for (int j0 = CH; j0 < p.W; j0 += CH) {
+      int c[CH];
+      MatT v[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (j0 + u < p.W) {
+          c[u] = ldm<LM>(cp + 32 * (j0 + u));
+          v[u] = ldm<LM>(vp + 32 * (j0 + u));
+        }
+      Acc g1v[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (j0 + u < p.W) g1v[u] = Acc(x.g1(c[u]));
+      if constexpr (X::NG == 2) {
+        Acc g2v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+          if (j0 + u < p.W) g2v[u] = Acc(x.g2(c[u]));
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+          if (j0 + u < p.W) sums[1] += Acc(v[u]) * g2v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (j0 + u < p.W) sums[0] += Acc(v[u]) * g1v[u];
+    }
+  }
+}
+
+// Accumulate slot `lane` of slice s of source X into sums[0..NG) in column order.
+template <Ld LM, class Acc, class X>
+__device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums) {
+  if constexpr (X::NG > 0) {
+    if (!x.on) return;
+    const int64_t b = ldm64<LM>(x.S.ptr + s), e = ldm64<LM>(x.S.ptr + s + 1);
+    const int W = int((e - b) >> 5);
+    const int* cp = x.S.col + b + lane;
+    const auto* vp = x.S.val + b + lane;
+#pragma unroll 4
+    for (int j = 0; j < W; ++j) {
+      const int c = ldm<LM>(cp + 32 * j);
+      const Acc v = Acc(ldm<LM>(vp + 32 * j));
+      sums[0] += v * Acc(x.g1(c));
+      if constexpr (X::NG == 2) sums[1] += v * Acc(x.g2(c));
+    }
+  }
+}
+
+template <class X>
+struct SrcMat {
+  using type = typename X::mat_type;
+};
+
+// Lane-strided partial of CSR row `row` of source X, start offset `first`,
+// stride `step`; 8 elements per lane in flight.
+template <Ld LM, class Acc, class X>
+__device__ __forceinline__ void csr_part(const X& x, int row, int first, int step, Acc* sums) {
+  if constexpr (X::NG > 0) {
+    if (!x.on) return;
+    using MatT = typename SrcMat<X>::type;
+    constexpr int U = 8;
+    const int b = __ldg(x.M.rowptr + row), e = __ldg(x.M.rowptr + row + 1);
+    for (int k0 = b + first; k0 < e; k0 += U * step) {
+      int c[U];
+      MatT v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k0 + u * step < e) {
+          c[u] = ldm<LM>(x.M.col + k0 + u * step);
+          v[u] = ldm<LM>(x.M.val + k0 + u * step);
+        }
+      Acc g1v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k0 + u * step < e) g1v[u] = Acc(x.g1(c[u]));
+      if constexpr (X::NG == 2) {
+        Acc g2v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u * step < e) g2v[u] = Acc(x.g2(c[u]));
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u * step < e) sums[1] += Acc(v[u]) * g2v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k0 + u * step < e) sums[0] += Acc(v[u]) * g1v[u];
+    }
+  }
+}
+
+// Walk this CTA's share of a row space and call epi(row, const Acc* sums) once
+// per row; sums holds the A gathers then the B gathers.  part_rank < 0: the
+// whole space (single-CTA group).  red: BS/32 * 4 doubles of shared scratch.
+template <int BS, Ld LM, class Acc, class SA, class SB, class Epi>
+__device__ __noinline__ void space_rows(const SpaceLayout& sp, int part_rank, const SA& A,
+                                        const SB& B, const RowCtx& rc, Epi epi) {
+  WarpStages* stages = rc.stages;
+  double* red = rc.red;
+  int* err = rc.err;
+  const uint64_t tmo = rc.timeout_ns;
+  constexpr int NA = SA::NG, NB = SB::NG, NS = NA + NB;
+  static_assert(NS >= 1 && NS <= 4, "1..4 sums per row");
+  constexpr int NW = BS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int s0 = 0, s1 = sp.nslices, l0 = 0, l1 = sp.nlong, h0 = 0, h1 = sp.nhuge;
+  if (part_rank >= 0 && sp.slice_part) {
+    s0 = sp.slice_part[part_rank];
+    s1 = sp.slice_part[part_rank + 1];
+    l0 = sp.long_part[part_rank];
+    l1 = sp.long_part[part_rank + 1];
+    h0 = sp.huge_part[part_rank];
+    h1 = sp.huge_part[part_rank + 1];
+  }
+#ifndef PDHCG_TMA_STAGING
+#define PDHCG_TMA_STAGING 0
+#endif
+#if PDHCG_TMA_STAGING
+  // regular rows: the warp streams its slices in chunks of kChunkCols columns.
+  // Lane 0 bulk-copies (TMA) the next chunk's column indices and values of both
+  // sources into the warp's other shared-memory stage while the lanes gather and
+  // multiply-add the current chunk; the row epilogue runs after a slice's last chunk.
+  if (sp.nslices > 0 && s0 + warp < s1) {
+    using MA = typename SrcMat<SA>::type;
+    using MB = typename SrcMat<SB>::type;
+    constexpr int CC = kChunkCols;
+    constexpr int CE = CC * 32;
+    WarpStages& ws = stages[warp];
+    const bool onA = NA > 0 && A.on, onB = NB > 0 && B.on;
+    // slice geometry
+    auto geom = [&](int s, int64_t& ba, int& wa, int64_t& bb, int& wb) {
+      ba = 0; wa = 0; bb = 0; wb = 0;
+      if constexpr (NA > 0) if (onA) { ba = ldm64<LM>(A.S.ptr + s); wa = int((ldm64<LM>(A.S.ptr + s + 1) - ba) >> 5); }
+      if constexpr (NB > 0) if (onB) { bb = ldm64<LM>(B.S.ptr + s); wb = int((ldm64<LM>(B.S.ptr + s + 1) - bb) >> 5); }
+    };
+    // issue chunk ch of slice (ba, wa, bb, wb) into stage st
+    auto issue = [&](int st, int ch, int64_t ba, int wa, int64_t bb, int wb) {
+      if (lane == 0) {
+        const int na = max(0, min(CC, wa - ch * CC)), nb = max(0, min(CC, wb - ch * CC));
+        const unsigned bytes = unsigned(na) * 32u * (4u + sizeof(MA)) + unsigned(nb) * 32u * (4u + sizeof(MB));
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&ws.bar[st], bytes);
+        if constexpr (NA > 0)
+          if (na > 0) {
+            const int64_t off = ba + int64_t(ch) * CE;
+            bulk_g2s(ws.colA(st), A.S.col + off, unsigned(na) * 128u, &ws.bar[st]);
+            bulk_g2s(ws.valA(st), A.S.val + off, unsigned(na) * 32u * sizeof(MA), &ws.bar[st]);
+          }
+        if constexpr (NB > 0)
+          if (nb > 0) {
+            const int64_t off = bb + int64_t(ch) * CE;
+            bulk_g2s(ws.colB(st), B.S.col + off, unsigned(nb) * 128u, &ws.bar[st]);
+            bulk_g2s(ws.valB(st), B.S.val + off, unsigned(nb) * 32u * sizeof(MB), &ws.bar[st]);
+          }
+      }
+    };
+    // stage index and barrier parities live in registers (identical in all
+    // lanes) and are written back to shared memory once at the end
+    int st = ws.next;
+    unsigned par[2] = {ws.parity[0], ws.parity[1]};
+    __syncwarp();
+    int s = s0 + warp;
+    int64_t ba, bb;
+    int wa, wb;
+    geom(s, ba, wa, bb, wb);
+    int nch = (max(wa, wb) + CC - 1) / CC;
+    int ch = 0;
+    bool have = false;  // chunk (s, ch) already issued into stage st
+    int row = ldm<LM>(sp.perm + s * 32 + lane);
+    Acc sums[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+    int sn = s + NW;
+    int64_t nba = 0, nbb = 0;
+    int nwa = 0, nwb = 0;
+    if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
+    bool failed = false;
+    while (true) {
+      if (ch < nch) {
+        if (!have) issue(st, ch, ba, wa, bb, wb);
+        // prefetch the following chunk (this slice or the next one)
+        bool have2 = false;
+        if (ch + 1 < nch) {
+          issue(st ^ 1, ch + 1, ba, wa, bb, wb);
+          have2 = true;
+        } else if (sn < s1 && max(nwa, nwb) > 0) {
+          issue(st ^ 1, 0, nba, nwa, nbb, nwb);
+          have2 = true;
+        }
+        if (!mbar_wait(&ws.bar[st], par[st], tmo)) {
+          // give the prefetched copy (if any) a bounded chance to land before leaving
+          if (have2) mbar_wait(&ws.bar[st ^ 1], par[st ^ 1], tmo);
+          failed = true;
+          break;
+        }
+        par[st] ^= 1u;
+        if constexpr (NA > 0)
+          if (onA && ch * CC < wa) {
+            const int na = min(CC, wa - ch * CC);
+            const int* cs = ws.colA(st) + lane;
+            const MA* vs = reinterpret_cast<const MA*>(ws.valA(st)) + lane;
+            Acc g1v[CC];
+#pragma unroll
+            for (int u = 0; u < CC; ++u)
+              if (u < na) g1v[u] = Acc(A.g1(cs[32 * u]));
+            if constexpr (NA == 2) {
+              Acc g2v[CC];
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < na) g2v[u] = Acc(A.g2(cs[32 * u]));
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < na) sums[1] += Acc(vs[32 * u]) * g2v[u];
+            }
+#pragma unroll
+            for (int u = 0; u < CC; ++u)
+              if (u < na) sums[0] += Acc(vs[32 * u]) * g1v[u];
+          }
+        if constexpr (NB > 0)
+          if (onB && ch * CC < wb) {
+            const int nb = min(CC, wb - ch * CC);
+            const int* cs = ws.colB(st) + lane;
+            const MB* vs = reinterpret_cast<const MB*>(ws.valB(st)) + lane;
+            Acc g1v[CC];
+#pragma unroll
+            for (int u = 0; u < CC; ++u)
+              if (u < nb) g1v[u] = Acc(B.g1(cs[32 * u]));
+            if constexpr (NB == 2) {
+              Acc g2v[CC];
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < nb) g2v[u] = Acc(B.g2(cs[32 * u]));
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < nb) sums[NA + 1] += Acc(vs[32 * u]) * g2v[u];
+            }
+#pragma unroll
+            for (int u = 0; u < CC; ++u)
+              if (u < nb) sums[NA] += Acc(vs[32 * u]) * g1v[u];
+          }
+        __syncwarp();  // every lane is done with stage st before it is refilled
+        st ^= 1;
+        ++ch;
+        have = have2;
+        continue;
+      }
+      // slice done
+      if (row >= 0) epi(row, sums);
+      if (sn >= s1) break;
+      s = sn;
+      ba = nba;
+      wa = nwa;
+      bb = nbb;
+      wb = nwb;
+      nch = (max(wa, wb) + CC - 1) / CC;
+      ch = 0;
+      row = ldm<LM>(sp.perm + s * 32 + lane);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+      sn = s + NW;
+      if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      ws.next = st;
+      ws.parity[0] = par[0];
+      ws.parity[1] = par[1];
+      if (failed) {
+        atomicExch(err, 1);
+        *rc.fail_flag = 1;
+      }
+    }
+    __syncwarp();
+  }
+#else
+  // regular rows: one slice per warp at a time, lane l summing the row in slot l
+  for (int s = s0 + warp; s < s1; s += NW) {
+    const int row = ldm<LM>(sp.perm + s * 32 + lane);
+    Acc sums[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+    slice_dot<LM, Acc>(A, s, lane, sums);
+    slice_dot<LM, Acc>(B, s, lane, sums + NA);
+    if (row >= 0) epi(row, sums);
+  }
+#endif
+  // long rows: one warp per row
+  for (int li = l0 + warp; li < l1; li += NW) {
+    const int row = __ldg(sp.longs + li);
+    Acc sums[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+    csr_part<LM, Acc>(A, row, lane, 32, sums);
+    csr_part<LM, Acc>(B, row, lane, 32, sums + NA);
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sums[q] += __shfl_xor_sync(kFull, sums[q], off);
+    if (lane == 0) epi(row, sums);
+  }
+  // huge rows: the whole CTA per row
+  for (int hi = h0; hi < h1; ++hi) {
+    const int row = __ldg(sp.huges + hi);
+    Acc sums[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+    csr_part<LM, Acc>(A, row, threadIdx.x, BS, sums);
+    csr_part<LM, Acc>(B, row, threadIdx.x, BS, sums + NA);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sums[q] += __shfl_xor_sync(kFull, sums[q], off);
+      if (lane == 0) red[warp * 4 + q] = double(sums[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Acc tot[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        tot[q] = Acc(0);
+        for (int w = 0; w < NW; ++w) tot[q] += Acc(red[w * 4 + q]);
+      }
+      epi(row, tot);
+    }
+    __syncthreads();
+  }
+}
+
+// Elementwise walk of [lo, hi) (no CSR work), one element per thread.
+template <int BS, class Body>
+__device__ __forceinline__ void for_elems(int lo, int hi, Body body) {
+#pragma unroll 4
+  for (int i = lo + (int)threadIdx.x; i < hi; i += BS) body(i);
+}
+
+}  // namespace pdhcg

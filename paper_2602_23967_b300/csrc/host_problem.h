@@ -1,0 +1,112 @@
+// host_problem.h — host-side representation of a pdhcg_t handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pdhcg_internal.h"
+
+namespace pdhcg {
+
+void set_error(const std::string& msg);
+
+// Validated, canonical host copy of a problem (integer layout work only: the
+// method's arithmetic all runs on the device).
+struct HostQP {
+  int32_t n = 0, m = 0;
+  bool has_q = false, diag_q = true, any_box = false;
+  std::vector<int32_t> Qp, Qc, Ap, Ac, ATp, ATc;
+  std::vector<double> Qv, Av, ATv;
+  std::vector<double> c, lc, uc, lv, uv;
+  std::vector<int8_t> vtype, ctype;
+};
+
+// Validate and canonicalise; returns PDHCG_OK or PDHCG_E_INVALID (with set_error).
+int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
+                  const double* uc, const double* lv, const double* uv, HostQP* out);
+
+// SELL-C-sigma layout of a row space with up to two matrices (integer part;
+// values are filled on the device from the scaled CSR values).
+struct SellHost {
+  int32_t nslices = 0;
+  std::vector<int32_t> perm;   // nslices*32, -1 = padding
+  std::vector<int32_t> longs;  // rows handled warp-per-row
+  std::vector<int32_t> huges;  // rows handled CTA-per-row
+  std::vector<int64_t> ptr[2];
+  std::vector<int32_t> col[2];
+};
+constexpr int kSellSigma = 1024;
+constexpr int64_t kLongRow = 64;
+constexpr int64_t kHugeRow = 2048;
+void build_sell(int32_t nrows, int nmat, const std::vector<int32_t>* rp[2],
+                const std::vector<int32_t>* ci[2], SellHost* out);
+// Split items with the given weights into nblk contiguous ranges (nblk + 1 bounds).
+std::vector<int32_t> split_balanced(const std::vector<int64_t>& w, int nblk);
+
+// Device bytes a problem will hold (for admission control).
+size_t device_footprint(const HostQP& h, int precision);
+
+struct PartitionSet {
+  int nblk = 0;
+  int32_t* d_buf = nullptr;  // 8 tables of nblk + 1 entries
+  int32_t *v_slice = nullptr, *v_long = nullptr, *v_huge = nullptr;
+  int32_t *c_slice = nullptr, *c_long = nullptr, *c_huge = nullptr;
+  int32_t *v_even = nullptr, *c_even = nullptr;  // even row splits for elementwise work
+};
+
+}  // namespace pdhcg
+
+// Opaque handle of the C ABI.
+struct pdhcg_problem {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pdhcg_params prm{};
+  int precision = PDHCG_FP64;
+  int method = PDHCG_INNER_DIAG;
+  int32_t n = 0, m = 0;
+  int64_t nnzQ = 0, nnzA = 0;
+  bool has_q = false;
+  int lanes_var = 4, lanes_con = 4;
+  // host copies kept for partitioning
+  std::vector<int32_t> Qp, Ap, ATp;
+  pdhcg::SellHost vsell, csell;  // integer SELL layouts (var space: AT [+ Q], con space: A)
+  // device SELL arrays
+  int32_t *v_perm = nullptr, *v_longs = nullptr, *v_huges = nullptr;
+  int32_t *c_perm = nullptr, *c_longs = nullptr, *c_huges = nullptr;
+  int64_t *sATp = nullptr, *sQp = nullptr, *sAp = nullptr;
+  int32_t *sATc = nullptr, *sQc = nullptr, *sAc = nullptr;
+  void *sATv = nullptr, *sQv = nullptr, *sAv = nullptr;  // MatT
+  // single device arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  // typed device pointers (void* so the handle is precision-agnostic)
+  int32_t *Qp_d = nullptr, *Qc_d = nullptr, *Ap_d = nullptr, *Ac_d = nullptr, *ATp_d = nullptr,
+          *ATc_d = nullptr;
+  double *Qv_o = nullptr, *Av_o = nullptr, *ATv_o = nullptr;
+  void *Qs = nullptr, *As = nullptr, *ATs = nullptr;  // MatT
+  double *c_o = nullptr, *lv_o = nullptr, *uv_o = nullptr, *lc_o = nullptr, *uc_o = nullptr;
+  double *D = nullptr, *E = nullptr, *Dn = nullptr, *En = nullptr, *pv = nullptr, *pw = nullptr,
+         *pt = nullptr;
+  void *c = nullptr, *lv = nullptr, *uv = nullptr, *lc = nullptr, *uc = nullptr, *qdiag = nullptr;
+  int8_t *vtype = nullptr, *ctype = nullptr;
+  void *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr, *xT = nullptr, *yT = nullptr,
+       *xa = nullptr, *ya = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr,
+       *bv = nullptr, *grad = nullptr, *gprev = nullptr, *xprev = nullptr, *xbar = nullptr;
+  double *x_stage = nullptr, *y_stage = nullptr, *x_init_stage = nullptr, *y_init_stage = nullptr;
+  pdhcg::SolverState* st = nullptr;
+  // launch scratch: desc, plan arrays, barrier counter, partials
+  void* inst_d = nullptr;  // one Inst<MatT, VecT>
+  int32_t* plan_i32 = nullptr;           // g_first, g_nblk, g_inst, pool_inst, pool_next, err
+  unsigned long long* bar = nullptr;
+  int64_t* part_off = nullptr;
+  double* part = nullptr;                // 2 * kSlots * max_blk
+  int max_blk = 0;
+  std::map<int, pdhcg::PartitionSet> partitions;
+  // setup results
+  pdhcg::SolverState setup_state{};
+  pdhcg::SolverState last_state{};  // state at the end of the last pdhcg_solve / _dev
+};

@@ -1,0 +1,86 @@
+// kernels_impl.cuh — launch wrappers, included once per precision.
+#pragma once
+#include "launch.h"
+#include "setup_kernel.cuh"
+#include "solve_kernel.cuh"
+
+#include <algorithm>
+
+namespace pdhcg {
+
+inline size_t solve_dyn_smem() { return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (kGroupBS / 32) : 0; }
+
+template <class MatT, class VecT>
+cudaError_t set_solve_attrs() {
+  return cudaFuncSetAttribute(solve_kernel<kGroupBS, MatT, VecT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(solve_dyn_smem()));
+}
+
+template <class MatT, class VecT>
+cudaError_t kernel_limits(KernelLimits* out) {
+  int dev = 0, sms = 0, nb = 0, ns = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = set_solve_attrs<MatT, VecT>();
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT>, kGroupBS,
+                                                    solve_dyn_smem());
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ns, setup_kernel<kGroupBS, MatT, VecT>, kGroupBS, 0);
+  if (e != cudaSuccess) return e;
+  out->max_coresident_group = sms * nb;
+  out->max_coresident_setup = sms * ns;
+  return cudaSuccess;
+}
+
+template <class MatT, class VecT>
+cudaError_t launch_setup(const SetupArgs<MatT, VecT>& a, int nblk, unsigned long long* bar,
+                         double* part, int32_t* err, uint64_t timeout_ns, cudaStream_t s) {
+  SetupArgs<MatT, VecT> aa = a;
+  if (nblk <= 1) {
+    setup_kernel<kGroupBS, MatT, VecT><<<1, kGroupBS, 0, s>>>(aa, bar, part, err, timeout_ns);
+    return cudaGetLastError();
+  }
+  void* args[] = {&aa, &bar, &part, &err, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void*)setup_kernel<kGroupBS, MatT, VecT>, dim3(nblk),
+                                     dim3(kGroupBS), args, 0, s);
+}
+
+template <class MatT, class VecT>
+cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan, int grid,
+                         cudaStream_t s) {
+  LaunchPlan p = plan;
+  const Inst<MatT, VecT>* di = d_insts;
+  cudaError_t e = set_solve_attrs<MatT, VecT>();
+  if (e != cudaSuccess) return e;
+  const size_t smem = solve_dyn_smem();
+  if (plan.group_blocks == 0) {
+    solve_kernel<kPoolBS, MatT, VecT><<<grid, kPoolBS, smem, s>>>(di, p);
+    return cudaGetLastError();
+  }
+  void* args[] = {&di, &p};
+  return cudaLaunchCooperativeKernel((const void*)solve_kernel<kGroupBS, MatT, VecT>, dim3(grid),
+                                     dim3(kGroupBS), args, smem, s);
+}
+
+template <class MatT>
+cudaError_t launch_sell_fill(int nslices, const int32_t* perm, const int64_t* sptr,
+                             const int32_t* rowptr, const MatT* csr_val, MatT* sell_val, cudaStream_t s) {
+  if (nslices <= 0) return cudaSuccess;
+  const int wpb = 8;
+  const int grid = std::min((nslices + wpb - 1) / wpb, 4096);
+  sell_fill_kernel<MatT><<<grid, wpb * 32, 0, s>>>(nslices, perm, sptr, rowptr, csr_val, sell_val);
+  return cudaGetLastError();
+}
+
+#define PDHCG_INSTANTIATE(MatT, VecT)                                                          \
+  template cudaError_t kernel_limits<MatT, VecT>(KernelLimits*);                               \
+  template cudaError_t launch_setup<MatT, VecT>(const SetupArgs<MatT, VecT>&, int,             \
+                                                unsigned long long*, double*, int32_t*,        \
+                                                uint64_t, cudaStream_t);                       \
+  template cudaError_t launch_solve<MatT, VecT>(const Inst<MatT, VecT>*, const LaunchPlan&, int, \
+                                                cudaStream_t);
+
+}  // namespace pdhcg

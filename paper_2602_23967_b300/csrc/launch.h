@@ -1,0 +1,40 @@
+// launch.h — typed launch entry points of the setup and solve kernels (one
+// explicit instantiation per precision in kernels_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pdhcg_internal.h"
+
+namespace pdhcg {
+
+template <class MatT, class VecT>
+struct SetupArgs;
+
+// CTA sizes: multi-CTA groups (one large instance) and pooled single-CTA solves.
+constexpr int kGroupBS = 256;
+constexpr int kPoolBS = 256;
+
+struct KernelLimits {
+  int max_coresident_group;  // CTAs of the solve kernel resident at once (SMs x occupancy)
+  int max_coresident_setup;
+};
+
+template <class MatT, class VecT>
+cudaError_t kernel_limits(KernelLimits* out);
+
+// Setup of one instance on nblk co-resident CTAs (cooperative when nblk > 1).
+template <class MatT, class VecT>
+cudaError_t launch_setup(const SetupArgs<MatT, VecT>& a, int nblk, unsigned long long* bar,
+                         double* part, int32_t* err, uint64_t timeout_ns, cudaStream_t s);
+
+// Solve launch; cooperative when plan.group_blocks > 0.
+template <class MatT, class VecT>
+cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan, int grid,
+                         cudaStream_t s);
+
+// Copy scaled CSR values into SELL slice order (one instantiation per value type).
+template <class MatT>
+cudaError_t launch_sell_fill(int nslices, const int32_t* perm, const int64_t* sptr,
+                             const int32_t* rowptr, const MatT* csr_val, MatT* sell_val, cudaStream_t s);
+
+}  // namespace pdhcg

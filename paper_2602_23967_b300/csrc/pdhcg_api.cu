@@ -1,0 +1,996 @@
+// pdhcg_api.cu — the C ABI of include/pdhcg.h: create / solve / solve_batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "host_problem.h"
+#include "launch.h"
+#include "setup_kernel.cuh"
+
+namespace pdhcg {
+
+const char* last_error_cstr();
+
+template <class M, class V>
+struct Prec {
+  using Mat = M;
+  using Vec = V;
+};
+
+template <class F>
+int dispatch_precision(int precision, F&& f) {
+  switch (precision) {
+    case PDHCG_FP64: return f(Prec<double, double>{});
+    case PDHCG_FP32: return f(Prec<float, float>{});
+    case PDHCG_MIXED: return f(Prec<float, double>{});
+    default: set_error("unknown precision"); return PDHCG_E_INVALID;
+  }
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PDHCG_E_OOM : PDHCG_E_CUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+size_t mat_bytes(int precision) { return precision == PDHCG_FP64 ? 8 : 4; }
+size_t vec_bytes(int precision) { return precision == PDHCG_FP32 ? 4 : 8; }
+
+// Carves 256-byte aligned buffers out of one allocation (first a sizing pass).
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += std::max<size_t>(count, 1) * sizeof(T);
+    return p;
+  }
+  void* take_bytes(size_t elems, size_t esize) {
+    off = (off + 255) & ~size_t(255);
+    void* p = base ? base + off : nullptr;
+    off += std::max<size_t>(elems, 1) * esize;
+    return p;
+  }
+};
+
+void carve(pdhcg_problem* P, Carver& cv) {
+  const size_t n = size_t(P->n), m = size_t(P->m), nq = size_t(P->nnzQ), na = size_t(P->nnzA);
+  const size_t mb = mat_bytes(P->precision), vb = vec_bytes(P->precision);
+  P->Qp_d = cv.take<int32_t>(n + 1);
+  P->Qc_d = cv.take<int32_t>(nq);
+  P->Ap_d = cv.take<int32_t>(m + 1);
+  P->Ac_d = cv.take<int32_t>(na);
+  P->ATp_d = cv.take<int32_t>(n + 1);
+  P->ATc_d = cv.take<int32_t>(na);
+  P->Qv_o = cv.take<double>(nq);
+  P->Av_o = cv.take<double>(na);
+  P->ATv_o = cv.take<double>(na);
+  P->Qs = cv.take_bytes(nq, mb);
+  P->As = cv.take_bytes(na, mb);
+  P->ATs = cv.take_bytes(na, mb);
+  P->c_o = cv.take<double>(n);
+  P->lv_o = cv.take<double>(n);
+  P->uv_o = cv.take<double>(n);
+  P->lc_o = cv.take<double>(m);
+  P->uc_o = cv.take<double>(m);
+  P->D = cv.take<double>(n);
+  P->E = cv.take<double>(m);
+  P->Dn = cv.take<double>(n);
+  P->En = cv.take<double>(m);
+  P->pv = cv.take<double>(n);
+  P->pw = cv.take<double>(n);
+  P->pt = cv.take<double>(m);
+  P->c = cv.take_bytes(n, vb);
+  P->lv = cv.take_bytes(n, vb);
+  P->uv = cv.take_bytes(n, vb);
+  P->qdiag = cv.take_bytes(n, vb);
+  P->lc = cv.take_bytes(m, vb);
+  P->uc = cv.take_bytes(m, vb);
+  P->vtype = cv.take<int8_t>(n);
+  P->ctype = cv.take<int8_t>(m);
+  void** nvecs[] = {&P->xb0, &P->xb1, &P->xT, &P->xa, &P->r, &P->p0, &P->p1, &P->q,
+                    &P->bv, &P->grad, &P->gprev, &P->xprev, &P->xbar};
+  for (void** pp : nvecs) *pp = cv.take_bytes(n, vb);
+  void** mvecs[] = {&P->yb0, &P->yb1, &P->yT, &P->ya};
+  for (void** pp : mvecs) *pp = cv.take_bytes(m, vb);
+  P->x_stage = cv.take<double>(n);
+  P->y_stage = cv.take<double>(m);
+  P->x_init_stage = cv.take<double>(n);
+  P->y_init_stage = cv.take<double>(m);
+  P->st = cv.take<SolverState>(1);
+  P->inst_d = cv.take_bytes(1, sizeof(Inst<double, double>));
+  P->plan_i32 = cv.take<int32_t>(16);
+  P->bar = static_cast<unsigned long long*>(cv.take_bytes(kBarBytes, 1));
+  P->part_off = cv.take<int64_t>(1);
+  P->part = cv.take<double>(size_t(2) * kSlots * size_t(std::max(P->max_blk, 1)));
+  // SELL layouts (+ 64 bytes of tail padding each)
+  P->v_perm = cv.take<int32_t>(P->vsell.perm.size());
+  P->v_longs = cv.take<int32_t>(P->vsell.longs.size());
+  P->v_huges = cv.take<int32_t>(P->vsell.huges.size());
+  P->c_perm = cv.take<int32_t>(P->csell.perm.size());
+  P->c_longs = cv.take<int32_t>(P->csell.longs.size());
+  P->c_huges = cv.take<int32_t>(P->csell.huges.size());
+  P->sATp = cv.take<int64_t>(P->vsell.ptr[0].size());
+  P->sQp = cv.take<int64_t>(P->vsell.ptr[1].size());
+  P->sAp = cv.take<int64_t>(P->csell.ptr[0].size());
+  P->sATc = cv.take<int32_t>(P->vsell.col[0].size() + 16);
+  P->sQc = cv.take<int32_t>(P->vsell.col[1].size() + 16);
+  P->sAc = cv.take<int32_t>(P->csell.col[0].size() + 16);
+  P->sATv = cv.take_bytes(P->vsell.col[0].size() + 16, mb);
+  P->sQv = cv.take_bytes(P->vsell.col[1].size() + 16, mb);
+  P->sAv = cv.take_bytes(P->csell.col[0].size() + 16, mb);
+}
+
+int lanes_for(double avg) {
+  int L = 2;
+  while (L < 32 && L * 2 <= avg) L *= 2;
+  return L;
+}
+
+// nnz-balanced row partition into nblk ranges; rows of length >= long_thr get a range alone.
+std::vector<int32_t> partition_rows(const std::vector<int64_t>& len, int nblk, int64_t long_thr) {
+  const int32_t R = int32_t(len.size());
+  int64_t total = 0;
+  for (int64_t l : len) total += l + 2;
+  double target = std::max(1.0, std::ceil(double(total) / nblk));
+  std::vector<int32_t> b;
+  for (int attempt = 0; attempt < 200; ++attempt) {
+    b.assign(1, 0);
+    int64_t acc = 0;
+    for (int32_t r = 0; r < R; ++r) {
+      if (len[r] >= long_thr) {
+        if (b.back() < r) b.push_back(r);
+        b.push_back(r + 1);
+        acc = 0;
+        continue;
+      }
+      acc += len[r] + 2;
+      if (double(acc) >= target) {
+        b.push_back(r + 1);
+        acc = 0;
+      }
+    }
+    if (b.back() < R) b.push_back(R);
+    if (int(b.size()) - 1 <= nblk) break;
+    target *= 1.1;
+  }
+  while (int(b.size()) - 1 < nblk) b.push_back(R);
+  return b;
+}
+
+// Elementwise phases split [0, n) and [0, m) evenly over the CTAs of a group.
+std::vector<int32_t> even_split(int32_t rows, int nblk) {
+  std::vector<int32_t> b(size_t(nblk) + 1);
+  for (int k = 0; k <= nblk; ++k) b[size_t(k)] = int32_t((int64_t(rows) * k) / nblk);
+  return b;
+}
+
+int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
+  auto it = P->partitions.find(nblk);
+  if (it != P->partitions.end()) {
+    *out = &it->second;
+    return PDHCG_OK;
+  }
+  PartitionSet ps;
+  ps.nblk = nblk;
+  auto slice_w = [](const SellHost& sh, int nmat) {
+    std::vector<int64_t> w(size_t(sh.nslices), 0);
+    for (int k = 0; k < nmat; ++k)
+      for (int32_t s = 0; s < sh.nslices; ++s) w[size_t(s)] += sh.ptr[k][size_t(s) + 1] - sh.ptr[k][size_t(s)] + 8;
+    return w;
+  };
+  auto row_w = [](const std::vector<int32_t>& rows, const std::vector<int32_t>* rp0,
+                  const std::vector<int32_t>* rp1) {
+    std::vector<int64_t> w(rows.size(), 0);
+    for (size_t i = 0; i < rows.size(); ++i) {
+      const int32_t r = rows[i];
+      w[i] = (*rp0)[size_t(r) + 1] - (*rp0)[size_t(r)] + (rp1 && !rp1->empty() ? (*rp1)[size_t(r) + 1] - (*rp1)[size_t(r)] : 0) + 8;
+    }
+    return w;
+  };
+  const std::vector<int32_t>* qrp = P->has_q ? &P->Qp : nullptr;
+  std::vector<int32_t> tabs[6] = {
+      split_balanced(slice_w(P->vsell, P->has_q ? 2 : 1), nblk),
+      split_balanced(row_w(P->vsell.longs, &P->ATp, qrp), nblk),
+      split_balanced(row_w(P->vsell.huges, &P->ATp, qrp), nblk),
+      split_balanced(slice_w(P->csell, 1), nblk),
+      split_balanced(row_w(P->csell.longs, &P->Ap, nullptr), nblk),
+      split_balanced(row_w(P->csell.huges, &P->Ap, nullptr), nblk)};
+  std::vector<int32_t> ev = even_split(P->n, nblk), ec = even_split(P->m, nblk);
+  // huge rows go to the last CTAs (their slice share is balanced separately)
+  for (int t : {2, 5}) {
+    std::vector<int32_t>& b = tabs[t];
+    const int32_t nh = b.back();
+    for (int k = 0; k <= nblk; ++k) b[size_t(k)] = std::max(0, std::min(nh, k - (nblk - nh)));
+  }
+  const size_t per = size_t(nblk) + 1;
+  CK(cudaMalloc(&ps.d_buf, sizeof(int32_t) * per * 8));
+  std::vector<int32_t> flat;
+  for (auto& t : tabs) flat.insert(flat.end(), t.begin(), t.end());
+  flat.insert(flat.end(), ev.begin(), ev.end());
+  flat.insert(flat.end(), ec.begin(), ec.end());
+  CK(cudaMemcpy(ps.d_buf, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
+  ps.v_slice = ps.d_buf;
+  ps.v_long = ps.d_buf + per;
+  ps.v_huge = ps.d_buf + 2 * per;
+  ps.c_slice = ps.d_buf + 3 * per;
+  ps.c_long = ps.d_buf + 4 * per;
+  ps.c_huge = ps.d_buf + 5 * per;
+  ps.v_even = ps.d_buf + 6 * per;
+  ps.c_even = ps.d_buf + 7 * per;
+  auto res = P->partitions.emplace(nblk, ps);
+  *out = &res.first->second;
+  return PDHCG_OK;
+}
+
+DevParams dev_params(const pdhcg_params& p) {
+  DevParams d;
+  d.eps_tol = p.eps_tol;
+  d.eps_inf = p.eps_inf;
+  d.time_limit_ns = p.time_limit_s * 1e9;
+  d.max_iter = p.max_iter;
+  d.theta = p.theta;
+  d.kp = p.kp;
+  d.ki = p.ki;
+  d.kd = p.kd;
+  d.gamma_inner = p.gamma_inner;
+  d.eps_inner_min = p.eps_inner_min;
+  d.eps_inner_first = p.eps_inner_first;
+  d.restart_sufficient = p.restart_sufficient;
+  d.restart_necessary = p.restart_necessary;
+  d.restart_artificial = p.restart_artificial;
+  d.omega_clamp = p.omega_clamp;
+  d.k_eval = p.k_eval;
+  d.max_inner_iter = p.max_inner_iter;
+  return d;
+}
+
+template <class MatT, class VecT>
+Inst<MatT, VecT> make_inst(const pdhcg_problem* P) {
+  Inst<MatT, VecT> I;
+  I.n = P->n;
+  I.m = P->m;
+  I.has_q = P->has_q ? 1 : 0;
+  I.lanes_var = P->lanes_var;
+  I.lanes_con = P->lanes_con;
+  I.Q = Csr<MatT>{P->n, int32_t(P->nnzQ), P->Qp_d, P->Qc_d, static_cast<const MatT*>(P->Qs)};
+  I.A = Csr<MatT>{P->m, int32_t(P->nnzA), P->Ap_d, P->Ac_d, static_cast<const MatT*>(P->As)};
+  I.AT = Csr<MatT>{P->n, int32_t(P->nnzA), P->ATp_d, P->ATc_d, static_cast<const MatT*>(P->ATs)};
+  I.ATs = Sell<MatT>{P->sATp, P->sATc, static_cast<const MatT*>(P->sATv)};
+  I.Qs = Sell<MatT>{P->sQp, P->sQc, static_cast<const MatT*>(P->sQv)};
+  I.As = Sell<MatT>{P->sAp, P->sAc, static_cast<const MatT*>(P->sAv)};
+  I.vsp.nslices = P->vsell.nslices;
+  I.vsp.nlong = int32_t(P->vsell.longs.size());
+  I.vsp.nhuge = int32_t(P->vsell.huges.size());
+  I.vsp.perm = P->v_perm;
+  I.vsp.longs = P->v_longs;
+  I.vsp.huges = P->v_huges;
+  I.csp.nslices = P->csell.nslices;
+  I.csp.nlong = int32_t(P->csell.longs.size());
+  I.csp.nhuge = int32_t(P->csell.huges.size());
+  I.csp.perm = P->c_perm;
+  I.csp.longs = P->c_longs;
+  I.csp.huges = P->c_huges;
+  I.c = static_cast<const VecT*>(P->c);
+  I.lv = static_cast<const VecT*>(P->lv);
+  I.uv = static_cast<const VecT*>(P->uv);
+  I.lc = static_cast<const VecT*>(P->lc);
+  I.uc = static_cast<const VecT*>(P->uc);
+  I.qdiag = static_cast<const VecT*>(P->qdiag);
+  I.vtype = P->vtype;
+  I.ctype = P->ctype;
+  I.D = P->D;
+  I.E = P->E;
+  I.c_o = P->c_o;
+  I.lv_o = P->lv_o;
+  I.uv_o = P->uv_o;
+  I.lc_o = P->lc_o;
+  I.uc_o = P->uc_o;
+  I.bscale = P->setup_state.bscale;
+  I.cinf = P->setup_state.cinf;
+  I.xb0 = static_cast<VecT*>(P->xb0);
+  I.xb1 = static_cast<VecT*>(P->xb1);
+  I.yb0 = static_cast<VecT*>(P->yb0);
+  I.yb1 = static_cast<VecT*>(P->yb1);
+  I.xT = static_cast<VecT*>(P->xT);
+  I.yT = static_cast<VecT*>(P->yT);
+  I.xa = static_cast<VecT*>(P->xa);
+  I.ya = static_cast<VecT*>(P->ya);
+  I.r = static_cast<VecT*>(P->r);
+  I.p0 = static_cast<VecT*>(P->p0);
+  I.p1 = static_cast<VecT*>(P->p1);
+  I.q = static_cast<VecT*>(P->q);
+  I.bv = static_cast<VecT*>(P->bv);
+  I.grad = static_cast<VecT*>(P->grad);
+  I.gprev = static_cast<VecT*>(P->gprev);
+  I.xprev = static_cast<VecT*>(P->xprev);
+  I.xbar = static_cast<VecT*>(P->xbar);
+  I.st = P->st;
+  I.prm = dev_params(P->prm);
+  return I;
+}
+
+template <class MatT, class VecT>
+void set_partition(Inst<MatT, VecT>& I, const PartitionSet& ps, const pdhcg_problem* P) {
+  I.vsp.slice_part = ps.v_slice;
+  I.vsp.long_part = ps.v_long;
+  I.vsp.huge_part = ps.v_huge;
+  I.csp.slice_part = ps.c_slice;
+  I.csp.long_part = ps.c_long;
+  I.csp.huge_part = ps.c_huge;
+  I.var_part = ps.v_even;
+  I.con_part = ps.c_even;
+  I.part_blocks = ps.nblk;
+  (void)P;
+}
+
+SolverState initial_state(const pdhcg_problem* P) {
+  SolverState S = P->setup_state;
+  S.K = 0;
+  S.k = 0;
+  S.inner_total = 0;
+  S.restarts = 0;
+  S.omega = S.omega0;
+  S.log_omega = std::log(S.omega0);
+  S.log_omega0 = S.log_omega;
+  S.e_sum = 0.0;
+  S.e_prev = 0.0;
+  S.tau = S.eta / S.omega;
+  S.sigma = S.eta * S.omega;
+  S.eps_in = INFINITY;
+  S.mv = 0.0;
+  S.fpr_anchor = 0.0;
+  S.fpr_last = 0.0;
+  S.r_primal = S.r_dual = S.r_gap = S.pobj = S.dobj = 0.0;
+  S.t_start_ns = S.t_end_ns = 0.0;
+  S.status = 0;
+  S.cur = 0;
+  S.started = 0;
+  S.method = P->method;
+  S.device_error = 0;
+  for (double& t : S.tm) t = 0.0;
+  return S;
+}
+
+void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res) {
+  std::memset(res, 0, sizeof(*res));
+  res->status = S.status;
+  res->inner_method = S.method;
+  res->iterations = S.K;
+  res->inner_iterations = S.inner_total;
+  res->restarts = S.restarts;
+  res->r_primal = S.r_primal;
+  res->r_dual = S.r_dual;
+  res->r_gap = S.r_gap;
+  res->primal_obj = S.pobj;
+  res->dual_obj = S.dobj;
+  res->eta = S.eta;
+  res->omega = S.omega;
+  res->norm_A = S.norm_A;
+  res->solve_seconds = (S.t_end_ns - S.t_start_ns) * 1e-9;
+  res->power_iters = S.power_iters;
+  res->precision = P->precision;
+}
+
+int max_group_blocks(int precision) {
+  KernelLimits kl{};
+  int rc = dispatch_precision(precision, [&](auto tag) {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    cudaError_t e = kernel_limits<M, V>(&kl);
+    return e == cudaSuccess ? PDHCG_OK : cuda_fail(e, "kernel_limits");
+  });
+  if (rc) return rc;
+  return std::min(kl.max_coresident_group, kl.max_coresident_setup);
+}
+
+int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
+  if (P->prm.group_blocks > 0) return std::min(P->prm.group_blocks, maxblk);
+  const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ : 0) + 2 * P->nnzA + P->n + P->m;
+  if (work < 150000) return 1;
+  return int(std::max<int64_t>(2, std::min<int64_t>(maxblk, work / 8192)));
+}
+
+int run_setup(pdhcg_problem* P) {
+  const int nblk = choose_group_blocks(P, P->max_blk);
+  PartitionSet* ps = nullptr;
+  if (nblk > 1) {
+    int rc = get_partition(P, nblk, &ps);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(P->bar, 0, kBarBytes, P->stream));
+  CK(cudaMemsetAsync(P->plan_i32, 0, sizeof(int32_t) * 16, P->stream));
+  return dispatch_precision(P->precision, [&](auto tag) {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    SetupArgs<M, V> a{};
+    a.n = P->n;
+    a.m = P->m;
+    a.has_q = P->has_q ? 1 : 0;
+    a.ruiz_iters = P->prm.ruiz_iters;
+    a.power_max_iter = P->prm.power_max_iter;
+    a.lanes_var = P->lanes_var;
+    a.lanes_con = P->lanes_con;
+    a.power_tol = P->prm.power_tol;
+    a.eta_override = P->prm.eta_override;
+    a.omega0_override = P->prm.omega0_override;
+    a.Qp = P->Qp_d;
+    a.Qc = P->Qc_d;
+    a.Ap = P->Ap_d;
+    a.Ac = P->Ac_d;
+    a.ATp = P->ATp_d;
+    a.ATc = P->ATc_d;
+    a.Qv_o = P->Qv_o;
+    a.Av_o = P->Av_o;
+    a.ATv_o = P->ATv_o;
+    a.c_o = P->c_o;
+    a.lv_o = P->lv_o;
+    a.uv_o = P->uv_o;
+    a.lc_o = P->lc_o;
+    a.uc_o = P->uc_o;
+    a.var_part = ps ? ps->v_even : nullptr;
+    a.con_part = ps ? ps->c_even : nullptr;
+    a.D = P->D;
+    a.E = P->E;
+    a.Dn = P->Dn;
+    a.En = P->En;
+    a.pv = P->pv;
+    a.pw = P->pw;
+    a.pt = P->pt;
+    a.Qs = static_cast<M*>(P->Qs);
+    a.As = static_cast<M*>(P->As);
+    a.ATs = static_cast<M*>(P->ATs);
+    a.c = static_cast<V*>(P->c);
+    a.lv = static_cast<V*>(P->lv);
+    a.uv = static_cast<V*>(P->uv);
+    a.lc = static_cast<V*>(P->lc);
+    a.uc = static_cast<V*>(P->uc);
+    a.qdiag = static_cast<V*>(P->qdiag);
+    a.st = P->st;
+    const uint64_t tmo = uint64_t(std::max(P->prm.device_timeout_ms, 1)) * 1000000ull;
+    cudaError_t e = launch_setup<M, V>(a, nblk, P->bar, P->part, P->plan_i32 + 5, tmo, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "setup launch");
+    CK(cudaMemcpyAsync(&P->setup_state, P->st, sizeof(SolverState), cudaMemcpyDeviceToHost, P->stream));
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, P->plan_i32 + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (err) {
+      set_error("setup: a bounded device wait gave up");
+      return PDHCG_E_DEVICE_TIMEOUT;
+    }
+    return PDHCG_OK;
+  });
+}
+
+int fill_sell(pdhcg_problem* P) {
+  auto go = [&](auto* tag) -> int {
+    using M = std::remove_pointer_t<decltype(tag)>;
+    cudaError_t e = launch_sell_fill<M>(P->vsell.nslices, P->v_perm, P->sATp, P->ATp_d,
+                                        static_cast<const M*>(P->ATs), static_cast<M*>(P->sATv), P->stream);
+    if (e == cudaSuccess && P->has_q)
+      e = launch_sell_fill<M>(P->vsell.nslices, P->v_perm, P->sQp, P->Qp_d, static_cast<const M*>(P->Qs),
+                              static_cast<M*>(P->sQv), P->stream);
+    if (e == cudaSuccess)
+      e = launch_sell_fill<M>(P->csell.nslices, P->c_perm, P->sAp, P->Ap_d, static_cast<const M*>(P->As),
+                              static_cast<M*>(P->sAv), P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    return e == cudaSuccess ? PDHCG_OK : cuda_fail(e, "sell fill");
+  };
+  if (P->precision == PDHCG_FP64) return go(static_cast<double*>(nullptr));
+  return go(static_cast<float*>(nullptr));
+}
+
+// One solve of one handle (device pointers for warm start / outputs).
+int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_result* res,
+              double* x_out_d, double* y_out_d) {
+  CK(cudaSetDevice(P->device));
+  const int nblk = choose_group_blocks(P, P->max_blk);
+  PartitionSet* ps = nullptr;
+  if (nblk > 1) {
+    int rc = get_partition(P, nblk, &ps);
+    if (rc) return rc;
+  }
+  SolverState S = initial_state(P);
+  CK(cudaMemcpyAsync(P->st, &S, sizeof(S), cudaMemcpyHostToDevice, P->stream));
+  int rc = dispatch_precision(P->precision, [&](auto tag) {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    Inst<M, V> I = make_inst<M, V>(P);
+    I.x_init = x0_d;
+    I.y_init = y0_d;
+    I.x_out = x_out_d;
+    I.y_out = y_out_d;
+    if (ps) set_partition(I, *ps, P);
+    CK(cudaMemcpyAsync(P->inst_d, &I, sizeof(I), cudaMemcpyHostToDevice, P->stream));
+    // plan_i32: [0] g_first [1] g_nblk [2] g_inst [3] pool_inst [4] pool_next [5] err
+    int32_t hp[16] = {0, nblk, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(P->plan_i32, hp, sizeof(hp), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemsetAsync(P->bar, 0, kBarBytes, P->stream));
+    int64_t zero = 0;
+    CK(cudaMemcpyAsync(P->part_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, P->stream));
+    LaunchPlan plan;
+    plan.err = P->plan_i32 + 5;
+    plan.timeout_ns = uint64_t(std::max(P->prm.device_timeout_ms, 1)) * 1000000ull;
+    int grid = 1;
+    if (nblk > 1) {
+      plan.ngroups = 1;
+      plan.group_blocks = nblk;
+      plan.g_first = P->plan_i32 + 0;
+      plan.g_nblk = P->plan_i32 + 1;
+      plan.g_inst = P->plan_i32 + 2;
+      plan.g_bar = P->bar;
+      plan.g_part = P->part;
+      plan.g_part_off = P->part_off;
+      grid = nblk;
+    } else {
+      plan.npool = 1;
+      plan.pool_inst = P->plan_i32 + 3;
+      plan.pool_next = P->plan_i32 + 4;
+    }
+    cudaError_t e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(P->inst_d), plan, grid, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+    return PDHCG_OK;
+  });
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(&S, P->st, sizeof(S), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  if (S.device_error) {
+    set_error("solve: a bounded device wait gave up");
+    return PDHCG_E_DEVICE_TIMEOUT;
+  }
+  if (res) fill_result(P, S, res);
+  P->last_state = S;
+  return PDHCG_OK;
+}
+
+}  // namespace pdhcg
+
+using namespace pdhcg;
+
+extern "C" {
+
+int pdhcg_default_params(pdhcg_params* p) {
+  if (!p) return PDHCG_E_INVALID;
+  std::memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(pdhcg_params);
+  p->precision = PDHCG_FP64;
+  p->eps_tol = 1e-6;
+  p->eps_inf = 1e-8;
+  p->time_limit_s = 3600.0;
+  p->max_iter = 1000000;
+  p->theta = 1.0;
+  p->kp = 0.99;
+  p->ki = 0.01;
+  p->kd = 0.0;
+  p->gamma_inner = 5e-4;
+  p->eps_inner_min = 1e-9;
+  p->eps_inner_first = 1e-2;
+  p->k_eval = 64;
+  p->inner = PDHCG_INNER_AUTO;
+  p->max_inner_iter = 1000;
+  p->ruiz_iters = 10;
+  p->restart_sufficient = 0.2;
+  p->restart_necessary = 0.8;
+  p->restart_artificial = 0.36;
+  p->power_max_iter = 1000;
+  p->lanes_override = 0;
+  p->power_tol = 1e-8;
+  p->eta_override = 0.0;
+  p->omega0_override = 0.0;
+  p->omega_clamp = 1e5;
+  p->group_blocks = 0;
+  p->device_timeout_ms = 8000;
+  return PDHCG_OK;
+}
+
+static int check_params(const pdhcg_params* p) {
+  if (!p || p->struct_size != sizeof(pdhcg_params)) {
+    set_error("params: struct_size mismatch (call pdhcg_default_params first)");
+    return PDHCG_E_INVALID;
+  }
+  if (p->precision < 0 || p->precision > 2 || p->k_eval < 1 || p->max_iter < 1 ||
+      !(p->eps_tol > 0) || !(p->eps_inf > 0) || p->max_inner_iter < 0 || p->ruiz_iters < 0 ||
+      p->inner < 0 || p->inner > 3 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
+      (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1))))) {
+    set_error("params: value out of range");
+    return PDHCG_E_INVALID;
+  }
+  return PDHCG_OK;
+}
+
+int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
+                 const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
+                 void* cuda_stream, pdhcg_t** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return PDHCG_E_INVALID;
+  }
+  *out = nullptr;
+  pdhcg_params prm;
+  if (params) {
+    int rc = check_params(params);
+    if (rc) return rc;
+    prm = *params;
+  } else {
+    pdhcg_default_params(&prm);
+  }
+  HostQP h;
+  int rc = build_host_qp(Q, A, c, lc, uc, lv, uv, &h);
+  if (rc) return rc;
+  int method = prm.inner;
+  if (method == PDHCG_INNER_AUTO) method = h.diag_q ? PDHCG_INNER_DIAG : (h.any_box ? PDHCG_INNER_BB : PDHCG_INNER_CG);
+  if (method == PDHCG_INNER_DIAG && !h.diag_q) {
+    set_error("inner = DIAG needs a diagonal Q");
+    return PDHCG_E_INVALID;
+  }
+  if (method == PDHCG_INNER_CG && h.any_box) {
+    set_error("inner = CG needs every variable free (no finite bound)");
+    return PDHCG_E_INVALID;
+  }
+  auto* P = new (std::nothrow) pdhcg_problem();
+  if (!P) return PDHCG_E_OOM;
+  P->prm = prm;
+  P->precision = prm.precision;
+  P->method = method;
+  P->n = h.n;
+  P->m = h.m;
+  P->nnzQ = int64_t(h.Qc.size());
+  P->nnzA = int64_t(h.Ac.size());
+  P->has_q = h.has_q;
+  P->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&P->device);
+  P->Qp = h.Qp;
+  P->Ap = h.Ap;
+  P->ATp = h.ATp;
+  {
+    const double avg_q = P->n ? double(P->nnzQ) / P->n : 0.0;
+    const double avg_at = P->n ? double(P->nnzA) / P->n : 0.0;
+    const double avg_a = P->m ? double(P->nnzA) / P->m : 0.0;
+    P->lanes_var = lanes_for(method == PDHCG_INNER_DIAG ? avg_at : std::max(avg_q, avg_at));
+    P->lanes_con = lanes_for(avg_a);
+    if (prm.lanes_override) P->lanes_var = P->lanes_con = prm.lanes_override;
+  }
+  {
+    const std::vector<int32_t>* vrp[2] = {&h.ATp, &h.Qp};
+    const std::vector<int32_t>* vci[2] = {&h.ATc, &h.Qc};
+    build_sell(h.n, h.has_q ? 2 : 1, vrp, vci, &P->vsell);
+    const std::vector<int32_t>* crp[2] = {&h.Ap, nullptr};
+    const std::vector<int32_t>* cci[2] = {&h.Ac, nullptr};
+    build_sell(h.m, 1, crp, cci, &P->csell);
+  }
+  int mb = max_group_blocks(P->precision);
+  if (mb < 0) {
+    delete P;
+    return mb;
+  }
+  P->max_blk = std::max(mb, 1);
+  Carver sizing;
+  carve(P, sizing);
+  P->arena_bytes = sizing.off + 256;
+  cudaError_t e = cudaMalloc(&P->arena, P->arena_bytes);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_fail(e, "cudaMalloc(arena)");
+  }
+  Carver real;
+  real.base = static_cast<char*>(P->arena);
+  carve(P, real);
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, P->stream);
+  };
+  const size_t n = size_t(h.n), m = size_t(h.m);
+  cudaError_t es[] = {
+      up(P->Qp_d, h.Qp.data(), sizeof(int32_t) * (n + 1)),
+      up(P->Qc_d, h.Qc.data(), sizeof(int32_t) * h.Qc.size()),
+      up(P->Ap_d, h.Ap.data(), sizeof(int32_t) * (m + 1)),
+      up(P->Ac_d, h.Ac.data(), sizeof(int32_t) * h.Ac.size()),
+      up(P->ATp_d, h.ATp.data(), sizeof(int32_t) * (n + 1)),
+      up(P->ATc_d, h.ATc.data(), sizeof(int32_t) * h.ATc.size()),
+      up(P->Qv_o, h.Qv.data(), sizeof(double) * h.Qv.size()),
+      up(P->Av_o, h.Av.data(), sizeof(double) * h.Av.size()),
+      up(P->ATv_o, h.ATv.data(), sizeof(double) * h.ATv.size()),
+      up(P->c_o, h.c.data(), sizeof(double) * n),
+      up(P->lv_o, h.lv.data(), sizeof(double) * n),
+      up(P->uv_o, h.uv.data(), sizeof(double) * n),
+      up(P->lc_o, h.lc.data(), sizeof(double) * m),
+      up(P->uc_o, h.uc.data(), sizeof(double) * m),
+      up(P->vtype, h.vtype.data(), n),
+      up(P->ctype, h.ctype.data(), m),
+      up(P->v_perm, P->vsell.perm.data(), sizeof(int32_t) * P->vsell.perm.size()),
+      up(P->v_longs, P->vsell.longs.data(), sizeof(int32_t) * P->vsell.longs.size()),
+      up(P->v_huges, P->vsell.huges.data(), sizeof(int32_t) * P->vsell.huges.size()),
+      up(P->c_perm, P->csell.perm.data(), sizeof(int32_t) * P->csell.perm.size()),
+      up(P->c_longs, P->csell.longs.data(), sizeof(int32_t) * P->csell.longs.size()),
+      up(P->c_huges, P->csell.huges.data(), sizeof(int32_t) * P->csell.huges.size()),
+      up(P->sATp, P->vsell.ptr[0].data(), sizeof(int64_t) * P->vsell.ptr[0].size()),
+      up(P->sQp, P->vsell.ptr[1].data(), sizeof(int64_t) * P->vsell.ptr[1].size()),
+      up(P->sAp, P->csell.ptr[0].data(), sizeof(int64_t) * P->csell.ptr[0].size()),
+      up(P->sATc, P->vsell.col[0].data(), sizeof(int32_t) * P->vsell.col[0].size()),
+      up(P->sQc, P->vsell.col[1].data(), sizeof(int32_t) * P->vsell.col[1].size()),
+      up(P->sAc, P->csell.col[0].data(), sizeof(int32_t) * P->csell.col[0].size()),
+  };
+  for (cudaError_t x : es)
+    if (x != cudaSuccess) {
+      int r = cuda_fail(x, "upload");
+      pdhcg_destroy(P);
+      return r;
+    }
+  {
+    SolverState S{};
+    S.method = method;
+    cudaError_t x = cudaMemcpyAsync(P->st, &S, sizeof(S), cudaMemcpyHostToDevice, P->stream);
+    if (x == cudaSuccess) x = cudaStreamSynchronize(P->stream);
+    if (x != cudaSuccess) {
+      int r = cuda_fail(x, "upload");
+      pdhcg_destroy(P);
+      return r;
+    }
+  }
+  rc = run_setup(P);
+  if (rc == PDHCG_OK) rc = fill_sell(P);
+  if (rc) {
+    pdhcg_destroy(P);
+    return rc;
+  }
+  // the integer SELL columns are on the device now; keep only what partitioning needs
+  for (int k = 0; k < 2; ++k) {
+    std::vector<int32_t>().swap(P->vsell.col[k]);
+    std::vector<int32_t>().swap(P->csell.col[k]);
+  }
+  *out = P;
+  return PDHCG_OK;
+}
+
+int pdhcg_solve(pdhcg_t* P, const double* x0, const double* y0, pdhcg_result* res, double* x_out,
+                double* y_out) {
+  if (!P) {
+    set_error("NULL handle");
+    return PDHCG_E_INVALID;
+  }
+  CK(cudaSetDevice(P->device));
+  const size_t n = size_t(P->n), m = size_t(P->m);
+  if (x0) CK(cudaMemcpyAsync(P->x_init_stage, x0, sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
+  if (y0 && m) CK(cudaMemcpyAsync(P->y_init_stage, y0, sizeof(double) * m, cudaMemcpyHostToDevice, P->stream));
+  int rc = solve_one(P, x0 ? P->x_init_stage : nullptr, (y0 && m) ? P->y_init_stage : nullptr, res,
+                     P->x_stage, P->y_stage);
+  if (rc) return rc;
+  if (x_out) CK(cudaMemcpyAsync(x_out, P->x_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream));
+  if (y_out && m) CK(cudaMemcpyAsync(y_out, P->y_stage, sizeof(double) * m, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return PDHCG_OK;
+}
+
+int pdhcg_solve_dev(pdhcg_t* P, const double* x0_dev, const double* y0_dev, pdhcg_result* res,
+                    double* x_out_dev, double* y_out_dev) {
+  if (!P) {
+    set_error("NULL handle");
+    return PDHCG_E_INVALID;
+  }
+  return solve_one(P, x0_dev, y0_dev, res, x_out_dev, y_out_dev);
+}
+
+int pdhcg_get_eta(const pdhcg_t* P, double* eta, double* norm_A) {
+  if (!P) return PDHCG_E_INVALID;
+  if (eta) *eta = P->setup_state.eta;
+  if (norm_A) *norm_A = P->setup_state.norm_A;
+  return PDHCG_OK;
+}
+
+int pdhcg_get_scaling(const pdhcg_t* P, double* D, double* E) {
+  if (!P) return PDHCG_E_INVALID;
+  CK(cudaSetDevice(P->device));
+  if (D) CK(cudaMemcpy(D, P->D, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost));
+  if (E && P->m) CK(cudaMemcpy(E, P->E, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToHost));
+  return PDHCG_OK;
+}
+
+int pdhcg_get_phase_times(const pdhcg_t* P, double* seconds8) {
+  if (!P || !seconds8) return PDHCG_E_INVALID;
+  for (int k = 0; k < 8; ++k) seconds8[k] = P->last_state.tm[k] * 1e-9;
+  return PDHCG_OK;
+}
+
+int pdhcg_get_info(const pdhcg_t* P, int32_t* n, int32_t* m, size_t* bytes) {
+  if (!P) return PDHCG_E_INVALID;
+  if (n) *n = P->n;
+  if (m) *m = P->m;
+  if (bytes) *bytes = P->arena_bytes;
+  return PDHCG_OK;
+}
+
+void pdhcg_destroy(pdhcg_t* P) {
+  if (!P) return;
+  cudaSetDevice(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (auto& kv : P->partitions) cudaFree(kv.second.d_buf);
+  if (P->arena) cudaFree(P->arena);
+  delete P;
+}
+
+const char* pdhcg_strerror(int code) {
+  switch (code) {
+    case PDHCG_OK: return "ok";
+    case PDHCG_PENDING: return "pending";
+    case PDHCG_E_INVALID: return "invalid argument or problem data";
+    case PDHCG_E_OOM: return "out of device memory / over budget";
+    case PDHCG_E_CUDA: return "CUDA error";
+    case PDHCG_E_BUSY: return "busy";
+    case PDHCG_E_NOT_FOUND: return "unknown ticket";
+    case PDHCG_E_DEVICE_TIMEOUT: return "bounded device wait gave up";
+    default: return "unknown error";
+  }
+}
+
+const char* pdhcg_last_error(void) { return last_error_cstr(); }
+
+}  // extern "C"
+
+// ---- batched solves: one persistent launch, CTAs pull instances from a queue ----
+namespace pdhcg {
+
+struct BatchScratch {
+  int device = -1;
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+static std::mutex g_batch_mu;
+static std::vector<BatchScratch> g_batch_scratch;
+
+static int batch_buffer(int device, size_t bytes, void** out) {
+  for (auto& b : g_batch_scratch)
+    if (b.device == device) {
+      if (b.bytes < bytes) {
+        cudaFree(b.buf);
+        b.buf = nullptr;
+        b.bytes = 0;
+        CK(cudaMalloc(&b.buf, bytes));
+        b.bytes = bytes;
+      }
+      *out = b.buf;
+      return PDHCG_OK;
+    }
+  BatchScratch b;
+  b.device = device;
+  CK(cudaMalloc(&b.buf, bytes));
+  b.bytes = bytes;
+  g_batch_scratch.push_back(b);
+  *out = b.buf;
+  return PDHCG_OK;
+}
+
+int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double* const* x_out,
+                     double* const* y_out, int64_t iter_budget) {
+  if (count < 0 || (count > 0 && !probs)) {
+    set_error("solve_batch: bad arguments");
+    return PDHCG_E_INVALID;
+  }
+  if (count == 0) return PDHCG_OK;
+  const pdhcg_problem* P0 = probs[0];
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i] || probs[i]->precision != P0->precision || probs[i]->device != P0->device ||
+        probs[i]->stream != P0->stream) {
+      set_error("solve_batch: handles must be non-NULL and share precision, device and stream");
+      return PDHCG_E_INVALID;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  CK(cudaSetDevice(P0->device));
+  cudaStream_t s = P0->stream;
+  size_t sum_n = 0, sum_m = 0;
+  std::vector<size_t> xoff(static_cast<size_t>(count)), yoff(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i) {
+    xoff[i] = sum_n;
+    yoff[i] = sum_m;
+    sum_n += size_t(probs[i]->n);
+    sum_m += size_t(probs[i]->m);
+  }
+  const size_t inst_sz = sizeof(Inst<double, double>);
+  Carver sizing;
+  sizing.take<SolverState>(size_t(count));
+  sizing.take_bytes(size_t(count), inst_sz);
+  sizing.take<int32_t>(size_t(count) + 8);
+  sizing.take<double>(sum_n);
+  sizing.take<double>(sum_m);
+  void* buf = nullptr;
+  int rc = batch_buffer(P0->device, sizing.off + 256, &buf);
+  if (rc) return rc;
+  Carver cv;
+  cv.base = static_cast<char*>(buf);
+  SolverState* d_st = cv.take<SolverState>(size_t(count));
+  void* d_inst = cv.take_bytes(size_t(count), inst_sz);
+  int32_t* d_i32 = cv.take<int32_t>(size_t(count) + 8);
+  double* d_x = cv.take<double>(sum_n);
+  double* d_y = cv.take<double>(sum_m);
+
+  std::vector<SolverState> hs(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i) hs[i] = initial_state(probs[i]);
+  // longest-processing-time-first order for the work queue
+  std::vector<int32_t> order(size_t(count) + 8, 0);
+  std::vector<int64_t> work(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i)
+    work[i] = (probs[i]->method != PDHCG_INNER_DIAG ? 4 * probs[i]->nnzQ : 0) + 2 * probs[i]->nnzA +
+              probs[i]->n + probs[i]->m;
+  std::vector<int32_t> idx(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
+  for (int i = 0; i < count; ++i) order[i] = idx[i];
+  order[size_t(count)] = 0;      // pool cursor
+  order[size_t(count) + 1] = 0;  // error flag
+
+  rc = dispatch_precision(P0->precision, [&](auto tag) {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    std::vector<Inst<M, V>> hi(static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) {
+      hi[i] = make_inst<M, V>(probs[i]);
+      hi[i].st = d_st + i;
+      hi[i].x_out = d_x + xoff[i];
+      hi[i].y_out = d_y + yoff[i];
+    }
+    CK(cudaMemcpyAsync(d_st, hs.data(), sizeof(SolverState) * size_t(count), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_inst, hi.data(), sizeof(Inst<M, V>) * size_t(count), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_i32, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, s));
+    KernelLimits kl{};
+    cudaError_t e = kernel_limits<M, V>(&kl);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel_limits");
+    LaunchPlan plan;
+    plan.npool = count;
+    plan.pool_inst = d_i32;
+    plan.pool_next = d_i32 + count;
+    plan.err = d_i32 + count + 1;
+    plan.iter_budget = iter_budget;
+    plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
+    const int grid = std::max(1, std::min(count, kl.max_coresident_group));
+    e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    CK(cudaMemcpyAsync(hs.data(), d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
+    return PDHCG_OK;
+  });
+  if (rc) return rc;
+  std::vector<double> hx, hy;
+  const bool want_x = x_out != nullptr, want_y = y_out != nullptr;
+  if (want_x) {
+    hx.resize(sum_n);
+    CK(cudaMemcpyAsync(hx.data(), d_x, sizeof(double) * sum_n, cudaMemcpyDeviceToHost, s));
+  }
+  if (want_y && sum_m) {
+    hy.resize(sum_m);
+    CK(cudaMemcpyAsync(hy.data(), d_y, sizeof(double) * sum_m, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  bool dev_err = false;
+  for (int i = 0; i < count; ++i) {
+    if (hs[i].device_error) dev_err = true;
+    if (res) fill_result(probs[i], hs[i], res + i);
+    if (want_x && x_out[i]) std::memcpy(x_out[i], hx.data() + xoff[i], sizeof(double) * size_t(probs[i]->n));
+    if (want_y && y_out[i] && probs[i]->m)
+      std::memcpy(y_out[i], hy.data() + yoff[i], sizeof(double) * size_t(probs[i]->m));
+  }
+  if (dev_err) {
+    set_error("solve_batch: a bounded device wait gave up");
+    return PDHCG_E_DEVICE_TIMEOUT;
+  }
+  return PDHCG_OK;
+}
+
+}  // namespace pdhcg
+
+extern "C" int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result* res,
+                                 double* const* x_out, double* const* y_out) {
+  return pdhcg::solve_batch_impl(probs, count, res, x_out, y_out, 0);
+}

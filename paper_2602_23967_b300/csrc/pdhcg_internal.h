@@ -1,0 +1,147 @@
+// pdhcg_internal.h — layouts shared by the host layer and the CUDA kernels of libpdhcg.
+#pragma once
+#include <cstdint>
+
+#include "pdhcg.h"
+
+namespace pdhcg {
+
+// Reduction slots available per group reduction (the KKT / infeasibility check
+// uses the most).
+constexpr int kSlots = 24;
+// Bytes of one group's barrier block (34 lines of 128 bytes).
+constexpr size_t kBarBytes = 34 * 128;
+
+// Bound-type code of a row or variable: bit 0 = lower bound finite,
+// bit 1 = upper bound finite.
+enum : int8_t { kFree = 0, kLowOnly = 1, kUpOnly = 2, kBoxed = 3 };
+
+// Parameters the device loop reads (host fills from pdhcg_params).
+struct DevParams {
+  double eps_tol, eps_inf, time_limit_ns;
+  int64_t max_iter;
+  double theta, kp, ki, kd;
+  double gamma_inner, eps_inner_min, eps_inner_first;
+  double restart_sufficient, restart_necessary, restart_artificial, omega_clamp;
+  int32_t k_eval, max_inner_iter;
+};
+
+// Scalar state of one solve, FP64, kept in device memory between launches so a
+// solve can be paused at a check boundary and resumed (serving loop).
+struct SolverState {
+  int64_t K;            // PDHG steps done
+  int64_t k;            // Halpern index since the last restart
+  int64_t inner_total;  // CG / BB steps
+  int64_t restarts;
+  double omega, log_omega, log_omega0, e_sum, e_prev;
+  double tau, sigma, eta, norm_A;
+  double eps_in, mv, fpr_anchor, fpr_last;
+  double r_primal, r_dual, r_gap, pobj, dobj;
+  double t_start_ns, t_end_ns;
+  double gersh, omega0;
+  double bscale, cinf;  // max(||lc||_inf, ||uc||_inf) over finite entries; ||c||_inf
+  // device-timer nanoseconds seen by thread 0 of the group's first CTA, per
+  // category: 0 Phase I, 1 inner row phases, 2 inner elementwise, 3 Phase II,
+  // 4 checks, 5 group barriers/reductions, 6 restarts and output, 7 unused
+  double tm[8];
+  int32_t status;       // PDHCG_* status, 0 while running
+  int32_t cur;          // which of the two x / y buffers holds the current iterate
+  int32_t started;      // 0 until the first launch initialised the iterates
+  int32_t method;       // PDHCG_INNER_DIAG / CG / BB
+  int32_t power_iters;
+  int32_t device_error; // a bounded device wait gave up
+};
+
+template <class T>
+struct Csr {
+  int32_t nrows = 0;
+  int32_t nnz = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const T* val = nullptr;
+};
+
+// SELL-C-sigma slices (C = 32 rows, one per lane) of one matrix of a row space.
+// Element j of slot (slice s, lane l) sits at ptr[s] + 32*j + l; padding has
+// value 0.  Rows listed as long / huge are not in the slices.
+template <class T>
+struct Sell {
+  const int64_t* ptr = nullptr;  // nslices + 1
+  const int32_t* col = nullptr;
+  const T* val = nullptr;
+};
+
+// Row space (the n variable rows, or the m constraint rows) in SELL form.
+struct SpaceLayout {
+  int32_t nslices = 0, nlong = 0, nhuge = 0;
+  const int32_t* perm = nullptr;   // nslices*32 row ids (-1 = padding slot)
+  const int32_t* longs = nullptr;  // rows summed by one warp each (CSR)
+  const int32_t* huges = nullptr;  // rows summed by a whole CTA each (CSR)
+  // per-CTA ranges of slices / long rows / huge rows (part_blocks + 1 each; null = all)
+  const int32_t* slice_part = nullptr;
+  const int32_t* long_part = nullptr;
+  const int32_t* huge_part = nullptr;
+};
+
+// Everything a kernel needs to know about one instance.  MatT: matrix value
+// type; VecT: iterate / vector type.
+template <class MatT, class VecT>
+struct Inst {
+  int32_t n = 0, m = 0;
+  int32_t has_q = 0;
+  int32_t lanes_var = 4, lanes_con = 4;  // CSR lanes per row in the n-space / m-space phases
+  Csr<MatT> Q, A, AT;                    // scaled matrices; AT is the explicit transpose of A
+  Sell<MatT> Qs, As, ATs;                // the same values in SELL form
+  SpaceLayout vsp, csp;                  // variable-row and constraint-row spaces
+  // Row partitions for multi-CTA groups: var_part / con_part hold part_blocks+1
+  // row offsets (nnz-balanced); long rows sit alone in their range.
+  const int32_t* var_part = nullptr;
+  const int32_t* con_part = nullptr;
+  int32_t part_blocks = 0;
+  int32_t long_row = 1 << 30;            // rows at least this long use the whole CTA
+  // scaled problem data
+  const VecT *c = nullptr, *lv = nullptr, *uv = nullptr, *lc = nullptr, *uc = nullptr,
+             *qdiag = nullptr;
+  const int8_t *vtype = nullptr, *ctype = nullptr;
+  // original-space data for the KKT residuals (double)
+  const double *D = nullptr, *E = nullptr, *c_o = nullptr, *lv_o = nullptr, *uv_o = nullptr,
+               *lc_o = nullptr, *uc_o = nullptr;
+  double bscale = 0.0;  // max(||lc||_inf, ||uc||_inf) over finite entries
+  double cinf = 0.0;    // ||c||_inf
+  // iterate / work vectors
+  VecT *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;
+  VecT *xT = nullptr, *yT = nullptr, *xa = nullptr, *ya = nullptr;
+  VecT *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+  VecT *bv = nullptr, *grad = nullptr, *gprev = nullptr, *xprev = nullptr;
+  VecT* xbar = nullptr;  // 2 x+ - x, written once x+ is known (one gather per nonzero in Phase II)
+  // warm start and outputs (device, double; may be null)
+  const double *x_init = nullptr, *y_init = nullptr;
+  double *x_out = nullptr, *y_out = nullptr;
+  SolverState* st = nullptr;
+  DevParams prm;
+};
+
+// How one launch of the solve kernel maps CTAs to instances.
+struct LaunchPlan {
+  // Multi-CTA groups occupy CTAs [0, group_blocks); group g owns
+  // [g_first[g], g_first[g] + g_nblk[g]) and solves instance g_inst[g].
+  int32_t ngroups = 0;
+  int32_t group_blocks = 0;
+  const int32_t* g_first = nullptr;
+  const int32_t* g_nblk = nullptr;
+  const int32_t* g_inst = nullptr;
+  unsigned long long* g_bar = nullptr;  // barrier blocks, kBarBytes per group (zeroed before launch)
+  double* g_part = nullptr;             // partial sums: group g at g_part_off[g], 2*kSlots*nblk
+  const int64_t* g_part_off = nullptr;
+  // Remaining CTAs take single-CTA instances from a queue.
+  int32_t npool = 0;
+  const int32_t* pool_inst = nullptr;
+  int32_t* pool_next = nullptr;         // atomic cursor (zeroed before launch)
+  // Slice limits for the serving loop: a solve pauses at the first check
+  // boundary after it has done iter_budget steps in this launch (0 = none).
+  int64_t iter_budget = 0;
+  uint64_t timeout_ns = 8000000000ull;  // bound on any device wait
+  int32_t* err = nullptr;               // set to 1 when a bounded wait gave up
+};
+
+}  // namespace pdhcg

@@ -1,0 +1,234 @@
+// setup_kernel.cuh — device setup of one instance (off the timed loop).
+//
+//  1. Ruiz equilibration of K = [Q A^T; A 0] in the infinity norm (reading of the
+//     paper's unstated "system scaling"): each pass divides every column of the
+//     currently scaled K by the square root of its largest magnitude.  The
+//     scaled entries are (Q_ij D_i) D_j and (A_ij E_i) D_j.
+//  2. Scaled data in the iteration's types: Q, A, A^T values, c = D c,
+//     lv = lv / D, uv = uv / D, lc = E lc, uc = E uc, diag(Q), the Gershgorin
+//     bound of Q (BB step range), ||c||, ||finite(lc, uc)|| (initial primal weight).
+//  3. ||A||_2 of the scaled A by power iteration on A^T A in FP64 (Sec. 3.2 fixes
+//     eta = 0.998/||A|| but not how ||A|| is obtained).
+#pragma once
+#include "device_common.cuh"
+
+namespace pdhcg {
+
+template <class MatT, class VecT>
+struct SetupArgs {
+  int32_t n, m, has_q, ruiz_iters, power_max_iter, lanes_var, lanes_con;
+  double power_tol, eta_override, omega0_override;
+  const int32_t *Qp, *Qc, *Ap, *Ac, *ATp, *ATc;
+  const double *Qv_o, *Av_o, *ATv_o;  // original values
+  const double *c_o, *lv_o, *uv_o, *lc_o, *uc_o;
+  const int32_t *var_part, *con_part;
+  double *D, *E, *Dn, *En;            // scaling work (D, E hold the result)
+  double *pv, *pw, *pt;               // power-iteration work (n, n, m)
+  MatT *Qs, *As, *ATs;                // scaled values (outputs)
+  VecT *c, *lv, *uv, *lc, *uc, *qdiag;
+  SolverState* st;
+};
+
+// max over a CSR row of f(k), by a sub-warp of L lanes; result in every lane.
+template <class F>
+__device__ __forceinline__ double sub_row_max(const int32_t* rp, int row, bool valid, int sl, int L,
+                                              F f) {
+  double acc = 0.0;
+  if (valid)
+    for (int k = rp[row] + sl; k < rp[row + 1]; k += L) acc = fmax(acc, f(k));
+  for (int off = L >> 1; off > 0; off >>= 1) acc = fmax(acc, __shfl_xor_sync(kFull, acc, off));
+  return acc;
+}
+template <class F>
+__device__ __forceinline__ double sub_row_sum(const int32_t* rp, int row, bool valid, int sl, int L,
+                                              F f) {
+  double acc = 0.0;
+  if (valid)
+    for (int k = rp[row] + sl; k < rp[row + 1]; k += L) acc += f(k);
+  for (int off = L >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+  return acc;
+}
+
+template <int BS, class F>
+__device__ __forceinline__ void rows_loop(int lo, int hi, int L, F f) {
+  const int sub = threadIdx.x / L, sl = threadIdx.x & (L - 1), nsub = BS / L;
+  for (int base = lo; base < hi; base += nsub) f(base + sub, base + sub < hi, sl);
+}
+
+template <int BS, class MatT, class VecT>
+__device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
+  int vlo, vhi, clo, chi;
+  g.range(a.var_part, a.n, vlo, vhi);
+  g.range(a.con_part, a.m, clo, chi);
+  const int Lv = a.lanes_var, Lc = a.lanes_con;
+  double* D = a.D;
+  double* E = a.E;
+  double* Dn = a.Dn;
+  double* En = a.En;
+  for_elems<BS>(vlo, vhi, [&](int j) { D[j] = 1.0; });
+  for_elems<BS>(clo, chi, [&](int i) { E[i] = 1.0; });
+  if (!group_sync<BS>(g)) return;
+
+  // ---- 1. Ruiz passes ----
+  for (int pass = 0; pass < a.ruiz_iters; ++pass) {
+    rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
+      double cq = 0.0;
+      if (a.has_q)
+        cq = sub_row_max(a.Qp, j, valid, sl, Lv, [&](int k) { return fabs((a.Qv_o[k] * D[a.Qc[k]]) * D[j]); });
+      double ca = sub_row_max(a.ATp, j, valid, sl, Lv,
+                              [&](int k) { return fabs((a.ATv_o[k] * E[a.ATc[k]]) * D[j]); });
+      if (valid && sl == 0) {
+        const double cn = fmax(cq, ca);
+        Dn[j] = D[j] * (cn > 0.0 ? 1.0 / sqrt(cn) : 1.0);
+      }
+    });
+    rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
+      double rn = sub_row_max(a.Ap, i, valid, sl, Lc, [&](int k) { return fabs((a.Av_o[k] * E[i]) * D[a.Ac[k]]); });
+      if (valid && sl == 0) En[i] = E[i] * (rn > 0.0 ? 1.0 / sqrt(rn) : 1.0);
+    });
+    if (!group_sync<BS>(g)) return;
+    double* t = D; D = Dn; Dn = t;
+    t = E; E = En; En = t;
+  }
+  // the result must end in a.D / a.E
+  if (D != a.D) {
+    for_elems<BS>(vlo, vhi, [&](int j) { a.D[j] = D[j]; });
+    for_elems<BS>(clo, chi, [&](int i) { a.E[i] = E[i]; });
+    if (!group_sync<BS>(g)) return;
+    D = a.D;
+    E = a.E;
+  }
+
+  // ---- 2. scaled data ----
+  double red[5];  // ||c~||^2, ||b~||^2, gersh (max), bscale (max), cinf (max)
+  {
+    double cn2 = 0.0, bn2 = 0.0, gmax = 0.0, bsc = 0.0, cinf = 0.0;
+    rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
+      double qd = 0.0, gs = 0.0;
+      if (a.has_q) {
+        if (valid)
+          for (int k = a.Qp[j] + sl; k < a.Qp[j + 1]; k += Lv) {
+            const double v = (a.Qv_o[k] * D[j]) * D[a.Qc[k]];
+            a.Qs[k] = MatT(v);
+            if (a.Qc[k] == j) qd += v;
+            gs += fabs(v);
+          }
+        for (int off = Lv >> 1; off > 0; off >>= 1) {
+          qd += __shfl_xor_sync(kFull, qd, off);
+          gs += __shfl_xor_sync(kFull, gs, off);
+        }
+      }
+      if (valid)
+        for (int k = a.ATp[j] + sl; k < a.ATp[j + 1]; k += Lv)
+          a.ATs[k] = MatT((a.ATv_o[k] * E[a.ATc[k]]) * D[j]);
+      if (valid && sl == 0) {
+        const double cs = a.c_o[j] * D[j];
+        a.c[j] = VecT(cs);
+        a.lv[j] = VecT(a.lv_o[j] / D[j]);
+        a.uv[j] = VecT(a.uv_o[j] / D[j]);
+        a.qdiag[j] = VecT(qd);
+        cn2 += cs * cs;
+        gmax = fmax(gmax, gs);
+        cinf = fmax(cinf, fabs(a.c_o[j]));
+      }
+    });
+    rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
+      if (valid)
+        for (int k = a.Ap[i] + sl; k < a.Ap[i + 1]; k += Lc) a.As[k] = MatT((a.Av_o[k] * E[i]) * D[a.Ac[k]]);
+      if (valid && sl == 0) {
+        const double l = a.lc_o[i] * E[i], u = a.uc_o[i] * E[i];
+        a.lc[i] = VecT(l);
+        a.uc[i] = VecT(u);
+        if (isfinite(l)) bn2 += l * l;
+        if (isfinite(u)) bn2 += u * u;
+        if (isfinite(a.lc_o[i])) bsc = fmax(bsc, fabs(a.lc_o[i]));
+        if (isfinite(a.uc_o[i])) bsc = fmax(bsc, fabs(a.uc_o[i]));
+      }
+    });
+    red[0] = cn2;
+    red[1] = bn2;
+    red[2] = gmax;
+    red[3] = bsc;
+    red[4] = cinf;
+    if (!group_reduce<BS, 5>(g, red, (1u << 2) | (1u << 3) | (1u << 4))) return;
+  }
+
+  // ---- 3. ||A||_2 by power iteration on A^T A (FP64, scaled values on the fly) ----
+  double lam = 0.0, lam_prev = 0.0;
+  int it = 0;
+  if (a.m > 0) {
+    const double v0 = 1.0 / sqrt(double(a.n));
+    for (it = 1; it <= a.power_max_iter; ++it) {
+      const bool first = (it == 1);
+      const double lp = lam;
+      rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
+        double t = sub_row_sum(a.Ap, i, valid, sl, Lc, [&](int k) {
+          const int j = a.Ac[k];
+          const double vj = first ? v0 : a.pw[j] / lp;
+          return ((a.Av_o[k] * E[i]) * D[j]) * vj;
+        });
+        if (valid && sl == 0) a.pt[i] = t;
+      });
+      if (!group_sync<BS>(g)) return;
+      double w2[1] = {0.0};
+      rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
+        double w = sub_row_sum(a.ATp, j, valid, sl, Lv, [&](int k) {
+          const int i = a.ATc[k];
+          return ((a.ATv_o[k] * E[i]) * D[j]) * a.pt[i];
+        });
+        if (valid && sl == 0) {
+          a.pw[j] = w;
+          w2[0] += w * w;
+        }
+      });
+      if (!group_reduce<BS, 1>(g, w2, 0u)) return;
+      lam = sqrt(w2[0]);
+      if (!(lam > 0.0)) {
+        lam = 0.0;
+        break;
+      }
+      if (it > 1 && fabs(lam - lam_prev) <= a.power_tol * lam) break;
+      lam_prev = lam;
+    }
+    if (it > a.power_max_iter) it = a.power_max_iter;
+  }
+  if (g.rank == 0 && threadIdx.x == 0) {
+    SolverState& S = *a.st;
+    const double normA = a.m > 0 ? sqrt(lam) : 0.0;
+    S.norm_A = normA;
+    S.eta = normA > 0.0 ? 0.998 / normA : 1.0;
+    if (a.eta_override > 0.0) S.eta = a.eta_override;
+    S.power_iters = it;
+    S.gersh = red[2];
+    const double cn = sqrt(red[0]), bn = sqrt(red[1]);
+    S.omega0 = (cn > 1e-10 && bn > 1e-10) ? cn / bn : 1.0;
+    if (a.omega0_override > 0.0) S.omega0 = a.omega0_override;
+    S.bscale = red[3];
+    S.cinf = red[4];
+  }
+}
+
+template <int BS, class MatT, class VecT>
+__global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsigned long long* bar,
+                                                   double* part, int32_t* err, uint64_t timeout_ns) {
+  __shared__ double sm_warp[2 * (BS / 32) * kSlots];
+  __shared__ double sm_tot[2 * kSlots];
+  __shared__ int sm_flag;
+  Group<BS> g;
+  g.nblk = gridDim.x;
+  g.rank = blockIdx.x;
+  g.bar32 = reinterpret_cast<unsigned*>(bar);
+  g.epoch = 0;
+  g.part = part;
+  g.sm_warp = sm_warp;
+  g.sm_tot = sm_tot;
+  g.sm_flag = &sm_flag;
+  g.err = err;
+  g.timeout_ns = timeout_ns;
+  g.failed = false;
+  if (threadIdx.x == 0) sm_flag = 0;
+  __syncthreads();
+  setup_instance<BS>(g, a);
+}
+
+}  // namespace pdhcg

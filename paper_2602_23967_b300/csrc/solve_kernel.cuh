@@ -1,0 +1,619 @@
+// solve_kernel.cuh — the PDHCG-II outer loop and inner solvers as one persistent kernel.
+//
+// One call of solve_instance() runs the iteration of one instance on a group of
+// CTAs (see device_common.cuh) until it stops (KKT tolerance, infeasibility,
+// limits) or its iteration slice is used up.  Per PDHG step:
+//
+//   Phase I   (n-space rows)  g = A^T y, b = x/tau - c - g            (Eq. primal_update)
+//                             DIAG: x+ = clamp(b / (diag Q + 1/tau))   (Sec. 2.2, closed form)
+//                             CG:   r = b - H x       BB: grad = H x - b, H = Q + I/tau
+//   inner loop                CG (2 phases/step) or projected BB (2 phases/step)  (Sec. 2.2)
+//                             to the adaptive tolerance eps_k                      (Sec. 3.3)
+//   Phase II  (m-space rows)  A xbar with xbar = 2x+ - x gathered on the fly,
+//                             y+ = sigma (v - proj_S(v)), v = y/sigma + A xbar    (Eq. dual_update)
+//                             reflected Halpern on y (and x)                       (Sec. 3.1)
+//   every k_eval steps        KKT residuals on the original data (Sec. 4.2), primal and dual
+//                             infeasibility tests (Sec. 5.1, 5.2), restart test and PID
+//                             update of the primal weight (Sec. 3.2, Eq. pid)
+//
+// Vector updates run in VecT; inner products use DotAcc (FP64, or compensated
+// FP32 that is exact to about 2^-48 relative) and are combined across the
+// group in FP64; all scalar decisions are FP64 and identical in every CTA.
+#pragma once
+#include "device_common.cuh"
+
+namespace pdhcg {
+
+// Thread-local inner-product accumulator.
+template <class T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+// FP32 values accumulated as an unevaluated sum hi + lo with error-free
+// transformations (TwoProduct by FMA, Knuth's TwoSum): the result is the
+// exact dot product of the FP32 inputs up to about 2^-48 relative, at FP32
+// throughput (the FP64 pipe of the B300 is too narrow for per-element use).
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float s = hi + p;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e + pe;
+  }
+  __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+};
+
+// PID update of log(omega) at the end of a restarted round (Eq. pid).  Skipped
+// when either movement is below 1e-10; omega kept within omega0 * [1/c, c].
+__device__ __forceinline__ void pid_update(SolverState& S, const DevParams& P, double dx,
+                                           double dy) {
+  if (!(dx > 1e-10) || !(dy > 1e-10)) return;
+  double omega = exp(S.log_omega);
+  double e = log(omega * dx / dy);
+  S.e_sum += e;
+  double lw = S.log_omega - (P.kp * e + P.ki * S.e_sum + P.kd * (e - S.e_prev));
+  S.e_prev = e;
+  double lim = log(P.omega_clamp);
+  lw = fmin(fmax(lw, S.log_omega0 - lim), S.log_omega0 + lim);
+  S.log_omega = lw;
+}
+
+// Accumulates device-timer intervals per category (thread 0 of the group's first CTA).
+struct PhaseClock {
+  bool on;
+  uint64_t last;
+  __device__ __forceinline__ void mark(double* tm, int cat) {
+    if (on) {
+      const uint64_t t = globaltimer_ns();
+      tm[cat] += double(t - last);
+      last = t;
+    }
+  }
+};
+
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I,
+                                            const LaunchPlan& plan, const RowCtx& red) {
+  using CT = VecT;   // arithmetic type of vector updates
+  using Acc = VecT;  // SpMV accumulation type in the hot phases
+  SolverState S = *I.st;
+  if (S.status != 0) return;
+  const DevParams P = I.prm;
+  const int method = S.method;
+  int vlo, vhi, clo, chi;
+  g.range(I.var_part, I.n, vlo, vhi);
+  g.range(I.con_part, I.m, clo, chi);
+  const bool use_q = I.has_q != 0;
+  // local copies of the read-only data pointers
+  const VecT* __restrict__ c_s = I.c;
+  const VecT* __restrict__ lv = I.lv;
+  const VecT* __restrict__ uv = I.uv;
+  const VecT* __restrict__ lc = I.lc;
+  const VecT* __restrict__ uc = I.uc;
+  const VecT* __restrict__ qdiag = I.qdiag;
+  const int8_t* __restrict__ vtype = I.vtype;
+  const int8_t* __restrict__ ctype = I.ctype;
+  const int prank = g.nblk > 1 ? g.rank : -1;
+  VecT* xa = I.xa;
+  VecT* ya = I.ya;
+  VecT* rv = I.r;
+  VecT* qv = I.q;
+  VecT* grad = I.grad;
+  VecT* gprev = I.gprev;
+  VecT* xprev = I.xprev;
+  VecT* bvv = I.bv;
+  VecT* xT = I.xT;
+  VecT* yT = I.yT;
+  VecT* xbar = I.xbar;
+  bool ok = true;
+
+  // ---- first launch: initial point (x0 = proj_X(x_init or 0), y0 = proj_Y(y_init or 0)) ----
+  if (!S.started) {
+    for_elems<BS>(vlo, vhi, [&](int j) {
+      double x0 = I.x_init ? I.x_init[j] / I.D[j] : 0.0;
+      VecT xv = VecT(clampv(x0, double(lv[j]), double(uv[j])));
+      I.xb0[j] = xv;
+      xa[j] = xv;
+    });
+    for_elems<BS>(clo, chi, [&](int i) {
+      double y0 = I.y_init ? proj_Y(I.y_init[i] / I.E[i], ctype[i]) : 0.0;
+      I.yb0[i] = VecT(y0);
+      ya[i] = VecT(y0);
+    });
+    double t[1] = {double(globaltimer_ns())};
+    ok = group_reduce<BS, 1>(g, t, 1u);
+    S.t_start_ns = t[0];
+    S.started = 1;
+    S.cur = 0;
+  }
+  const int64_t K_first = S.K;
+  const auto none = nosrc<MatT>();
+  PhaseClock clk{threadIdx.x == 0 && g.rank == 0, globaltimer_ns()};
+
+  while (ok) {
+    VecT* x = S.cur ? I.xb1 : I.xb0;
+    VecT* xn = S.cur ? I.xb0 : I.xb1;
+    VecT* y = S.cur ? I.yb1 : I.yb0;
+    VecT* yn = S.cur ? I.yb0 : I.yb1;
+    const double inv_tau = 1.0 / S.tau, inv_sigma = 1.0 / S.sigma;
+    const double wk = double(S.k + 1) / double(S.k + 2), ak = 1.0 / double(S.k + 2);
+    const CT itau = CT(inv_tau), isig = CT(inv_sigma), sig = CT(S.sigma);
+    const CT wkc = CT(wk), akc = CT(ak), th = CT(P.theta), th1 = CT(1.0 + P.theta);
+
+    // ---------------- Phase I: g = A^T y, b, inner-solver start ----------------
+    double red1[4];
+    {
+      DotAcc<CT> a0, a1, a2, a3;  // inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2
+      space_rows<BS, LM, Acc>(
+          I.vsp, prank, src(I.ATs, I.AT, [&](int i) { return y[i]; }),
+          src(I.Qs, I.Q, [&](int k) { return x[k]; }, method != PDHCG_INNER_DIAG && use_q), red,
+          [&](int j, const Acc* sums) {
+            const CT xj = x[j];
+            const CT bj = xj * itau - c_s[j] - CT(sums[0]);
+            a1.add_prod(bj, bj);
+            if (method == PDHCG_INNER_DIAG) {
+              const CT xt = clampv(bj / (qdiag[j] + itau), lv[j], uv[j]);
+              const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
+              xT[j] = xt;
+              xbar[j] = CT(2) * xt - xj;
+              xn[j] = xnj;
+              a2.add_prod(xt - xj, xt - xj);
+              a3.add_prod(xnj - xj, xnj - xj);
+            } else if (method == PDHCG_INNER_CG) {
+              const CT hx = CT(sums[1]) + xj * itau;
+              const CT rj = bj - hx;
+              rv[j] = rj;
+              xT[j] = xj;
+              a0.add_prod(rj, rj);
+            } else {
+              const CT hx = CT(sums[1]) + xj * itau;
+              const CT gj = hx - bj;
+              grad[j] = gj;
+              bvv[j] = bj;
+              xT[j] = xj;
+              const CT d = xj - clampv(xj - gj, lv[j], uv[j]);
+              a0.add_prod(d, d);
+            }
+          });
+      red1[0] = a0.get();
+      red1[1] = a1.get();
+      red1[2] = a2.get();
+      red1[3] = a3.get();
+      clk.mark(S.tm, 0);
+      if (!group_reduce<BS, 4>(g, red1, 0u)) { ok = false; break; }
+      clk.mark(S.tm, 5);
+    }
+
+    // adaptive inner tolerance (Sec. 3.3)
+    if (S.K == 0) S.eps_in = P.eps_inner_first * fmax(1.0, sqrt(red1[1]));
+    else S.eps_in = fmin(S.eps_in, fmax(P.gamma_inner * S.omega * S.mv * inv_tau, P.eps_inner_min));
+    // With FP32 vectors the subproblem residual cannot be resolved below a few
+    // units in the last place of b: the inner solve stops there instead of
+    // running to its step cap (FP64 vectors: the paper's rule unchanged).
+    const double eps = sizeof(VecT) == 4 ? fmax(S.eps_in, 0x1p-20 * sqrt(red1[1])) : S.eps_in;
+
+    // ---------------- inner solve ----------------
+    if (method == PDHCG_INNER_CG) {
+      double rr = red1[0], beta = 0.0;
+      int j = 0, pc = 0;
+      while (true) {
+        if (sqrt(rr) <= eps || j >= P.max_inner_iter) break;
+        const VecT* pold = pc ? I.p1 : I.p0;
+        VecT* pnew = pc ? I.p0 : I.p1;
+        const CT be = CT(beta);
+        const bool first = (j == 0);
+        // Phase A: p = r + beta p (gathered on the fly, bit-identical to the
+        // owner's write), q = H p, p^T q
+        double pq[1];
+        {
+          DotAcc<CT> apq;
+          space_rows<BS, LM, Acc>(
+              I.vsp, prank,
+              src(I.Qs, I.Q, [&](int k) { return first ? rv[k] : CT(fma(be, pold[k], rv[k])); }, use_q),
+              none, red, [&](int i, const Acc* sums) {
+                const CT pi = first ? rv[i] : CT(fma(be, pold[i], rv[i]));
+                pnew[i] = pi;
+                const CT qi = CT(sums[0]) + pi * itau;
+                qv[i] = qi;
+                apq.add_prod(pi, qi);
+              });
+          pq[0] = apq.get();
+          clk.mark(S.tm, 1);
+          if (!group_reduce<BS, 1>(g, pq, 0u)) { ok = false; break; }
+          clk.mark(S.tm, 5);
+        }
+        if (!(pq[0] > 0.0)) break;
+        const double alpha = rr / pq[0];
+        const CT al = CT(alpha);
+        // Phase B: x += alpha p, r -= alpha q, r^T r
+        double rn[1];
+        {
+          DotAcc<CT> arr;
+          for_elems<BS>(vlo, vhi, [&](int i) {
+            xT[i] = xT[i] + al * pnew[i];
+            const CT ri = rv[i] - al * qv[i];
+            rv[i] = ri;
+            arr.add_prod(ri, ri);
+          });
+          rn[0] = arr.get();
+          clk.mark(S.tm, 2);
+          if (!group_reduce<BS, 1>(g, rn, 0u)) { ok = false; break; }
+          clk.mark(S.tm, 5);
+        }
+        beta = rn[0] / rr;
+        rr = rn[0];
+        pc ^= 1;
+        ++j;
+      }
+      if (!ok) break;
+      S.inner_total += j;
+      for_elems<BS>(vlo, vhi, [&](int i) { xbar[i] = CT(2) * xT[i] - x[i]; });
+      if (!group_sync<BS>(g)) { ok = false; break; }
+    } else if (method == PDHCG_INNER_BB) {
+      // x and grad alternate between two buffers each: (xT, xprev) and (grad, gprev);
+      // the previous step's pair is read where the oracle keeps copies.
+      const double alpha_min = 1.0 / (S.gersh + inv_tau), alpha_max = 1.0 / inv_tau;
+      double nr = red1[0], ss = 0.0, sy = 0.0;
+      int j = 0;
+      VecT* xc = xT;      // current inner iterate
+      VecT* xo = xprev;   // previous inner iterate
+      VecT* gc = grad;
+      VecT* go = gprev;
+      while (true) {
+        if (sqrt(nr) <= eps || j >= P.max_inner_iter) break;
+        double alpha = alpha_min;
+        if (j > 0) {
+          alpha = sy > 0.0 ? ss / sy : alpha_max;
+          alpha = fmin(fmax(alpha, alpha_min), alpha_max);
+        }
+        const CT al = CT(alpha);
+        // Phase B': projected step into the other buffer
+        {
+          VecT* __restrict__ xn2 = xo;
+          const VecT* __restrict__ x1 = xc;
+          const VecT* __restrict__ g1 = gc;
+          for_elems<BS>(vlo, vhi, [&](int i) { xn2[i] = clampv(x1[i] - al * g1[i], lv[i], uv[i]); });
+        }
+        { VecT* t = xo; xo = xc; xc = t; }
+        clk.mark(S.tm, 2);
+        if (!group_sync<BS>(g)) { ok = false; break; }
+        clk.mark(S.tm, 5);
+        // Phase A': gradient, BB quantities, natural residual
+        double v3[3];
+        {
+          DotAcc<CT> ass, asy, anr;
+          VecT* __restrict__ gn = go;
+          space_rows<BS, LM, Acc>(
+              I.vsp, prank, src(I.Qs, I.Q, [&](int k) { return xc[k]; }, use_q), none, red,
+              [&](int i, const Acc* sums) {
+                const CT xi = xc[i];
+                const CT gi = (CT(sums[0]) + xi * itau) - bvv[i];
+                gn[i] = gi;
+                const CT sv = xi - xo[i];
+                const CT yv = gi - gc[i];
+                ass.add_prod(sv, sv);
+                asy.add_prod(sv, yv);
+                const CT d = xi - clampv(xi - gi, lv[i], uv[i]);
+                anr.add_prod(d, d);
+              });
+          v3[0] = ass.get();
+          v3[1] = asy.get();
+          v3[2] = anr.get();
+          clk.mark(S.tm, 1);
+          if (!group_reduce<BS, 3>(g, v3, 0u)) { ok = false; break; }
+          clk.mark(S.tm, 5);
+        }
+        { VecT* t = go; go = gc; gc = t; }
+        ss = v3[0];
+        sy = v3[1];
+        nr = v3[2];
+        ++j;
+      }
+      if (!ok) break;
+      S.inner_total += j;
+      // the result must be in xT for Phase II and the checks; xbar = 2 x+ - x
+      if (xc != xT) {
+        for_elems<BS>(vlo, vhi, [&](int i) {
+          const CT xi = xc[i];
+          xT[i] = xi;
+          xbar[i] = CT(2) * xi - x[i];
+        });
+      } else {
+        for_elems<BS>(vlo, vhi, [&](int i) { xbar[i] = CT(2) * xT[i] - x[i]; });
+      }
+      if (!group_sync<BS>(g)) { ok = false; break; }
+    }
+
+    // ---------------- Phase II: A xbar, dual step, Halpern ----------------
+    double red2[3];
+    {
+      DotAcc<CT> ady, adx, amv;
+      space_rows<BS, LM, Acc>(
+          I.csp, prank, src(I.As, I.A, [&](int j) { return xbar[j]; }), none, red,
+          [&](int i, const Acc* sums) {
+            const CT yi = y[i];
+            const CT v = yi * isig + CT(sums[0]);
+            const CT yt = sig * (v - clampv(v, lc[i], uc[i]));
+            yT[i] = yt;
+            yn[i] = wkc * (th1 * yt - th * yi) + akc * ya[i];
+            ady.add_prod(yt - yi, yt - yi);
+          });
+      if (method != PDHCG_INNER_DIAG) {
+        for_elems<BS>(vlo, vhi, [&](int j) {
+          const CT xt = xT[j], xj = x[j];
+          const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
+          xn[j] = xnj;
+          adx.add_prod(xt - xj, xt - xj);
+          amv.add_prod(xnj - xj, xnj - xj);
+        });
+      }
+      red2[0] = ady.get();
+      red2[1] = adx.get();
+      red2[2] = amv.get();
+      clk.mark(S.tm, 3);
+      if (!group_reduce<BS, 3>(g, red2, 0u)) { ok = false; break; }
+      clk.mark(S.tm, 5);
+    }
+    const double dy2 = red2[0];
+    const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
+    const double mvh2 = method == PDHCG_INNER_DIAG ? red1[3] : red2[2];
+    const double fpr = sqrt(S.omega * dx2 + dy2 / S.omega);
+    if (S.k == 0) {
+      S.fpr_anchor = fpr;
+      S.fpr_last = fpr;
+    }
+
+    bool do_restart = false;
+    const bool check = ((S.K + 1) % P.k_eval == 0) || (S.K + 1 >= P.max_iter);
+    if (check) {
+      // ------------- check phase: KKT (Sec. 4.2) + infeasibility (Sec. 5) -------------
+      double cv[18];
+#pragma unroll
+      for (int q = 0; q < 18; ++q) cv[q] = 0.0;
+      space_rows<BS, LM, double>(
+          I.csp, prank,
+          src2(I.As, I.A, [&](int j) { return double(xT[j]); },
+               [&](int j) { return double(xT[j]) - double(x[j]); }),
+          none, red, [&](int i, const double* sums) {
+            const double ax = sums[0], ad = sums[1];
+            const double axu = ax / I.E[i];
+            cv[0] = fmax(cv[0], fabs(axu - clampv(axu, I.lc_o[i], I.uc_o[i])));
+            const double yu = double(yT[i]) * I.E[i];
+            cv[7] += support_term(yu, I.lc_o[i], I.uc_o[i]);
+            const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]);
+            cv[9] += support_term(ytl, double(lc[i]), double(uc[i]));
+            cv[13] = fmax(cv[13], fabs(ad - proj_recc(ad, ctype[i])));
+            const double dya = double(yT[i]) - double(ya[i]);
+            cv[16] += dya * dya;
+          });
+      space_rows<BS, LM, double>(
+          I.vsp, prank,
+          src2(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
+               [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
+          src2(I.Qs, I.Q, [&](int k) { return double(xT[k]); },
+               [&](int k) { return double(xT[k]) - double(x[k]); }, use_q),
+          red, [&](int j, const double* sums) {
+            const double aty = sums[0], atyt = sums[1], qx = sums[2], qd = sums[3];
+            const double Dj = I.D[j];
+            const double xu = double(xT[j]) * Dj;
+            const double qxu = qx / Dj, atyu = aty / Dj;
+            const double rj = qxu + I.c_o[j] + atyu;
+            const double rh = proj_R(rj, vtype[j]);
+            cv[1] = fmax(cv[1], fabs(rj - rh));
+            cv[2] = fmax(cv[2], fabs(qxu));
+            cv[3] = fmax(cv[3], fabs(atyu));
+            cv[4] += xu * qxu;
+            cv[5] += I.c_o[j] * xu;
+            cv[6] += support_term(-rh, I.lv_o[j], I.uv_o[j]);
+            cv[8] = fmax(cv[8], fabs(atyt - proj_R(atyt, vtype[j])));
+            cv[9] += support_term(-atyt, double(lv[j]), double(uv[j]));
+            const double dx = double(xT[j]) - double(x[j]);
+            cv[10] = fmax(cv[10], fabs(dx));
+            cv[11] += double(c_s[j]) * dx;
+            cv[12] = fmax(cv[12], fabs(dx - proj_recc(dx, vtype[j])));
+            cv[14] = fmax(cv[14], fabs(qd));
+            const double dxa = double(xT[j]) - double(xa[j]);
+            cv[15] += dxa * dxa;
+          });
+      cv[17] = double(globaltimer_ns());
+      // max slots: 0 1 2 3 8 10 12 13 14 17
+      const unsigned mm = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3) | (1u << 8) | (1u << 10) |
+                          (1u << 12) | (1u << 13) | (1u << 14) | (1u << 17);
+      clk.mark(S.tm, 4);
+      if (!group_reduce<BS, 18>(g, cv, mm)) { ok = false; break; }
+      clk.mark(S.tm, 5);
+
+      const double r_primal = cv[0] / (1.0 + I.bscale);
+      const double r_dual = cv[1] / (1.0 + fmax(fmax(cv[2], cv[3]), I.cinf));
+      const double xQx = cv[4], cx = cv[5], pr = cv[6], py = cv[7];
+      const double pobj = 0.5 * xQx + cx;
+      const double dobj = -pr - 0.5 * xQx - py;
+      const double gap = fabs(xQx + cx + pr + py);
+      const double r_gap = gap / (1.0 + fmax(fabs(pobj), fabs(0.5 * xQx + pr + py)));
+      const double rmax = fmax(r_primal, fmax(r_dual, r_gap));
+      S.r_primal = r_primal;
+      S.r_dual = r_dual;
+      S.r_gap = r_gap;
+      S.pobj = pobj;
+      S.dobj = dobj;
+      int status = 0;
+      if (!isfinite(rmax)) status = PDHCG_NUMERICAL_ERROR;
+      else if (rmax <= P.eps_tol) status = PDHCG_OPTIMAL;
+      if (!status) {
+        const double neg = cv[9] < 0.0 ? -cv[9] : 0.0;
+        if (neg > 0.0 && cv[8] <= P.eps_inf * neg) status = PDHCG_PRIMAL_INFEASIBLE;
+      }
+      if (!status) {
+        const double dn = cv[10];
+        if (dn > 0.0) {
+          const double vmax = fmax(cv[12] / dn, fmax(cv[13] / dn, cv[14] / dn));
+          if (cv[11] / dn < -P.eps_tol && vmax <= P.eps_inf) status = PDHCG_DUAL_INFEASIBLE;
+        }
+      }
+      if (!status && S.K + 1 >= P.max_iter) status = PDHCG_ITERATION_LIMIT;
+      if (!status && cv[17] - S.t_start_ns >= P.time_limit_ns) status = PDHCG_TIME_LIMIT;
+
+      if (status) {
+        // ---- output phase: unscale (x = D x+, y = E y+) or normalised rays ----
+        const double dn = cv[10];
+        double mx[2] = {0.0, 0.0};
+        if (status == PDHCG_PRIMAL_INFEASIBLE || status == PDHCG_DUAL_INFEASIBLE) {
+          for_elems<BS>(clo, chi, [&](int i) {
+            const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]) * I.E[i];
+            mx[0] = fmax(mx[0], fabs(ytl));
+          });
+          for_elems<BS>(vlo, vhi, [&](int j) {
+            const double d = ((double(xT[j]) - double(x[j])) / dn) * I.D[j];
+            mx[1] = fmax(mx[1], fabs(d));
+          });
+          if (!group_reduce<BS, 2>(g, mx, 3u)) { ok = false; break; }
+        }
+        if (I.x_out) {
+          for_elems<BS>(vlo, vhi, [&](int j) {
+            double v = double(xT[j]) * I.D[j];
+            if (status == PDHCG_DUAL_INFEASIBLE) {
+              const double d = ((double(xT[j]) - double(x[j])) / dn) * I.D[j];
+              v = mx[1] > 0.0 ? d / mx[1] : 0.0;
+            }
+            I.x_out[j] = v;
+          });
+        }
+        if (I.y_out) {
+          for_elems<BS>(clo, chi, [&](int i) {
+            double v = double(yT[i]) * I.E[i];
+            if (status == PDHCG_PRIMAL_INFEASIBLE) {
+              const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]) * I.E[i];
+              v = mx[0] > 0.0 ? ytl / mx[0] : 0.0;
+            }
+            I.y_out[i] = v;
+          });
+        }
+        S.status = status;
+        S.K += 1;
+        S.t_end_ns = cv[17];
+        break;
+      }
+
+      // restart test on the fixed-point residual (reading of the unstated rule)
+      if (S.k >= 1) {
+        if (fpr <= P.restart_sufficient * S.fpr_anchor) do_restart = true;
+        else if (fpr <= P.restart_necessary * S.fpr_anchor && fpr > S.fpr_last) do_restart = true;
+        else if (double(S.k + 1) >= P.restart_artificial * double(S.K + 1)) do_restart = true;
+      }
+      S.fpr_last = fpr;
+      if (do_restart) {
+        pid_update(S, P, sqrt(cv[15]), sqrt(cv[16]));
+        S.omega = exp(S.log_omega);
+        S.tau = S.eta / S.omega;
+        S.sigma = S.eta * S.omega;
+      }
+    }
+
+    if (do_restart) {
+      // new anchor and iterate: T(z)
+      for_elems<BS>(vlo, vhi, [&](int j) {
+        const VecT v = xT[j];
+        x[j] = v;
+        xa[j] = v;
+      });
+      for_elems<BS>(clo, chi, [&](int i) {
+        const VecT v = yT[i];
+        y[i] = v;
+        ya[i] = v;
+      });
+      if (!group_sync<BS>(g)) { ok = false; break; }
+      clk.mark(S.tm, 6);
+      S.mv = sqrt(dx2);
+      S.k = 0;
+      S.restarts += 1;
+    } else {
+      S.cur ^= 1;
+      S.mv = sqrt(mvh2);
+      S.k += 1;
+    }
+    S.K += 1;
+    if (plan.iter_budget > 0 && S.K - K_first >= plan.iter_budget) break;  // paused
+  }
+  if (!ok) S.device_error = 1;
+  if (g.rank == 0 && threadIdx.x == 0) *I.st = S;
+}
+
+#ifndef PDHCG_MIN_BLOCKS
+#define PDHCG_MIN_BLOCKS 4
+#endif
+template <int BS, class MatT, class VecT>
+__global__ void __launch_bounds__(BS, PDHCG_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
+  __shared__ double sm_warp[2 * (BS / 32) * kSlots];
+  __shared__ double sm_tot[2 * kSlots];
+  __shared__ double sm_red[(BS / 32) * 4];
+  extern __shared__ __align__(16) char dsm[];
+  __shared__ int sm_flag;
+  __shared__ int sm_idx;
+  Group<BS> g;
+  g.sm_warp = sm_warp;
+  g.sm_tot = sm_tot;
+  g.sm_flag = &sm_flag;
+  g.err = plan.err;
+  g.timeout_ns = plan.timeout_ns;
+  g.failed = false;
+  g.epoch = 0;
+  if (threadIdx.x == 0) sm_flag = 0;
+  WarpStages* stages = reinterpret_cast<WarpStages*>(dsm);
+#if PDHCG_TMA_STAGING
+  init_stages<BS>(stages);
+#else
+  __syncthreads();
+#endif
+  const RowCtx rc{stages, sm_red, plan.err, &sm_flag, plan.timeout_ns};
+  if ((int)blockIdx.x < plan.group_blocks) {
+    int gi = 0;
+    while (gi + 1 < plan.ngroups && (int)blockIdx.x >= plan.g_first[gi + 1]) ++gi;
+    g.nblk = plan.g_nblk[gi];
+    g.rank = (int)blockIdx.x - plan.g_first[gi];
+    g.bar32 = reinterpret_cast<unsigned*>(plan.g_bar) + size_t(gi) * kBarWords;
+    g.part = plan.g_part + plan.g_part_off[gi];
+    solve_instance<BS, Ld::Stream>(g, insts[plan.g_inst[gi]], plan, rc);
+    return;
+  }
+  g.nblk = 1;
+  g.rank = 0;
+  g.bar32 = nullptr;
+  g.part = nullptr;
+  while (true) {
+    if (threadIdx.x == 0) sm_idx = atomicAdd(plan.pool_next, 1);
+    __syncthreads();
+    const int idx = sm_idx;
+    __syncthreads();
+    if (idx >= plan.npool) break;
+    g.epoch = 0;
+    solve_instance<BS, Ld::Cached>(g, insts[plan.pool_inst[idx]], plan, rc);
+    __syncthreads();
+  }
+}
+
+// SELL values from the scaled CSR values: one warp per slice.
+template <class MatT>
+__global__ void sell_fill_kernel(int nslices, const int32_t* perm, const int64_t* sptr,
+                                 const int32_t* rowptr, const MatT* csr_val, MatT* sell_val) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x / 32;
+  for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nslices; s += gridDim.x * wpb) {
+    const int row = perm[s * 32 + lane];
+    const int64_t b = sptr[s];
+    const int W = int((sptr[s + 1] - b) >> 5);
+    const int rb = row >= 0 ? rowptr[row] : 0;
+    const int len = row >= 0 ? rowptr[row + 1] - rb : 0;
+    for (int j = 0; j < W; ++j) sell_val[b + 32 * j + lane] = j < len ? csr_val[rb + j] : MatT(0);
+  }
+}
+
+}  // namespace pdhcg

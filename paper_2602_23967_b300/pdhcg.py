@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libpdhcg.so (include/pdhcg.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Importing this module loads the in-tree ``libpdhcg.so``; if it is
+missing the import fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdhcg.so")
+
+OK, PENDING = 0, 1
+E_INVALID, E_OOM, E_CUDA, E_BUSY, E_NOT_FOUND, E_DEVICE_TIMEOUT = -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "UNSOLVED", 1: "OPTIMAL", 2: "PRIMAL_INFEASIBLE", 3: "DUAL_INFEASIBLE",
+                4: "ITERATION_LIMIT", 5: "TIME_LIMIT", 6: "NUMERICAL_ERROR"}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
+INNER = {"auto": 0, "diag": 1, "cg": 2, "bb": 3}
+
+
+class PdhcgError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__(f"{where}: {code} ({detail})")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("precision", C.c_int32),
+        ("eps_tol", C.c_double), ("eps_inf", C.c_double), ("time_limit_s", C.c_double),
+        ("max_iter", C.c_int64),
+        ("theta", C.c_double), ("kp", C.c_double), ("ki", C.c_double), ("kd", C.c_double),
+        ("gamma_inner", C.c_double), ("eps_inner_min", C.c_double), ("eps_inner_first", C.c_double),
+        ("k_eval", C.c_int32), ("inner", C.c_int32), ("max_inner_iter", C.c_int32),
+        ("ruiz_iters", C.c_int32),
+        ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
+        ("restart_artificial", C.c_double),
+        ("power_max_iter", C.c_int32), ("lanes_override", C.c_int32),
+        ("power_tol", C.c_double), ("eta_override", C.c_double), ("omega0_override", C.c_double),
+        ("omega_clamp", C.c_double),
+        ("group_blocks", C.c_int32), ("device_timeout_ms", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("inner_method", C.c_int32),
+        ("iterations", C.c_int64), ("inner_iterations", C.c_int64), ("restarts", C.c_int64),
+        ("r_primal", C.c_double), ("r_dual", C.c_double), ("r_gap", C.c_double),
+        ("primal_obj", C.c_double), ("dual_obj", C.c_double),
+        ("eta", C.c_double), ("omega", C.c_double), ("norm_A", C.c_double),
+        ("solve_seconds", C.c_double), ("power_iters", C.c_int32), ("precision", C.c_int32),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, "?")
+        return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("rejected", C.c_uint64), ("launches", C.c_uint64), ("live", C.c_int32),
+                ("queued", C.c_int32), ("hbm_in_use", C.c_size_t)]
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libpdhcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2602_23967_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        L.pdhcg_default_params.argtypes = [C.POINTER(Params)]
+        L.pdhcg_create.argtypes = [C.POINTER(Csr), C.POINTER(Csr), _D, _D, _D, _D, _D,
+                                   C.POINTER(Params), _P, C.POINTER(_P)]
+        L.pdhcg_solve.argtypes = [_P, _D, _D, C.POINTER(Result), _D, _D]
+        L.pdhcg_solve_dev.argtypes = [_P, _P, _P, C.POINTER(Result), _P, _P]
+        L.pdhcg_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(Result), C.POINTER(_D),
+                                        C.POINTER(_D)]
+        L.pdhcg_get_eta.argtypes = [_P, _D, _D]
+        L.pdhcg_get_scaling.argtypes = [_P, _D, _D]
+        L.pdhcg_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_size_t)]
+        L.pdhcg_get_phase_times.argtypes = [_P, _D]
+        L.pdhcg_destroy.argtypes = [_P]
+        L.pdhcg_destroy.restype = None
+        L.pdhcg_strerror.restype = C.c_char_p
+        L.pdhcg_last_error.restype = C.c_char_p
+        if hasattr(L, "pdhcg_server_create"):
+            L.pdhcg_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(Params), _P,
+                                              C.POINTER(_P)]
+            L.pdhcg_submit.argtypes = [_P, C.POINTER(Csr), C.POINTER(Csr), _D, _D, _D, _D, _D,
+                                       C.POINTER(C.c_uint64)]
+            L.pdhcg_poll.argtypes = [_P, C.c_uint64, C.POINTER(Result), _D, _D]
+            L.pdhcg_server_get_stats.argtypes = [_P, C.POINTER(ServerStats)]
+            L.pdhcg_server_destroy.argtypes = [_P]
+            L.pdhcg_server_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def check(code, where):
+    if code < 0:
+        L = lib()
+        raise PdhcgError(code, where, (L.pdhcg_strerror(code) or b"").decode() + ": " +
+                         (L.pdhcg_last_error() or b"").decode())
+    return code
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    check(lib().pdhcg_default_params(C.byref(p)), "pdhcg_default_params")
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "inner" and isinstance(v, str):
+            v = INNER[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+class _CsrHold:
+    def __init__(self, M, nrows, ncols):
+        self.indptr = np.ascontiguousarray(M.indptr, dtype=np.int64)
+        self.indices = np.ascontiguousarray(M.indices, dtype=np.int32)
+        self.data = _f64(M.data)
+        self.s = Csr(nrows, ncols, int(self.indptr[-1]) if len(self.indptr) else 0,
+                     self.indptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                     self.indices.ctypes.data_as(C.POINTER(C.c_int32)),
+                     self.data.ctypes.data_as(_D))
+
+
+def _qp_args(qp):
+    n, m = int(qp.n), int(qp.m)
+    hold = {"A": _CsrHold(qp.A, m, n)}
+    if qp.Q is not None:
+        hold["Q"] = _CsrHold(qp.Q, n, n)
+    for k in ("c", "lc", "uc", "lv", "uv"):
+        hold[k] = _f64(getattr(qp, k))
+    return hold
+
+
+class Problem:
+    """A QP resident on the device (pdhcg_create)."""
+
+    def __init__(self, qp, params: Params | None = None, stream=None):
+        L = lib()
+        self.n, self.m = int(qp.n), int(qp.m)
+        self.params = params if params is not None else default_params()
+        h = _qp_args(qp)
+        handle = _P()
+        rc = L.pdhcg_create(C.byref(h["Q"].s) if "Q" in h else None, C.byref(h["A"].s),
+                            _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]),
+                            C.byref(self.params), _P(stream) if stream else None, C.byref(handle))
+        check(rc, "pdhcg_create")
+        self.handle = handle
+
+    def solve(self, x0=None, y0=None):
+        x = np.zeros(self.n)
+        y = np.zeros(max(self.m, 1))
+        res = Result()
+        x0 = _f64(x0) if x0 is not None else None
+        y0 = _f64(y0) if y0 is not None else None
+        check(lib().pdhcg_solve(self.handle, _dp(x0), _dp(y0), C.byref(res), _dp(x), _dp(y)),
+              "pdhcg_solve")
+        return x, y[: self.m], res.as_dict()
+
+    def solve_dev(self, x_out, y_out, x0=None, y0=None):
+        """Device-buffer solve: x_out / y_out (and optional x0 / y0) are float64 CUDA tensors."""
+        res = Result()
+        ptr = (lambda t: _P(t.data_ptr()) if t is not None else None)
+        check(lib().pdhcg_solve_dev(self.handle, ptr(x0), ptr(y0), C.byref(res), ptr(x_out),
+                                    ptr(y_out)), "pdhcg_solve_dev")
+        return res.as_dict()
+
+    def eta(self):
+        e, a = C.c_double(), C.c_double()
+        check(lib().pdhcg_get_eta(self.handle, C.byref(e), C.byref(a)), "pdhcg_get_eta")
+        return e.value, a.value
+
+    def scaling(self):
+        D = np.zeros(self.n)
+        E = np.zeros(max(self.m, 1))
+        check(lib().pdhcg_get_scaling(self.handle, _dp(D), _dp(E)), "pdhcg_get_scaling")
+        return D, E[: self.m]
+
+    def phase_times(self):
+        t = np.zeros(8)
+        check(lib().pdhcg_get_phase_times(self.handle, _dp(t)), "pdhcg_get_phase_times")
+        names = ["phase1", "inner_rows", "inner_elem", "phase2", "check", "barrier", "restart", "other"]
+        return dict(zip(names, t.tolist()))
+
+    def device_bytes(self):
+        n, m, b = C.c_int32(), C.c_int32(), C.c_size_t()
+        check(lib().pdhcg_get_info(self.handle, C.byref(n), C.byref(m), C.byref(b)), "pdhcg_get_info")
+        return int(b.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdhcg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(problems, want_solutions=True):
+    """Solve many Problems in one persistent launch (pdhcg_solve_batch)."""
+    count = len(problems)
+    handles = (_P * count)(*[p.handle for p in problems])
+    res = (Result * count)()
+    xs = [np.zeros(p.n) for p in problems] if want_solutions else None
+    ys = [np.zeros(max(p.m, 1)) for p in problems] if want_solutions else None
+    xp = (_D * count)(*[_dp(x) for x in xs]) if want_solutions else None
+    yp = (_D * count)(*[_dp(y) for y in ys]) if want_solutions else None
+    check(lib().pdhcg_solve_batch(handles, count, res, xp, yp), "pdhcg_solve_batch")
+    out = [r.as_dict() for r in res]
+    if want_solutions:
+        return [(xs[i], ys[i][: problems[i].m], out[i]) for i in range(count)]
+    return out
+
+
+def strerror(code):
+    return lib().pdhcg_strerror(code).decode()

@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function that
+include/pdhcg.h declares, and rejects malformed problems before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2602_23967_b300 import pdhcg
+from paper_2602_23967_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(pdhcg_\w+)\s*\(", txt, re.M):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = pdhcg.lib()
+    names = declared_functions()
+    assert "pdhcg_create" in names and "pdhcg_solve_batch" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_default_params_and_strerror():
+    p = pdhcg.default_params()
+    assert p.struct_size == C.sizeof(pdhcg.Params)
+    assert p.eps_tol == 1e-6 and p.k_eval == 64 and p.theta == 1.0
+    assert p.gamma_inner == 5e-4 and p.eps_inner_min == 1e-9
+    assert pdhcg.strerror(pdhcg.E_INVALID).startswith("invalid")
+
+
+def _bad(qp, **kw):
+    with pytest.raises(pdhcg.PdhcgError) as ei:
+        pdhcg.Problem(qp, pdhcg.default_params(**kw))
+    assert ei.value.code == pdhcg.E_INVALID
+    return str(ei.value)
+
+
+def test_rejects_malformed_problems():
+    base = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=0)
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=0)
+    qp.lc = qp.lc.copy(); qp.lc[5] = qp.uc[5] + 1.0
+    assert "bound" in _bad(qp)
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=0)
+    qp.c = qp.c.copy(); qp.c[0] = np.nan
+    assert "c" in _bad(qp)
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=0)
+    Qd = qp.Q.toarray(); Qd[0, 1] += 1.0
+    qp.Q = sp.csr_matrix(Qd)
+    assert "symmetric" in _bad(qp)
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=0)
+    qp.lv = qp.lv.copy(); qp.lv[3] = np.inf
+    assert "bound" in _bad(qp)
+    # CG is only valid when every variable is free; DIAG needs a diagonal Q
+    assert "CG" in _bad(base, inner="cg")
+    assert "DIAG" in _bad(base, inner="diag")
+
+
+def test_rejects_bad_csr_structure():
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=1)
+    A = qp.A.copy()
+    A.indices = A.indices.copy(); A.indices[0] = 25    # column out of range
+    qp.A = A
+    assert "range" in _bad(qp)
+
+
+def test_rejects_bad_params():
+    qp = W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=1)
+    p = pdhcg.default_params()
+    p.struct_size = 12
+    with pytest.raises(pdhcg.PdhcgError):
+        pdhcg.Problem(qp, p)
+    with pytest.raises(pdhcg.PdhcgError):
+        pdhcg.Problem(qp, pdhcg.default_params(k_eval=0))

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (written in each test):
+* final results: the oracle's independent KKT evaluator (Sec. 4.2) applied to
+  the GPU solution is <= eps_tol, and the relative objective difference to the
+  oracle's solve is <= 1e-6;
+* FP64 iterates: after N = 1 .. 100 PDHG steps the GPU iterate equals the
+  oracle's to 1e-10 relative (same eta, passed to the oracle);
+* setup: Ruiz vectors to 1e-13, ||A|| to 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_23967_b300 import pdhcg
+from paper_2602_23967_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def kkt_of(qp, x, y):
+    Q = qp.Q
+    Qx = Q @ x if Q is not None else np.zeros(qp.n)
+    return oracle.kkt(qp.n, qp.m, x, y, qp.A @ x, qp.A.T @ y, Qx, qp.c, qp.lc, qp.uc, qp.lv, qp.uv)
+
+
+def rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+def gpu_solve(qp, **kw):
+    prob = pdhcg.Problem(qp, pdhcg.default_params(**kw))
+    try:
+        x, y, r = prob.solve()
+        eta, _ = prob.eta()
+    finally:
+        prob.close()
+    return x, y, r, eta
+
+
+def check_optimal_parity(qp, eps=1e-6, precision="fp64", obj_tol=1e-6, **kw):
+    x, y, r, _ = gpu_solve(qp, eps_tol=eps, precision=precision, **kw)
+    assert r["status_name"] == "OPTIMAL", r
+    rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
+    assert max(rp, rd, rg) <= eps * (1.5 if precision == "fp64" else 3.0), (rp, rd, rg)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(eps_tol=eps, **{k: v for k, v in kw.items()
+                                                                       if k in ("inner",)}))
+    assert ro["status_name"] == "OPTIMAL"
+    assert rel(pobj, ro["primal_obj"]) <= obj_tol, (pobj, ro["primal_obj"])
+    return r, ro
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_random_qp_fp64(seed):
+    r, ro = check_optimal_parity(W.random_qp(seed=seed))
+    # same algorithm, same decisions: iteration counts agree closely
+    assert abs(r["iterations"] - ro["iterations"]) <= 64
+
+
+def test_setup_matches_oracle():
+    qp = W.random_qp(seed=3)
+    prob = pdhcg.Problem(qp, pdhcg.default_params())
+    D, E = prob.scaling()
+    eta, normA = prob.eta()
+    prob.close()
+    Do, Eo = oracle.ruiz(qp, passes=10)
+    assert np.max(np.abs(D - Do) / Do) <= 1e-13
+    assert np.max(np.abs(E - Eo) / Eo) <= 1e-13
+    import scipy.sparse as sp
+    As = sp.diags(Eo) @ qp.A @ sp.diags(Do)
+    ref = np.linalg.norm(As.toarray(), 2)
+    assert normA == pytest.approx(ref, rel=1e-6)
+
+
+@pytest.mark.parametrize("group_blocks", [1, 7])
+@pytest.mark.parametrize("N", [1, 2, 5, 17, 64, 100])
+def test_fp64_iterates_first_100(N, group_blocks):
+    qp = W.random_qp(seed=4)
+    x, y, r, eta = gpu_solve(qp, max_iter=N, group_blocks=group_blocks)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
+    assert r["iterations"] == ro["iterations"] == N
+    assert r["inner_iterations"] == ro["inner_iterations"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
+
+
+@pytest.mark.parametrize("group_blocks", [3, 16, 0])
+def test_multi_cta_iterates_mid_size(group_blocks):
+    # several partitions, ragged tails, BB inner solver on a non-diagonal Q
+    qp = W.large_sparse_qp(n=6000, m=3000, seed=1)
+    N = 100
+    x, y, r, eta = gpu_solve(qp, max_iter=N, group_blocks=group_blocks)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
+    assert r["inner_iterations"] == ro["inner_iterations"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
+
+
+def test_cg_inner_solver_iterates():
+    # every variable free -> CG (Sec. 2.2 / Sec. 3.3)
+    qp = W.equality_qp(n=120, m=40, seed=2)
+    for N in (3, 64, 100):
+        x, y, r, eta = gpu_solve(qp, max_iter=N)
+        xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
+        assert r["inner_method"] == 2 and ro["inner_method"] == 2
+        assert r["inner_iterations"] == ro["inner_iterations"]
+        assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+
+
+def test_equality_qp_matches_dense_kkt():
+    qp = W.equality_qp(n=30, m=10, seed=0)
+    Q, A = qp.Q.toarray(), qp.A.toarray()
+    K = np.block([[Q, A.T], [A, np.zeros((qp.m, qp.m))]])
+    sol = np.linalg.solve(K, np.concatenate([-qp.c, qp.lc]))
+    x, y, r, _ = gpu_solve(qp, eps_tol=1e-10)
+    assert r["status_name"] == "OPTIMAL"
+    assert np.linalg.norm(x - sol[:qp.n]) <= 1e-7 * (1 + np.linalg.norm(sol[:qp.n]))
+
+
+def test_mpc_fp64_and_fp32():
+    qp = W.mpc_qp(seed=11)
+    check_optimal_parity(qp)
+    # FP32 iterates stall near 1e-6 relative KKT on this class; 1e-5 is the FP32 bar,
+    # FP32 matrix values with FP64 vectors (mixed) reach 1e-6.
+    check_optimal_parity(qp, precision="fp32", eps=1e-5, obj_tol=1e-5, max_iter=200000)
+    check_optimal_parity(qp, precision="mixed", max_iter=200000)
+
+
+def test_factor_portfolio_with_long_row_multi_cta():
+    # the budget row 1^T x has 20000 nonzeros and runs on a whole CTA
+    qp = W.factor_portfolio(n=20000, k=50, seed=0)
+    check_optimal_parity(qp, group_blocks=16)
+    x, y, r, eta = gpu_solve(qp, max_iter=100, group_blocks=16)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=100, eta_override=eta))
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
+
+
+def test_large_sparse_mid_size_fp64_fp32():
+    qp = W.large_sparse_qp(n=20000, m=10000, seed=0)
+    check_optimal_parity(qp)
+    check_optimal_parity(qp, precision="fp32", eps=1e-5, obj_tol=1e-5, max_iter=200000)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_primal_infeasible_detected(seed):
+    qp = W.infeasible_qp(n=8, m=4, seed=seed)
+    x, y, r, _ = gpu_solve(qp)
+    assert r["status_name"] == "PRIMAL_INFEASIBLE"
+    g = qp.A.T @ y
+    # Farkas ray: p(-A^T y) + p(y) < 0 with A^T y in R (Sec. 5.1)
+    def p(z, lo, hi):
+        return sum(hi[i] * z[i] if z[i] > 0 else (lo[i] * z[i] if z[i] < 0 else 0.0)
+                   for i in range(len(z)))
+    val = p(-g, qp.lv, qp.uv) + p(y, qp.lc, qp.uc)
+    assert val < 0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dual_infeasible_detected(seed):
+    qp = W.unbounded_qp(n=6, seed=seed)
+    x, y, r, _ = gpu_solve(qp)
+    assert r["status_name"] == "DUAL_INFEASIBLE"
+    assert qp.c @ x < 0
+    assert np.max(np.abs(qp.Q @ x)) <= 1e-5
+
+
+def test_edge_no_constraints_and_lp():
+    rng = np.random.default_rng(0)
+    n = 37
+    base = W.random_qp(n=n, m=10, n_eq=5, m_rows=10, density=0.3, seed=7)
+    import scipy.sparse as sp
+    qp = W.QP(n, 0, base.Q, W._csr(sp.csr_matrix((0, n))), base.c, np.zeros(0), np.zeros(0),
+              base.lv, base.uv, name="no_rows")
+    x, y, r, _ = gpu_solve(qp, eps_tol=1e-8)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(eps_tol=1e-8))
+    assert r["status_name"] == ro["status_name"] == "OPTIMAL"
+    assert rel(r["primal_obj"], ro["primal_obj"]) <= 1e-7
+    lp = W.QP(base.n, base.m, None, base.A, base.c, base.lc, base.uc, base.lv, base.uv, name="lp")
+    x, y, r, _ = gpu_solve(lp, eps_tol=1e-7)
+    xo, yo, ro = oracle.solve(lp, oracle.default_params(eps_tol=1e-7))
+    assert r["status_name"] == ro["status_name"] == "OPTIMAL"
+    assert rel(r["primal_obj"], ro["primal_obj"]) <= 1e-6
+
+
+def test_single_variable():
+    import scipy.sparse as sp
+    qp = W.QP(1, 1, W._csr(sp.csr_matrix(np.array([[2.0]]))), W._csr(sp.csr_matrix(np.array([[1.0]]))),
+              np.array([-3.0]), np.array([-np.inf]), np.array([1.0]), np.array([-5.0]), np.array([5.0]))
+    x, y, r, _ = gpu_solve(qp, eps_tol=1e-9)
+    assert r["status_name"] == "OPTIMAL"
+    assert x[0] == pytest.approx(1.0, abs=1e-8)     # min x^2 - 3x s.t. x <= 1
+
+
+def test_batch_equals_single_solves():
+    qps = [W.mpc_qp(seed=100 + i) for i in range(12)] + [W.random_qp(seed=20 + i) for i in range(4)]
+    probs = [pdhcg.Problem(q, pdhcg.default_params()) for q in qps]
+    try:
+        batch = pdhcg.solve_batch(probs)
+        for p, (xb, yb, rb) in zip(probs, batch):
+            xs, ys, rs = p.solve()
+            assert rb["status_name"] == rs["status_name"] == "OPTIMAL"
+            assert rb["iterations"] == rs["iterations"]
+            assert np.max(np.abs(xb - xs)) <= 1e-12 * (1 + np.max(np.abs(xs)))
+    finally:
+        for p in probs:
+            p.close()
+
+
+def test_warm_start_from_solution_is_immediate():
+    qp = W.random_qp(seed=9)
+    prob = pdhcg.Problem(qp, pdhcg.default_params(eps_tol=1e-7))
+    try:
+        x, y, r = prob.solve()
+        x2, y2, r2 = prob.solve(x0=x, y0=y)
+        assert r2["status_name"] == "OPTIMAL"
+        assert r2["iterations"] <= r["iterations"]
+    finally:
+        prob.close()
