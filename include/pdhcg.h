@@ -144,6 +144,21 @@ int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const 
                  const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
                  void* cuda_stream, pdhcg_t** out);
 
+/* One problem of a batch creation (same meaning as the pdhcg_create arguments). */
+typedef struct {
+  const pdhcg_csr* Q; /* NULL = no quadratic term */
+  const pdhcg_csr* A;
+  const double *c, *lc, *uc, *lv, *uv;
+} pdhcg_problem_data;
+
+/* Create count handles at once: host validation runs on several threads, all
+ * handles share one device allocation (released with the last handle), every
+ * input is staged through pinned memory, and the device setup of all problems
+ * runs in one launch (one CTA per problem).  On failure no handle is created
+ * and pdhcg_last_error() names the first bad problem.  out: count handles. */
+int pdhcg_create_batch(int count, const pdhcg_problem_data* problems, const pdhcg_params* params,
+                       void* cuda_stream, pdhcg_t** out);
+
 /* Solve from host buffers (blocking).  x0 (n) / y0 (m) are optional warm
  * starts (NULL = x = proj_X(0), y = 0).  x_out (n) / y_out (m) may be NULL.
  * Host<->device copies of the warm start and of the result are part of the call.

@@ -615,7 +615,7 @@ __device__ __forceinline__ void csr_part(const X& x, int row, int first, int ste
 // per row; sums holds the A gathers then the B gathers.  part_rank < 0: the
 // whole space (single-CTA group).  red: BS/32 * 4 doubles of shared scratch.
 template <int BS, Ld LM, class Acc, class SA, class SB, class Epi>
-__device__ __noinline__ void space_rows(const SpaceLayout& sp, int part_rank, const SA& A,
+__device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank, const SA& A,
                                         const SB& B, const RowCtx& rc, Epi epi) {
   WarpStages* stages = rc.stages;
   double* red = rc.red;

@@ -80,9 +80,12 @@ struct pdhcg_problem {
   int64_t *sATp = nullptr, *sQp = nullptr, *sAp = nullptr;
   int32_t *sATc = nullptr, *sQc = nullptr, *sAc = nullptr;
   void *sATv = nullptr, *sQv = nullptr, *sAv = nullptr;  // MatT
-  // single device arena
+  size_t vsell_cols[2] = {0, 0}, csell_cols = 0;  // SELL element counts
+  // device arena (possibly a slice of an allocation shared by a batch of handles)
   void* arena = nullptr;
   size_t arena_bytes = 0;
+  size_t input_bytes = 0;              // uploaded prefix of the arena
+  std::shared_ptr<void> arena_owner;  // frees the allocation with its last handle
   // typed device pointers (void* so the handle is precision-agnostic)
   int32_t *Qp_d = nullptr, *Qc_d = nullptr, *Ap_d = nullptr, *Ac_d = nullptr, *ATp_d = nullptr,
           *ATc_d = nullptr;

@@ -11,9 +11,25 @@ namespace pdhcg {
 inline size_t solve_dyn_smem() { return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (kGroupBS / 32) : 0; }
 
 template <class MatT, class VecT>
-cudaError_t set_solve_attrs() {
+cudaError_t set_solve_attrs(size_t extra = 0) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  size_t want = solve_dyn_smem() + extra;
+  const size_t static_part = 8192;  // group_reduce / row-engine shared arrays
+  if (want + static_part > size_t(optin)) want = size_t(optin) - static_part;
   return cudaFuncSetAttribute(solve_kernel<kGroupBS, MatT, VecT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(solve_dyn_smem()));
+                              int(want));
+}
+
+template <class MatT, class VecT>
+int pool_blocks_per_sm(size_t smem_vec_bytes) {
+  int nb = 0;
+  if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT>, kPoolBS,
+                                                    solve_dyn_smem() + smem_vec_bytes) != cudaSuccess)
+    return 0;
+  return nb;
 }
 
 template <class MatT, class VecT>
@@ -53,9 +69,10 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
                          cudaStream_t s) {
   LaunchPlan p = plan;
   const Inst<MatT, VecT>* di = d_insts;
-  cudaError_t e = set_solve_attrs<MatT, VecT>();
+  const size_t extra = plan.group_blocks == 0 ? size_t(plan.smem_vec_bytes) : 0;
+  cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
   if (e != cudaSuccess) return e;
-  const size_t smem = solve_dyn_smem();
+  const size_t smem = solve_dyn_smem() + extra;
   if (plan.group_blocks == 0) {
     solve_kernel<kPoolBS, MatT, VecT><<<grid, kPoolBS, smem, s>>>(di, p);
     return cudaGetLastError();
@@ -63,6 +80,26 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   void* args[] = {&di, &p};
   return cudaLaunchCooperativeKernel((const void*)solve_kernel<kGroupBS, MatT, VecT>, dim3(grid),
                                      dim3(kGroupBS), args, smem, s);
+}
+
+template <class MatT, class VecT>
+cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, int* next, int32_t* err,
+                              uint64_t timeout_ns, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int dev = 0, sms = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, setup_pool_kernel<kGroupBS, MatT, VecT>, kGroupBS, 0);
+  const int grid = std::max(1, std::min(count, std::max(nb, 1) * sms));
+  setup_pool_kernel<kGroupBS, MatT, VecT><<<grid, kGroupBS, 0, s>>>(d_args, count, next, err, timeout_ns);
+  return cudaGetLastError();
+}
+
+template <class MatT>
+cudaError_t launch_sell_fill_batch(const FillDesc* d, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  sell_fill_batch_kernel<MatT><<<std::min(count, 4096), 256, 0, s>>>(d, count);
+  return cudaGetLastError();
 }
 
 template <class MatT>
@@ -80,6 +117,9 @@ cudaError_t launch_sell_fill(int nslices, const int32_t* perm, const int64_t* sp
   template cudaError_t launch_setup<MatT, VecT>(const SetupArgs<MatT, VecT>&, int,             \
                                                 unsigned long long*, double*, int32_t*,        \
                                                 uint64_t, cudaStream_t);                       \
+  template int pool_blocks_per_sm<MatT, VecT>(size_t);                                          \
+  template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
+                                                     int32_t*, uint64_t, cudaStream_t);           \
   template cudaError_t launch_solve<MatT, VecT>(const Inst<MatT, VecT>*, const LaunchPlan&, int, \
                                                 cudaStream_t);
 

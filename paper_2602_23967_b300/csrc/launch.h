@@ -27,10 +27,23 @@ template <class MatT, class VecT>
 cudaError_t launch_setup(const SetupArgs<MatT, VecT>& a, int nblk, unsigned long long* bar,
                          double* part, int32_t* err, uint64_t timeout_ns, cudaStream_t s);
 
+// Resident pool CTAs per SM when each keeps smem_vec_bytes of vectors on chip.
+template <class MatT, class VecT>
+int pool_blocks_per_sm(size_t smem_vec_bytes);
+
 // Solve launch; cooperative when plan.group_blocks > 0.
 template <class MatT, class VecT>
 cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan, int grid,
                          cudaStream_t s);
+
+// Setup of count instances in one launch (one CTA per instance at a time).
+template <class MatT, class VecT>
+cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, int* next, int32_t* err,
+                              uint64_t timeout_ns, cudaStream_t s);
+
+struct FillDesc;
+template <class MatT>
+cudaError_t launch_sell_fill_batch(const FillDesc* d, int count, cudaStream_t s);
 
 // Copy scaled CSR values into SELL slice order (one instantiation per value type).
 template <class MatT>

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -67,9 +69,13 @@ struct Carver {
   }
 };
 
-void carve(pdhcg_problem* P, Carver& cv) {
+// Device layout of one handle.  Everything uploaded from the host comes first
+// (one contiguous prefix, copied with a single transfer); computed and work
+// arrays follow.  With external_state the SolverState lives outside the arena.
+void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
   const size_t n = size_t(P->n), m = size_t(P->m), nq = size_t(P->nnzQ), na = size_t(P->nnzA);
   const size_t mb = mat_bytes(P->precision), vb = vec_bytes(P->precision);
+  // ---- uploaded inputs ----
   P->Qp_d = cv.take<int32_t>(n + 1);
   P->Qc_d = cv.take<int32_t>(nq);
   P->Ap_d = cv.take<int32_t>(m + 1);
@@ -79,14 +85,34 @@ void carve(pdhcg_problem* P, Carver& cv) {
   P->Qv_o = cv.take<double>(nq);
   P->Av_o = cv.take<double>(na);
   P->ATv_o = cv.take<double>(na);
-  P->Qs = cv.take_bytes(nq, mb);
-  P->As = cv.take_bytes(na, mb);
-  P->ATs = cv.take_bytes(na, mb);
   P->c_o = cv.take<double>(n);
   P->lv_o = cv.take<double>(n);
   P->uv_o = cv.take<double>(n);
   P->lc_o = cv.take<double>(m);
   P->uc_o = cv.take<double>(m);
+  P->vtype = cv.take<int8_t>(n);
+  P->ctype = cv.take<int8_t>(m);
+  P->v_perm = cv.take<int32_t>(P->vsell.perm.size());
+  P->v_longs = cv.take<int32_t>(P->vsell.longs.size());
+  P->v_huges = cv.take<int32_t>(P->vsell.huges.size());
+  P->c_perm = cv.take<int32_t>(P->csell.perm.size());
+  P->c_longs = cv.take<int32_t>(P->csell.longs.size());
+  P->c_huges = cv.take<int32_t>(P->csell.huges.size());
+  P->sATp = cv.take<int64_t>(P->vsell.ptr[0].size());
+  P->sQp = cv.take<int64_t>(P->vsell.ptr[1].size());
+  P->sAp = cv.take<int64_t>(P->csell.ptr[0].size());
+  P->sATc = cv.take<int32_t>(P->vsell_cols[0] + 16);
+  P->sQc = cv.take<int32_t>(P->vsell_cols[1] + 16);
+  P->sAc = cv.take<int32_t>(P->csell_cols + 16);
+  if (!external_state) P->st = cv.take<SolverState>(1);
+  P->input_bytes = (cv.off + 255) & ~size_t(255);
+  // ---- computed on the device ----
+  P->Qs = cv.take_bytes(nq, mb);
+  P->As = cv.take_bytes(na, mb);
+  P->ATs = cv.take_bytes(na, mb);
+  P->sATv = cv.take_bytes(P->vsell_cols[0] + 16, mb);
+  P->sQv = cv.take_bytes(P->vsell_cols[1] + 16, mb);
+  P->sAv = cv.take_bytes(P->csell_cols + 16, mb);
   P->D = cv.take<double>(n);
   P->E = cv.take<double>(m);
   P->Dn = cv.take<double>(n);
@@ -100,8 +126,6 @@ void carve(pdhcg_problem* P, Carver& cv) {
   P->qdiag = cv.take_bytes(n, vb);
   P->lc = cv.take_bytes(m, vb);
   P->uc = cv.take_bytes(m, vb);
-  P->vtype = cv.take<int8_t>(n);
-  P->ctype = cv.take<int8_t>(m);
   void** nvecs[] = {&P->xb0, &P->xb1, &P->xT, &P->xa, &P->r, &P->p0, &P->p1, &P->q,
                     &P->bv, &P->grad, &P->gprev, &P->xprev, &P->xbar};
   for (void** pp : nvecs) *pp = cv.take_bytes(n, vb);
@@ -111,28 +135,54 @@ void carve(pdhcg_problem* P, Carver& cv) {
   P->y_stage = cv.take<double>(m);
   P->x_init_stage = cv.take<double>(n);
   P->y_init_stage = cv.take<double>(m);
-  P->st = cv.take<SolverState>(1);
   P->inst_d = cv.take_bytes(1, sizeof(Inst<double, double>));
   P->plan_i32 = cv.take<int32_t>(16);
   P->bar = static_cast<unsigned long long*>(cv.take_bytes(kBarBytes, 1));
   P->part_off = cv.take<int64_t>(1);
   P->part = cv.take<double>(size_t(2) * kSlots * size_t(std::max(P->max_blk, 1)));
-  // SELL layouts (+ 64 bytes of tail padding each)
-  P->v_perm = cv.take<int32_t>(P->vsell.perm.size());
-  P->v_longs = cv.take<int32_t>(P->vsell.longs.size());
-  P->v_huges = cv.take<int32_t>(P->vsell.huges.size());
-  P->c_perm = cv.take<int32_t>(P->csell.perm.size());
-  P->c_longs = cv.take<int32_t>(P->csell.longs.size());
-  P->c_huges = cv.take<int32_t>(P->csell.huges.size());
-  P->sATp = cv.take<int64_t>(P->vsell.ptr[0].size());
-  P->sQp = cv.take<int64_t>(P->vsell.ptr[1].size());
-  P->sAp = cv.take<int64_t>(P->csell.ptr[0].size());
-  P->sATc = cv.take<int32_t>(P->vsell.col[0].size() + 16);
-  P->sQc = cv.take<int32_t>(P->vsell.col[1].size() + 16);
-  P->sAc = cv.take<int32_t>(P->csell.col[0].size() + 16);
-  P->sATv = cv.take_bytes(P->vsell.col[0].size() + 16, mb);
-  P->sQv = cv.take_bytes(P->vsell.col[1].size() + 16, mb);
-  P->sAv = cv.take_bytes(P->csell.col[0].size() + 16, mb);
+}
+
+// Copy the uploaded inputs of P into a host staging image of its arena prefix.
+void pack_inputs(const pdhcg_problem* P, const HostQP& h, char* stage) {
+  const char* base = static_cast<const char*>(P->arena);
+  auto put = [&](const void* dst, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(stage + (static_cast<const char*>(dst) - base), src, bytes);
+  };
+  const size_t n = size_t(h.n), m = size_t(h.m);
+  put(P->Qp_d, h.Qp.data(), sizeof(int32_t) * (n + 1));
+  put(P->Qc_d, h.Qc.data(), sizeof(int32_t) * h.Qc.size());
+  put(P->Ap_d, h.Ap.data(), sizeof(int32_t) * (m + 1));
+  put(P->Ac_d, h.Ac.data(), sizeof(int32_t) * h.Ac.size());
+  put(P->ATp_d, h.ATp.data(), sizeof(int32_t) * (n + 1));
+  put(P->ATc_d, h.ATc.data(), sizeof(int32_t) * h.ATc.size());
+  put(P->Qv_o, h.Qv.data(), sizeof(double) * h.Qv.size());
+  put(P->Av_o, h.Av.data(), sizeof(double) * h.Av.size());
+  put(P->ATv_o, h.ATv.data(), sizeof(double) * h.ATv.size());
+  put(P->c_o, h.c.data(), sizeof(double) * n);
+  put(P->lv_o, h.lv.data(), sizeof(double) * n);
+  put(P->uv_o, h.uv.data(), sizeof(double) * n);
+  put(P->lc_o, h.lc.data(), sizeof(double) * m);
+  put(P->uc_o, h.uc.data(), sizeof(double) * m);
+  put(P->vtype, h.vtype.data(), n);
+  put(P->ctype, h.ctype.data(), m);
+  put(P->v_perm, P->vsell.perm.data(), sizeof(int32_t) * P->vsell.perm.size());
+  put(P->v_longs, P->vsell.longs.data(), sizeof(int32_t) * P->vsell.longs.size());
+  put(P->v_huges, P->vsell.huges.data(), sizeof(int32_t) * P->vsell.huges.size());
+  put(P->c_perm, P->csell.perm.data(), sizeof(int32_t) * P->csell.perm.size());
+  put(P->c_longs, P->csell.longs.data(), sizeof(int32_t) * P->csell.longs.size());
+  put(P->c_huges, P->csell.huges.data(), sizeof(int32_t) * P->csell.huges.size());
+  put(P->sATp, P->vsell.ptr[0].data(), sizeof(int64_t) * P->vsell.ptr[0].size());
+  put(P->sQp, P->vsell.ptr[1].data(), sizeof(int64_t) * P->vsell.ptr[1].size());
+  put(P->sAp, P->csell.ptr[0].data(), sizeof(int64_t) * P->csell.ptr[0].size());
+  put(P->sATc, P->vsell.col[0].data(), sizeof(int32_t) * P->vsell.col[0].size());
+  put(P->sQc, P->vsell.col[1].data(), sizeof(int32_t) * P->vsell.col[1].size());
+  put(P->sAc, P->csell.col[0].data(), sizeof(int32_t) * P->csell.col[0].size());
+  if (static_cast<const char*>(static_cast<const void*>(P->st)) >= base &&
+      static_cast<const char*>(static_cast<const void*>(P->st)) < base + P->input_bytes) {
+    SolverState S{};
+    S.method = P->method;
+    put(P->st, &S, sizeof(S));
+  }
 }
 
 int lanes_for(double avg) {
@@ -398,11 +448,67 @@ int max_group_blocks(int precision) {
   return std::min(kl.max_coresident_group, kl.max_coresident_setup);
 }
 
+// Largest per-instance vector footprint a pool CTA keeps in shared memory.
+constexpr size_t kSmemVecBudget = 110 * 1024;
+
+size_t smem_need(const pdhcg_problem* P) {
+  return smem_vector_bytes(P->n, P->m, P->method, vec_bytes(P->precision));
+}
+
 int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
   if (P->prm.group_blocks > 0) return std::min(P->prm.group_blocks, maxblk);
   const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ : 0) + 2 * P->nnzA + P->n + P->m;
   if (work < 150000) return 1;
   return int(std::max<int64_t>(2, std::min<int64_t>(maxblk, work / 8192)));
+}
+
+template <class M, class V>
+SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) {
+  SetupArgs<M, V> a{};
+  a.n = P->n;
+  a.m = P->m;
+  a.has_q = P->has_q ? 1 : 0;
+  a.ruiz_iters = P->prm.ruiz_iters;
+  a.power_max_iter = P->prm.power_max_iter;
+  a.lanes_var = P->lanes_var;
+  a.lanes_con = P->lanes_con;
+  a.power_tol = P->prm.power_tol;
+  a.eta_override = P->prm.eta_override;
+  a.omega0_override = P->prm.omega0_override;
+  a.Qp = P->Qp_d;
+  a.Qc = P->Qc_d;
+  a.Ap = P->Ap_d;
+  a.Ac = P->Ac_d;
+  a.ATp = P->ATp_d;
+  a.ATc = P->ATc_d;
+  a.Qv_o = P->Qv_o;
+  a.Av_o = P->Av_o;
+  a.ATv_o = P->ATv_o;
+  a.c_o = P->c_o;
+  a.lv_o = P->lv_o;
+  a.uv_o = P->uv_o;
+  a.lc_o = P->lc_o;
+  a.uc_o = P->uc_o;
+  a.var_part = ps ? ps->v_even : nullptr;
+  a.con_part = ps ? ps->c_even : nullptr;
+  a.D = P->D;
+  a.E = P->E;
+  a.Dn = P->Dn;
+  a.En = P->En;
+  a.pv = P->pv;
+  a.pw = P->pw;
+  a.pt = P->pt;
+  a.Qs = static_cast<M*>(P->Qs);
+  a.As = static_cast<M*>(P->As);
+  a.ATs = static_cast<M*>(P->ATs);
+  a.c = static_cast<V*>(P->c);
+  a.lv = static_cast<V*>(P->lv);
+  a.uv = static_cast<V*>(P->uv);
+  a.lc = static_cast<V*>(P->lc);
+  a.uc = static_cast<V*>(P->uc);
+  a.qdiag = static_cast<V*>(P->qdiag);
+  a.st = P->st;
+  return a;
 }
 
 int run_setup(pdhcg_problem* P) {
@@ -417,50 +523,7 @@ int run_setup(pdhcg_problem* P) {
   return dispatch_precision(P->precision, [&](auto tag) {
     using M = typename decltype(tag)::Mat;
     using V = typename decltype(tag)::Vec;
-    SetupArgs<M, V> a{};
-    a.n = P->n;
-    a.m = P->m;
-    a.has_q = P->has_q ? 1 : 0;
-    a.ruiz_iters = P->prm.ruiz_iters;
-    a.power_max_iter = P->prm.power_max_iter;
-    a.lanes_var = P->lanes_var;
-    a.lanes_con = P->lanes_con;
-    a.power_tol = P->prm.power_tol;
-    a.eta_override = P->prm.eta_override;
-    a.omega0_override = P->prm.omega0_override;
-    a.Qp = P->Qp_d;
-    a.Qc = P->Qc_d;
-    a.Ap = P->Ap_d;
-    a.Ac = P->Ac_d;
-    a.ATp = P->ATp_d;
-    a.ATc = P->ATc_d;
-    a.Qv_o = P->Qv_o;
-    a.Av_o = P->Av_o;
-    a.ATv_o = P->ATv_o;
-    a.c_o = P->c_o;
-    a.lv_o = P->lv_o;
-    a.uv_o = P->uv_o;
-    a.lc_o = P->lc_o;
-    a.uc_o = P->uc_o;
-    a.var_part = ps ? ps->v_even : nullptr;
-    a.con_part = ps ? ps->c_even : nullptr;
-    a.D = P->D;
-    a.E = P->E;
-    a.Dn = P->Dn;
-    a.En = P->En;
-    a.pv = P->pv;
-    a.pw = P->pw;
-    a.pt = P->pt;
-    a.Qs = static_cast<M*>(P->Qs);
-    a.As = static_cast<M*>(P->As);
-    a.ATs = static_cast<M*>(P->ATs);
-    a.c = static_cast<V*>(P->c);
-    a.lv = static_cast<V*>(P->lv);
-    a.uv = static_cast<V*>(P->uv);
-    a.lc = static_cast<V*>(P->lc);
-    a.uc = static_cast<V*>(P->uc);
-    a.qdiag = static_cast<V*>(P->qdiag);
-    a.st = P->st;
+    SetupArgs<M, V> a = make_setup_args<M, V>(P, ps);
     const uint64_t tmo = uint64_t(std::max(P->prm.device_timeout_ms, 1)) * 1000000ull;
     cudaError_t e = launch_setup<M, V>(a, nblk, P->bar, P->part, P->plan_i32 + 5, tmo, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "setup launch");
@@ -540,6 +603,8 @@ int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_re
       plan.npool = 1;
       plan.pool_inst = P->plan_i32 + 3;
       plan.pool_next = P->plan_i32 + 4;
+      const size_t need = smem_need(P);
+      plan.smem_vec_bytes = need <= kSmemVecBudget ? int64_t(need) : 0;
     }
     cudaError_t e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(P->inst_d), plan, grid, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "solve launch");
@@ -612,32 +677,28 @@ static int check_params(const pdhcg_params* p) {
   return PDHCG_OK;
 }
 
-int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
-                 const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
-                 void* cuda_stream, pdhcg_t** out) {
-  if (!out) {
-    set_error("out is NULL");
-    return PDHCG_E_INVALID;
-  }
-  *out = nullptr;
-  pdhcg_params prm;
-  if (params) {
-    int rc = check_params(params);
-    if (rc) return rc;
-    prm = *params;
-  } else {
-    pdhcg_default_params(&prm);
-  }
-  HostQP h;
-  int rc = build_host_qp(Q, A, c, lc, uc, lv, uv, &h);
+}  // extern "C"
+
+namespace pdhcg {
+
+struct CreateInput {
+  const pdhcg_csr *Q, *A;
+  const double *c, *lc, *uc, *lv, *uv;
+};
+
+// Host side of creation: validate, canonicalise, choose the inner solver, build
+// the SELL layouts.  No device work.
+int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream, pdhcg_problem** out,
+                    HostQP* h) {
+  int rc = build_host_qp(in.Q, in.A, in.c, in.lc, in.uc, in.lv, in.uv, h);
   if (rc) return rc;
   int method = prm.inner;
-  if (method == PDHCG_INNER_AUTO) method = h.diag_q ? PDHCG_INNER_DIAG : (h.any_box ? PDHCG_INNER_BB : PDHCG_INNER_CG);
-  if (method == PDHCG_INNER_DIAG && !h.diag_q) {
+  if (method == PDHCG_INNER_AUTO) method = h->diag_q ? PDHCG_INNER_DIAG : (h->any_box ? PDHCG_INNER_BB : PDHCG_INNER_CG);
+  if (method == PDHCG_INNER_DIAG && !h->diag_q) {
     set_error("inner = DIAG needs a diagonal Q");
     return PDHCG_E_INVALID;
   }
-  if (method == PDHCG_INNER_CG && h.any_box) {
+  if (method == PDHCG_INNER_CG && h->any_box) {
     set_error("inner = CG needs every variable free (no finite bound)");
     return PDHCG_E_INVALID;
   }
@@ -646,16 +707,15 @@ int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const 
   P->prm = prm;
   P->precision = prm.precision;
   P->method = method;
-  P->n = h.n;
-  P->m = h.m;
-  P->nnzQ = int64_t(h.Qc.size());
-  P->nnzA = int64_t(h.Ac.size());
-  P->has_q = h.has_q;
-  P->stream = static_cast<cudaStream_t>(cuda_stream);
-  cudaGetDevice(&P->device);
-  P->Qp = h.Qp;
-  P->Ap = h.Ap;
-  P->ATp = h.ATp;
+  P->n = h->n;
+  P->m = h->m;
+  P->nnzQ = int64_t(h->Qc.size());
+  P->nnzA = int64_t(h->Ac.size());
+  P->has_q = h->has_q;
+  P->stream = static_cast<cudaStream_t>(stream);
+  P->Qp = h->Qp;
+  P->Ap = h->Ap;
+  P->ATp = h->ATp;
   {
     const double avg_q = P->n ? double(P->nnzQ) / P->n : 0.0;
     const double avg_at = P->n ? double(P->nnzA) / P->n : 0.0;
@@ -664,96 +724,225 @@ int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const 
     P->lanes_con = lanes_for(avg_a);
     if (prm.lanes_override) P->lanes_var = P->lanes_con = prm.lanes_override;
   }
-  {
-    const std::vector<int32_t>* vrp[2] = {&h.ATp, &h.Qp};
-    const std::vector<int32_t>* vci[2] = {&h.ATc, &h.Qc};
-    build_sell(h.n, h.has_q ? 2 : 1, vrp, vci, &P->vsell);
-    const std::vector<int32_t>* crp[2] = {&h.Ap, nullptr};
-    const std::vector<int32_t>* cci[2] = {&h.Ac, nullptr};
-    build_sell(h.m, 1, crp, cci, &P->csell);
-  }
-  int mb = max_group_blocks(P->precision);
-  if (mb < 0) {
-    delete P;
-    return mb;
-  }
-  P->max_blk = std::max(mb, 1);
-  Carver sizing;
-  carve(P, sizing);
-  P->arena_bytes = sizing.off + 256;
-  cudaError_t e = cudaMalloc(&P->arena, P->arena_bytes);
-  if (e != cudaSuccess) {
-    delete P;
-    return cuda_fail(e, "cudaMalloc(arena)");
-  }
-  Carver real;
-  real.base = static_cast<char*>(P->arena);
-  carve(P, real);
-  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
-    if (bytes == 0) return cudaSuccess;
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, P->stream);
-  };
-  const size_t n = size_t(h.n), m = size_t(h.m);
-  cudaError_t es[] = {
-      up(P->Qp_d, h.Qp.data(), sizeof(int32_t) * (n + 1)),
-      up(P->Qc_d, h.Qc.data(), sizeof(int32_t) * h.Qc.size()),
-      up(P->Ap_d, h.Ap.data(), sizeof(int32_t) * (m + 1)),
-      up(P->Ac_d, h.Ac.data(), sizeof(int32_t) * h.Ac.size()),
-      up(P->ATp_d, h.ATp.data(), sizeof(int32_t) * (n + 1)),
-      up(P->ATc_d, h.ATc.data(), sizeof(int32_t) * h.ATc.size()),
-      up(P->Qv_o, h.Qv.data(), sizeof(double) * h.Qv.size()),
-      up(P->Av_o, h.Av.data(), sizeof(double) * h.Av.size()),
-      up(P->ATv_o, h.ATv.data(), sizeof(double) * h.ATv.size()),
-      up(P->c_o, h.c.data(), sizeof(double) * n),
-      up(P->lv_o, h.lv.data(), sizeof(double) * n),
-      up(P->uv_o, h.uv.data(), sizeof(double) * n),
-      up(P->lc_o, h.lc.data(), sizeof(double) * m),
-      up(P->uc_o, h.uc.data(), sizeof(double) * m),
-      up(P->vtype, h.vtype.data(), n),
-      up(P->ctype, h.ctype.data(), m),
-      up(P->v_perm, P->vsell.perm.data(), sizeof(int32_t) * P->vsell.perm.size()),
-      up(P->v_longs, P->vsell.longs.data(), sizeof(int32_t) * P->vsell.longs.size()),
-      up(P->v_huges, P->vsell.huges.data(), sizeof(int32_t) * P->vsell.huges.size()),
-      up(P->c_perm, P->csell.perm.data(), sizeof(int32_t) * P->csell.perm.size()),
-      up(P->c_longs, P->csell.longs.data(), sizeof(int32_t) * P->csell.longs.size()),
-      up(P->c_huges, P->csell.huges.data(), sizeof(int32_t) * P->csell.huges.size()),
-      up(P->sATp, P->vsell.ptr[0].data(), sizeof(int64_t) * P->vsell.ptr[0].size()),
-      up(P->sQp, P->vsell.ptr[1].data(), sizeof(int64_t) * P->vsell.ptr[1].size()),
-      up(P->sAp, P->csell.ptr[0].data(), sizeof(int64_t) * P->csell.ptr[0].size()),
-      up(P->sATc, P->vsell.col[0].data(), sizeof(int32_t) * P->vsell.col[0].size()),
-      up(P->sQc, P->vsell.col[1].data(), sizeof(int32_t) * P->vsell.col[1].size()),
-      up(P->sAc, P->csell.col[0].data(), sizeof(int32_t) * P->csell.col[0].size()),
-  };
-  for (cudaError_t x : es)
-    if (x != cudaSuccess) {
-      int r = cuda_fail(x, "upload");
-      pdhcg_destroy(P);
-      return r;
-    }
-  {
-    SolverState S{};
-    S.method = method;
-    cudaError_t x = cudaMemcpyAsync(P->st, &S, sizeof(S), cudaMemcpyHostToDevice, P->stream);
-    if (x == cudaSuccess) x = cudaStreamSynchronize(P->stream);
-    if (x != cudaSuccess) {
-      int r = cuda_fail(x, "upload");
-      pdhcg_destroy(P);
-      return r;
-    }
-  }
-  rc = run_setup(P);
-  if (rc == PDHCG_OK) rc = fill_sell(P);
-  if (rc) {
-    pdhcg_destroy(P);
-    return rc;
-  }
-  // the integer SELL columns are on the device now; keep only what partitioning needs
-  for (int k = 0; k < 2; ++k) {
-    std::vector<int32_t>().swap(P->vsell.col[k]);
-    std::vector<int32_t>().swap(P->csell.col[k]);
-  }
+  const std::vector<int32_t>* vrp[2] = {&h->ATp, &h->Qp};
+  const std::vector<int32_t>* vci[2] = {&h->ATc, &h->Qc};
+  build_sell(h->n, h->has_q ? 2 : 1, vrp, vci, &P->vsell);
+  const std::vector<int32_t>* crp[2] = {&h->Ap, nullptr};
+  const std::vector<int32_t>* cci[2] = {&h->Ac, nullptr};
+  build_sell(h->m, 1, crp, cci, &P->csell);
+  P->vsell_cols[0] = P->vsell.col[0].size();
+  P->vsell_cols[1] = P->vsell.col[1].size();
+  P->csell_cols = P->csell.col[0].size();
   *out = P;
   return PDHCG_OK;
+}
+
+int cached_max_group_blocks(int precision) {
+  static std::mutex mu;
+  static int cache[3][64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && cache[precision][dev] > 0) return cache[precision][dev];
+  const int mb = max_group_blocks(precision);
+  if (mb > 0 && dev >= 0 && dev < 64) cache[precision][dev] = mb;
+  return mb;
+}
+
+// Create count handles: one device allocation, one staging transfer per handle,
+// and (count > 1) one pooled setup launch.
+int create_impl(int count, const CreateInput* in, const pdhcg_params* params, void* stream,
+                pdhcg_t** out) {
+  pdhcg_params prm;
+  if (params) {
+    int rc = check_params(params);
+    if (rc) return rc;
+    prm = *params;
+  } else {
+    pdhcg_default_params(&prm);
+  }
+  std::vector<pdhcg_problem*> P(static_cast<size_t>(count), nullptr);
+  std::vector<HostQP> H(static_cast<size_t>(count));
+  std::vector<int> rcs(static_cast<size_t>(count), PDHCG_OK);
+  std::vector<std::string> errs(static_cast<size_t>(count));
+  {
+    const int nth = std::max(1, std::min<int>(count, int(std::thread::hardware_concurrency())));
+    std::atomic<int> nextq(0);
+    auto work = [&]() {
+      for (int i = nextq++; i < count; i = nextq++) {
+        rcs[size_t(i)] = prepare_problem(in[i], prm, stream, &P[size_t(i)], &H[size_t(i)]);
+        if (rcs[size_t(i)]) errs[size_t(i)] = last_error_cstr();
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nth; ++t) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+  }
+  auto cleanup = [&]() {
+    for (auto* q : P) delete q;
+  };
+  for (int i = 0; i < count; ++i)
+    if (rcs[size_t(i)]) {
+      set_error("problem " + std::to_string(i) + ": " + errs[size_t(i)]);
+      cleanup();
+      return rcs[size_t(i)];
+    }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int mb = cached_max_group_blocks(prm.precision);
+  if (mb < 0) {
+    cleanup();
+    return mb;
+  }
+  const bool batch = count > 1;
+  // sizes and offsets inside one allocation
+  std::vector<size_t> off(static_cast<size_t>(count));
+  size_t total = batch ? ((sizeof(SolverState) * size_t(count) + 255) & ~size_t(255)) : 0;
+  size_t stage_total = 0;
+  for (int i = 0; i < count; ++i) {
+    P[size_t(i)]->device = dev;
+    P[size_t(i)]->max_blk = batch ? 1 : std::max(mb, 1);
+    Carver sizing;
+    carve(P[size_t(i)], sizing, batch);
+    P[size_t(i)]->arena_bytes = (sizing.off + 255) & ~size_t(255);
+    off[size_t(i)] = total;
+    total += P[size_t(i)]->arena_bytes;
+    stage_total += P[size_t(i)]->input_bytes;
+  }
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, total);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMalloc(arena)");
+  }
+  std::shared_ptr<void> owner(raw, [](void* q) { cudaFree(q); });
+  SolverState* states = batch ? static_cast<SolverState*>(raw) : nullptr;
+  for (int i = 0; i < count; ++i) {
+    pdhcg_problem* Pi = P[size_t(i)];
+    Pi->arena = static_cast<char*>(raw) + off[size_t(i)];
+    Pi->arena_owner = owner;
+    if (batch) Pi->st = states + i;
+    Carver real;
+    real.base = static_cast<char*>(Pi->arena);
+    carve(Pi, real, batch);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // stage the inputs in pinned memory and copy each handle's prefix
+  void* stage = nullptr;
+  e = cudaMallocHost(&stage, std::max<size_t>(stage_total, 1));
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMallocHost(stage)");
+  }
+  size_t soff = 0;
+  std::vector<SolverState> hstates(batch ? size_t(count) : 0);
+  for (int i = 0; i < count; ++i) {
+    pdhcg_problem* Pi = P[size_t(i)];
+    char* dst = static_cast<char*>(stage) + soff;
+    pack_inputs(Pi, H[size_t(i)], dst);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Pi->arena, dst, Pi->input_bytes, cudaMemcpyHostToDevice, s);
+    soff += Pi->input_bytes;
+    if (batch) {
+      hstates[size_t(i)] = SolverState{};
+      hstates[size_t(i)].method = Pi->method;
+    }
+  }
+  if (batch && e == cudaSuccess)
+    e = cudaMemcpyAsync(states, hstates.data(), sizeof(SolverState) * size_t(count), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeHost(stage);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "upload");
+  }
+  int rc = PDHCG_OK;
+  if (!batch) {
+    rc = run_setup(P[0]);
+    if (rc == PDHCG_OK) rc = fill_sell(P[0]);
+  } else {
+    rc = dispatch_precision(prm.precision, [&](auto tag) -> int {
+      using M = typename decltype(tag)::Mat;
+      using V = typename decltype(tag)::Vec;
+      std::vector<SetupArgs<M, V>> args(static_cast<size_t>(count));
+      std::vector<FillDesc> fills;
+      fills.reserve(size_t(count) * 3);
+      for (int i = 0; i < count; ++i) {
+        const pdhcg_problem* Pi = P[size_t(i)];
+        args[size_t(i)] = make_setup_args<M, V>(Pi, nullptr);
+        fills.push_back(FillDesc{Pi->vsell.nslices, Pi->v_perm, Pi->sATp, Pi->ATp_d, Pi->ATs, Pi->sATv});
+        if (Pi->has_q) fills.push_back(FillDesc{Pi->vsell.nslices, Pi->v_perm, Pi->sQp, Pi->Qp_d, Pi->Qs, Pi->sQv});
+        fills.push_back(FillDesc{Pi->csell.nslices, Pi->c_perm, Pi->sAp, Pi->Ap_d, Pi->As, Pi->sAv});
+      }
+      const size_t abytes = sizeof(SetupArgs<M, V>) * args.size(), fbytes = sizeof(FillDesc) * fills.size();
+      char* dscratch = nullptr;
+      CK(cudaMalloc(&dscratch, abytes + fbytes + 256));
+      std::unique_ptr<char, void (*)(char*)> guard(dscratch, [](char* q) { cudaFree(q); });
+      int32_t* ctl = reinterpret_cast<int32_t*>(dscratch + abytes + fbytes);
+      CK(cudaMemcpyAsync(dscratch, args.data(), abytes, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(dscratch + abytes, fills.data(), fbytes, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(ctl, 0, 2 * sizeof(int32_t), s));
+      const uint64_t tmo = uint64_t(std::max(prm.device_timeout_ms, 1)) * 1000000ull;
+      cudaError_t e2 = launch_setup_pool<M, V>(reinterpret_cast<SetupArgs<M, V>*>(dscratch), count, ctl,
+                                               ctl + 1, tmo, s);
+      if (e2 == cudaSuccess)
+        e2 = launch_sell_fill_batch<M>(reinterpret_cast<FillDesc*>(dscratch + abytes), int(fills.size()), s);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "batched setup");
+      CK(cudaMemcpyAsync(hstates.data(), states, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
+      int32_t err = 0;
+      CK(cudaMemcpyAsync(&err, ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (err) {
+        set_error("batched setup: a bounded device wait gave up");
+        return PDHCG_E_DEVICE_TIMEOUT;
+      }
+      for (int i = 0; i < count; ++i) P[size_t(i)]->setup_state = hstates[size_t(i)];
+      return PDHCG_OK;
+    });
+  }
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  for (int i = 0; i < count; ++i) {
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int32_t>().swap(P[size_t(i)]->vsell.col[k]);
+      std::vector<int32_t>().swap(P[size_t(i)]->csell.col[k]);
+    }
+    out[i] = P[size_t(i)];
+  }
+  return PDHCG_OK;
+}
+
+}  // namespace pdhcg
+
+extern "C" {
+
+int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
+                 const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
+                 void* cuda_stream, pdhcg_t** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return PDHCG_E_INVALID;
+  }
+  *out = nullptr;
+  CreateInput in{Q, A, c, lc, uc, lv, uv};
+  return create_impl(1, &in, params, cuda_stream, out);
+}
+
+int pdhcg_create_batch(int count, const pdhcg_problem_data* problems, const pdhcg_params* params,
+                       void* cuda_stream, pdhcg_t** out) {
+  if (count < 0 || (count > 0 && (!problems || !out))) {
+    set_error("create_batch: bad arguments");
+    return PDHCG_E_INVALID;
+  }
+  if (count == 0) return PDHCG_OK;
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  std::vector<CreateInput> in(static_cast<size_t>(count));
+  for (int i = 0; i < count; ++i)
+    in[size_t(i)] = CreateInput{problems[i].Q, problems[i].A, problems[i].c, problems[i].lc,
+                                problems[i].uc, problems[i].lv, problems[i].uv};
+  return create_impl(count, in.data(), params, cuda_stream, out);
 }
 
 int pdhcg_solve(pdhcg_t* P, const double* x0, const double* y0, pdhcg_result* res, double* x_out,
@@ -818,7 +1007,7 @@ void pdhcg_destroy(pdhcg_t* P) {
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (auto& kv : P->partitions) cudaFree(kv.second.d_buf);
-  if (P->arena) cudaFree(P->arena);
+  P->arena_owner.reset();  // frees the allocation with its last handle
   delete P;
 }
 
@@ -920,7 +1109,7 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
   std::vector<SolverState> hs(static_cast<size_t>(count));
   for (int i = 0; i < count; ++i) hs[i] = initial_state(probs[i]);
   // longest-processing-time-first order for the work queue
-  std::vector<int32_t> order(size_t(count) + 8, 0);
+  std::vector<int32_t> order(static_cast<size_t>(count) + 8, 0);
   std::vector<int64_t> work(static_cast<size_t>(count));
   for (int i = 0; i < count; ++i)
     work[i] = (probs[i]->method != PDHCG_INNER_DIAG ? 4 * probs[i]->nnzQ : 0) + 2 * probs[i]->nnzA +
@@ -955,7 +1144,17 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
     plan.err = d_i32 + count + 1;
     plan.iter_budget = iter_budget;
     plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
-    const int grid = std::max(1, std::min(count, kl.max_coresident_group));
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      const size_t b = smem_need(probs[i]);
+      if (b <= kSmemVecBudget) need = std::max(need, b);
+    }
+    plan.smem_vec_bytes = int64_t(need);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    const int grid = std::max(1, std::min(count, per_sm * sms));
     e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     CK(cudaMemcpyAsync(hs.data(), d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));

@@ -121,6 +121,14 @@ struct Inst {
   DevParams prm;
 };
 
+// Shared-memory bytes the vectors of an (n, m) instance take when a pool CTA
+// keeps them on chip: 9 n-vectors (+4 for CG / BB), 6 m-vectors, bound codes.
+inline __host__ __device__ size_t smem_vector_bytes(int n, int m, int method, size_t vec_bytes) {
+  const size_t nv = 9 + ((method == 2 || method == 3) ? 4 : 0);
+  auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  return nv * al(size_t(n) * vec_bytes) + 6 * al(size_t(m) * vec_bytes) + al(size_t(n)) + al(size_t(m));
+}
+
 // How one launch of the solve kernel maps CTAs to instances.
 struct LaunchPlan {
   // Multi-CTA groups occupy CTAs [0, group_blocks); group g owns
@@ -140,6 +148,9 @@ struct LaunchPlan {
   // Slice limits for the serving loop: a solve pauses at the first check
   // boundary after it has done iter_budget steps in this launch (0 = none).
   int64_t iter_budget = 0;
+  // Pool CTAs copy an instance's vectors into dynamic shared memory when they
+  // fit in this many bytes (0 = never); see smem_vector_bytes().
+  int64_t smem_vec_bytes = 0;
   uint64_t timeout_ns = 8000000000ull;  // bound on any device wait
   int32_t* err = nullptr;               // set to 1 when a bounded wait gave up
 };

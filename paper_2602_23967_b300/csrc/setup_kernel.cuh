@@ -231,4 +231,65 @@ __global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsi
   setup_instance<BS>(g, a);
 }
 
+// Setup of many instances in one launch: each CTA takes the next instance from a
+// queue and sets it up alone.
+template <int BS, class MatT, class VecT>
+__global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, VecT>* args, int count,
+                                                        int* next, int32_t* err, uint64_t timeout_ns) {
+  __shared__ double sm_warp[2 * (BS / 32) * kSlots];
+  __shared__ double sm_tot[2 * kSlots];
+  __shared__ int sm_flag;
+  __shared__ int sm_idx;
+  Group<BS> g;
+  g.nblk = 1;
+  g.rank = 0;
+  g.bar32 = nullptr;
+  g.part = nullptr;
+  g.sm_warp = sm_warp;
+  g.sm_tot = sm_tot;
+  g.sm_flag = &sm_flag;
+  g.err = err;
+  g.timeout_ns = timeout_ns;
+  g.failed = false;
+  if (threadIdx.x == 0) sm_flag = 0;
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) sm_idx = atomicAdd(next, 1);
+    __syncthreads();
+    const int idx = sm_idx;
+    __syncthreads();
+    if (idx >= count) break;
+    g.epoch = 0;
+    setup_instance<BS>(g, args[idx]);
+    __syncthreads();
+  }
+}
+
+// SELL values of many matrices: one CTA per descriptor, one warp per slice.
+struct FillDesc {
+  int nslices;
+  const int32_t* perm;
+  const int64_t* sptr;
+  const int32_t* rowptr;
+  const void* csr_val;
+  void* sell_val;
+};
+template <class MatT>
+__global__ void sell_fill_batch_kernel(const FillDesc* d, int count) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const FillDesc f = d[i];
+    const MatT* csr = static_cast<const MatT*>(f.csr_val);
+    MatT* out = static_cast<MatT*>(f.sell_val);
+    for (int s = threadIdx.x >> 5; s < f.nslices; s += wpb) {
+      const int row = f.perm[s * 32 + lane];
+      const int64_t b = f.sptr[s];
+      const int W = int((f.sptr[s + 1] - b) >> 5);
+      const int rb = row >= 0 ? f.rowptr[row] : 0;
+      const int len = row >= 0 ? f.rowptr[row + 1] - rb : 0;
+      for (int j = 0; j < W; ++j) out[b + 32 * j + lane] = j < len ? csr[rb + j] : MatT(0);
+    }
+  }
+}
+
 }  // namespace pdhcg

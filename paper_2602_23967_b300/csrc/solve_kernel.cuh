@@ -67,12 +67,16 @@ __device__ __forceinline__ void pid_update(SolverState& S, const DevParams& P, d
   S.log_omega = lw;
 }
 
-// Accumulates device-timer intervals per category (thread 0 of the group's first CTA).
+// Accumulates device-timer intervals per category (thread 0 of the group's first
+// CTA) when built with PDHCG_PHASE_TIMERS=1; otherwise every mark is a no-op.
+#ifndef PDHCG_PHASE_TIMERS
+#define PDHCG_PHASE_TIMERS 0
+#endif
 struct PhaseClock {
   bool on;
   uint64_t last;
   __device__ __forceinline__ void mark(double* tm, int cat) {
-    if (on) {
+    if (PDHCG_PHASE_TIMERS && on) {
       const uint64_t t = globaltimer_ns();
       tm[cat] += double(t - last);
       last = t;
@@ -80,11 +84,360 @@ struct PhaseClock {
   }
 };
 
+template <int NV>
+struct Red {
+  double v[NV];
+};
+
+// Scalars of one PDHG step in the vector arithmetic type.
+template <class CT>
+struct StepScalars {
+  CT itau, isig, sig, wk, ak, th, th1;
+};
+
+// ---- Phase I: g = A^T y, b = x/tau - c - g, inner-solver start (Eq. primal_update) ----
+// returns {inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2}
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I,
-                                            const LaunchPlan& plan, const RowCtx& red) {
-  using CT = VecT;   // arithmetic type of vector updates
-  using Acc = VecT;  // SpMV accumulation type in the hot phases
+__device__ __noinline__ Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
+                                      StepScalars<VecT> sc, const RowCtx& rc) {
+  using CT = VecT;
+  using Acc = VecT;
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  VecT* __restrict__ xn = cur ? I.xb0 : I.xb1;
+  const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  const VecT* __restrict__ c = I.c;
+  const VecT* __restrict__ lv = I.lv;
+  const VecT* __restrict__ uv = I.uv;
+  const VecT* __restrict__ qd = I.qdiag;
+  const VecT* __restrict__ xa = I.xa;
+  VecT* __restrict__ xT = I.xT;
+  VecT* __restrict__ xbar = I.xbar;
+  VecT* __restrict__ rv = I.r;
+  VecT* __restrict__ grad = I.grad;
+  VecT* __restrict__ bvv = I.bv;
+  const CT itau = sc.itau, wkc = sc.wk, akc = sc.ak, th = sc.th, th1 = sc.th1;
+  DotAcc<CT> a0, a1, a2, a3;
+  space_rows<BS, LM, Acc>(
+      I.vsp, prank, src(I.ATs, I.AT, [&](int i) { return y[i]; }),
+      src(I.Qs, I.Q, [&](int k) { return x[k]; }, method != PDHCG_INNER_DIAG && I.has_q != 0), rc,
+      [&](int j, const Acc* sums) {
+        const CT xj = x[j];
+        const CT bj = xj * itau - c[j] - CT(sums[0]);
+        a1.add_prod(bj, bj);
+        if (method == PDHCG_INNER_DIAG) {
+          const CT xt = clampv(bj / (qd[j] + itau), lv[j], uv[j]);
+          const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
+          xT[j] = xt;
+          xbar[j] = CT(2) * xt - xj;
+          xn[j] = xnj;
+          a2.add_prod(xt - xj, xt - xj);
+          a3.add_prod(xnj - xj, xnj - xj);
+        } else if (method == PDHCG_INNER_CG) {
+          const CT hx = CT(sums[1]) + xj * itau;
+          const CT rj = bj - hx;
+          rv[j] = rj;
+          xT[j] = xj;
+          a0.add_prod(rj, rj);
+        } else {
+          const CT hx = CT(sums[1]) + xj * itau;
+          const CT gj = hx - bj;
+          grad[j] = gj;
+          bvv[j] = bj;
+          xT[j] = xj;
+          const CT d = xj - clampv(xj - gj, lv[j], uv[j]);
+          a0.add_prod(d, d);
+        }
+      });
+  return Red<4>{{a0.get(), a1.get(), a2.get(), a3.get()}};
+}
+
+// ---- CG Phase A: p = r + beta p_old (gathered on the fly, bit-identical to the
+// owner's write), q = H p; returns p^T q ----
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ double cg_phase_a(const Inst<MatT, VecT>& I, int prank, bool first, VecT be,
+                                          const VecT* __restrict__ pold, VecT* __restrict__ pnew, VecT itau,
+                                          const RowCtx& rc) {
+  using CT = VecT;
+  using Acc = VecT;
+  const VecT* __restrict__ rv = I.r;
+  VecT* __restrict__ qv = I.q;
+  DotAcc<CT> apq;
+  space_rows<BS, LM, Acc>(
+      I.vsp, prank,
+      src(I.Qs, I.Q, [&](int k) { return first ? rv[k] : CT(fma(be, pold[k], rv[k])); }, I.has_q != 0),
+      nosrc<MatT>(), rc, [&](int i, const Acc* sums) {
+        const CT pi = first ? rv[i] : CT(fma(be, pold[i], rv[i]));
+        pnew[i] = pi;
+        const CT qi = CT(sums[0]) + pi * itau;
+        qv[i] = qi;
+        apq.add_prod(pi, qi);
+      });
+  return apq.get();
+}
+
+// ---- CG Phase B: x += alpha p, r -= alpha q; returns r^T r ----
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ double cg_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
+                                          const VecT* __restrict__ pnew) {
+  using CT = VecT;
+  VecT* __restrict__ xT = I.xT;
+  VecT* __restrict__ rv = I.r;
+  const VecT* __restrict__ qv = I.q;
+  DotAcc<CT> arr;
+  for_elems<BS>(lo, hi, [&](int i) {
+    xT[i] = xT[i] + al * pnew[i];
+    const CT ri = rv[i] - al * qv[i];
+    rv[i] = ri;
+    arr.add_prod(ri, ri);
+  });
+  return arr.get();
+}
+
+// ---- xbar = 2 x+ - x, optionally copying x+ from another buffer into xT ----
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void write_xbar(const Inst<MatT, VecT>& I, int lo, int hi, const VecT* __restrict__ xp,
+                                        const VecT* __restrict__ x, bool copy) {
+  VecT* __restrict__ xT = I.xT;
+  VecT* __restrict__ xbar = I.xbar;
+  for_elems<BS>(lo, hi, [&](int i) {
+    const VecT xi = xp[i];
+    if (copy) xT[i] = xi;
+    xbar[i] = VecT(2) * xi - x[i];
+  });
+}
+
+// ---- BB Phase B': projected step x_new = proj(x - alpha grad) ----
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void bb_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
+                                        const VecT* __restrict__ xc, const VecT* __restrict__ gc,
+                                        VecT* __restrict__ xo) {
+  const VecT* __restrict__ lv = I.lv;
+  const VecT* __restrict__ uv = I.uv;
+  for_elems<BS>(lo, hi, [&](int i) { xo[i] = clampv(xc[i] - al * gc[i], lv[i], uv[i]); });
+}
+
+// ---- BB Phase A': gradient, BB quantities and natural residual at xc ----
+// returns {s^T s, s^T (g - g_prev), ||x - proj(x - g)||^2}
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int prank, const VecT* __restrict__ xc,
+                                          const VecT* __restrict__ xo, const VecT* __restrict__ gc,
+                                          VecT* __restrict__ gn, VecT itau, const RowCtx& rc) {
+  using CT = VecT;
+  using Acc = VecT;
+  const VecT* __restrict__ bvv = I.bv;
+  const VecT* __restrict__ lv = I.lv;
+  const VecT* __restrict__ uv = I.uv;
+  DotAcc<CT> ass, asy, anr;
+  space_rows<BS, LM, Acc>(I.vsp, prank, src(I.Qs, I.Q, [&](int k) { return xc[k]; }, I.has_q != 0),
+                          nosrc<MatT>(), rc, [&](int i, const Acc* sums) {
+                            const CT xi = xc[i];
+                            const CT gi = (CT(sums[0]) + xi * itau) - bvv[i];
+                            gn[i] = gi;
+                            const CT sv = xi - xo[i];
+                            const CT yv = gi - gc[i];
+                            ass.add_prod(sv, sv);
+                            asy.add_prod(sv, yv);
+                            const CT d = xi - clampv(xi - gi, lv[i], uv[i]);
+                            anr.add_prod(d, d);
+                          });
+  return Red<3>{{ass.get(), asy.get(), anr.get()}};
+}
+
+// ---- Phase II: A xbar, dual step (Eq. dual_update), reflected Halpern (Sec. 3.1) ----
+// returns {||y+ - y||^2, ||x+ - x||^2, ||x_new - x||^2} (the x terms only for CG / BB)
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int method, int cur, int vlo,
+                                      int vhi, StepScalars<VecT> sc, const RowCtx& rc) {
+  using CT = VecT;
+  using Acc = VecT;
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  VecT* __restrict__ xn = cur ? I.xb0 : I.xb1;
+  const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  VecT* __restrict__ yn = cur ? I.yb0 : I.yb1;
+  const VecT* __restrict__ xbar = I.xbar;
+  const VecT* __restrict__ xT = I.xT;
+  VecT* __restrict__ yT = I.yT;
+  const VecT* __restrict__ lc = I.lc;
+  const VecT* __restrict__ uc = I.uc;
+  const VecT* __restrict__ ya = I.ya;
+  const VecT* __restrict__ xa = I.xa;
+  const CT isig = sc.isig, sig = sc.sig, wkc = sc.wk, akc = sc.ak, th = sc.th, th1 = sc.th1;
+  DotAcc<CT> ady, adx, amv;
+  space_rows<BS, LM, Acc>(I.csp, prank, src(I.As, I.A, [&](int j) { return xbar[j]; }), nosrc<MatT>(), rc,
+                          [&](int i, const Acc* sums) {
+                            const CT yi = y[i];
+                            const CT v = yi * isig + CT(sums[0]);
+                            const CT yt = sig * (v - clampv(v, lc[i], uc[i]));
+                            yT[i] = yt;
+                            yn[i] = wkc * (th1 * yt - th * yi) + akc * ya[i];
+                            ady.add_prod(yt - yi, yt - yi);
+                          });
+  if (method != PDHCG_INNER_DIAG) {
+    for_elems<BS>(vlo, vhi, [&](int j) {
+      const CT xt = xT[j], xj = x[j];
+      const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
+      xn[j] = xnj;
+      adx.add_prod(xt - xj, xt - xj);
+      amv.add_prod(xnj - xj, xnj - xj);
+    });
+  }
+  return Red<3>{{ady.get(), adx.get(), amv.get()}};
+}
+
+// ---- check phase: KKT residual pieces on the original data (Sec. 4.2) and the
+// infeasibility tests' pieces (Sec. 5.1, 5.2), with Delta = T(z) - z ----
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  const VecT* __restrict__ xT = I.xT;
+  const VecT* __restrict__ yT = I.yT;
+  const VecT* __restrict__ xa = I.xa;
+  const VecT* __restrict__ ya = I.ya;
+  const VecT* __restrict__ lc = I.lc;
+  const VecT* __restrict__ uc = I.uc;
+  const VecT* __restrict__ lv = I.lv;
+  const VecT* __restrict__ uv = I.uv;
+  const VecT* __restrict__ c_s = I.c;
+  const int8_t* __restrict__ ctype = I.ctype;
+  const int8_t* __restrict__ vtype = I.vtype;
+  Red<18> cv;
+#pragma unroll
+  for (int q = 0; q < 18; ++q) cv.v[q] = 0.0;
+  space_rows<BS, LM, double>(
+      I.csp, prank,
+      src2(I.As, I.A, [&](int j) { return double(xT[j]); }, [&](int j) { return double(xT[j]) - double(x[j]); }),
+      nosrc<MatT>(), rc, [&](int i, const double* sums) {
+        const double ax = sums[0], ad = sums[1];
+        const double axu = ax / I.E[i];
+        cv.v[0] = fmax(cv.v[0], fabs(axu - clampv(axu, I.lc_o[i], I.uc_o[i])));
+        const double yu = double(yT[i]) * I.E[i];
+        cv.v[7] += support_term(yu, I.lc_o[i], I.uc_o[i]);
+        const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]);
+        cv.v[9] += support_term(ytl, double(lc[i]), double(uc[i]));
+        cv.v[13] = fmax(cv.v[13], fabs(ad - proj_recc(ad, ctype[i])));
+        const double dya = double(yT[i]) - double(ya[i]);
+        cv.v[16] += dya * dya;
+      });
+  space_rows<BS, LM, double>(
+      I.vsp, prank,
+      src2(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
+           [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
+      src2(I.Qs, I.Q, [&](int k) { return double(xT[k]); }, [&](int k) { return double(xT[k]) - double(x[k]); },
+           I.has_q != 0),
+      rc, [&](int j, const double* sums) {
+        const double aty = sums[0], atyt = sums[1], qx = sums[2], qdd = sums[3];
+        const double Dj = I.D[j];
+        const double xu = double(xT[j]) * Dj;
+        const double qxu = qx / Dj, atyu = aty / Dj;
+        const double rj = qxu + I.c_o[j] + atyu;
+        const double rh = proj_R(rj, vtype[j]);
+        cv.v[1] = fmax(cv.v[1], fabs(rj - rh));
+        cv.v[2] = fmax(cv.v[2], fabs(qxu));
+        cv.v[3] = fmax(cv.v[3], fabs(atyu));
+        cv.v[4] += xu * qxu;
+        cv.v[5] += I.c_o[j] * xu;
+        cv.v[6] += support_term(-rh, I.lv_o[j], I.uv_o[j]);
+        cv.v[8] = fmax(cv.v[8], fabs(atyt - proj_R(atyt, vtype[j])));
+        cv.v[9] += support_term(-atyt, double(lv[j]), double(uv[j]));
+        const double dx = double(xT[j]) - double(x[j]);
+        cv.v[10] = fmax(cv.v[10], fabs(dx));
+        cv.v[11] += double(c_s[j]) * dx;
+        cv.v[12] = fmax(cv.v[12], fabs(dx - proj_recc(dx, vtype[j])));
+        cv.v[14] = fmax(cv.v[14], fabs(qdd));
+        const double dxa = double(xT[j]) - double(xa[j]);
+        cv.v[15] += dxa * dxa;
+      });
+  return cv;
+}
+
+// ---- output: unscaled solution (x = D x+, y = E y+) or normalised rays ----
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ Red<2> ray_norms(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
+                                         double dn) {
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  Red<2> mx{{0.0, 0.0}};
+  for_elems<BS>(clo, chi, [&](int i) {
+    const double ytl = proj_Y(double(I.yT[i]) - double(y[i]), I.ctype[i]) * I.E[i];
+    mx.v[0] = fmax(mx.v[0], fabs(ytl));
+  });
+  for_elems<BS>(vlo, vhi, [&](int j) {
+    const double d = ((double(I.xT[j]) - double(x[j])) / dn) * I.D[j];
+    mx.v[1] = fmax(mx.v[1], fabs(d));
+  });
+  return mx;
+}
+
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void write_outputs(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
+                                           int status, double dn, double mxy, double mxx) {
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  if (I.x_out) {
+    for_elems<BS>(vlo, vhi, [&](int j) {
+      double v = double(I.xT[j]) * I.D[j];
+      if (status == PDHCG_DUAL_INFEASIBLE) {
+        const double d = ((double(I.xT[j]) - double(x[j])) / dn) * I.D[j];
+        v = mxx > 0.0 ? d / mxx : 0.0;
+      }
+      I.x_out[j] = v;
+    });
+  }
+  if (I.y_out) {
+    for_elems<BS>(clo, chi, [&](int i) {
+      double v = double(I.yT[i]) * I.E[i];
+      if (status == PDHCG_PRIMAL_INFEASIBLE) {
+        const double ytl = proj_Y(double(I.yT[i]) - double(y[i]), I.ctype[i]) * I.E[i];
+        v = mxy > 0.0 ? ytl / mxy : 0.0;
+      }
+      I.y_out[i] = v;
+    });
+  }
+}
+
+// ---- restart: new anchor and iterate T(z) ----
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void restart_copy(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi) {
+  VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
+  VecT* __restrict__ xa = I.xa;
+  VecT* __restrict__ ya = I.ya;
+  const VecT* __restrict__ xT = I.xT;
+  const VecT* __restrict__ yT = I.yT;
+  for_elems<BS>(vlo, vhi, [&](int j) {
+    const VecT v = xT[j];
+    x[j] = v;
+    xa[j] = v;
+  });
+  for_elems<BS>(clo, chi, [&](int i) {
+    const VecT v = yT[i];
+    y[i] = v;
+    ya[i] = v;
+  });
+}
+
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void init_point(const Inst<MatT, VecT>& I, int vlo, int vhi, int clo, int chi) {
+  for_elems<BS>(vlo, vhi, [&](int j) {
+    double x0 = I.x_init ? I.x_init[j] / I.D[j] : 0.0;
+    VecT xv = VecT(clampv(x0, double(I.lv[j]), double(I.uv[j])));
+    I.xb0[j] = xv;
+    I.xa[j] = xv;
+  });
+  for_elems<BS>(clo, chi, [&](int i) {
+    double y0 = I.y_init ? proj_Y(I.y_init[i] / I.E[i], I.ctype[i]) : 0.0;
+    I.yb0[i] = VecT(y0);
+    I.ya[i] = VecT(y0);
+  });
+}
+
+// The control loop: scalar state, decisions and group reductions; the row and
+// elementwise work is in the phase functions above.
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
+                                            const RowCtx& rc) {
+  using CT = VecT;
   SolverState S = *I.st;
   if (S.status != 0) return;
   const DevParams P = I.prm;
@@ -92,43 +445,12 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
   int vlo, vhi, clo, chi;
   g.range(I.var_part, I.n, vlo, vhi);
   g.range(I.con_part, I.m, clo, chi);
-  const bool use_q = I.has_q != 0;
-  // local copies of the read-only data pointers
-  const VecT* __restrict__ c_s = I.c;
-  const VecT* __restrict__ lv = I.lv;
-  const VecT* __restrict__ uv = I.uv;
-  const VecT* __restrict__ lc = I.lc;
-  const VecT* __restrict__ uc = I.uc;
-  const VecT* __restrict__ qdiag = I.qdiag;
-  const int8_t* __restrict__ vtype = I.vtype;
-  const int8_t* __restrict__ ctype = I.ctype;
   const int prank = g.nblk > 1 ? g.rank : -1;
-  VecT* xa = I.xa;
-  VecT* ya = I.ya;
-  VecT* rv = I.r;
-  VecT* qv = I.q;
-  VecT* grad = I.grad;
-  VecT* gprev = I.gprev;
-  VecT* xprev = I.xprev;
-  VecT* bvv = I.bv;
-  VecT* xT = I.xT;
-  VecT* yT = I.yT;
-  VecT* xbar = I.xbar;
   bool ok = true;
+  PhaseClock clk{threadIdx.x == 0 && g.rank == 0, PDHCG_PHASE_TIMERS ? globaltimer_ns() : 0};
 
-  // ---- first launch: initial point (x0 = proj_X(x_init or 0), y0 = proj_Y(y_init or 0)) ----
   if (!S.started) {
-    for_elems<BS>(vlo, vhi, [&](int j) {
-      double x0 = I.x_init ? I.x_init[j] / I.D[j] : 0.0;
-      VecT xv = VecT(clampv(x0, double(lv[j]), double(uv[j])));
-      I.xb0[j] = xv;
-      xa[j] = xv;
-    });
-    for_elems<BS>(clo, chi, [&](int i) {
-      double y0 = I.y_init ? proj_Y(I.y_init[i] / I.E[i], ctype[i]) : 0.0;
-      I.yb0[i] = VecT(y0);
-      ya[i] = VecT(y0);
-    });
+    init_point<BS>(I, vlo, vhi, clo, chi);
     double t[1] = {double(globaltimer_ns())};
     ok = group_reduce<BS, 1>(g, t, 1u);
     S.t_start_ns = t[0];
@@ -136,62 +458,23 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
     S.cur = 0;
   }
   const int64_t K_first = S.K;
-  const auto none = nosrc<MatT>();
-  PhaseClock clk{threadIdx.x == 0 && g.rank == 0, globaltimer_ns()};
 
   while (ok) {
-    VecT* x = S.cur ? I.xb1 : I.xb0;
-    VecT* xn = S.cur ? I.xb0 : I.xb1;
-    VecT* y = S.cur ? I.yb1 : I.yb0;
-    VecT* yn = S.cur ? I.yb0 : I.yb1;
+    const int cur = S.cur;
     const double inv_tau = 1.0 / S.tau, inv_sigma = 1.0 / S.sigma;
     const double wk = double(S.k + 1) / double(S.k + 2), ak = 1.0 / double(S.k + 2);
-    const CT itau = CT(inv_tau), isig = CT(inv_sigma), sig = CT(S.sigma);
-    const CT wkc = CT(wk), akc = CT(ak), th = CT(P.theta), th1 = CT(1.0 + P.theta);
+    StepScalars<CT> sc{CT(inv_tau), CT(inv_sigma), CT(S.sigma), CT(wk), CT(ak), CT(P.theta), CT(1.0 + P.theta)};
 
-    // ---------------- Phase I: g = A^T y, b, inner-solver start ----------------
+    // Phase I
     double red1[4];
     {
-      DotAcc<CT> a0, a1, a2, a3;  // inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2
-      space_rows<BS, LM, Acc>(
-          I.vsp, prank, src(I.ATs, I.AT, [&](int i) { return y[i]; }),
-          src(I.Qs, I.Q, [&](int k) { return x[k]; }, method != PDHCG_INNER_DIAG && use_q), red,
-          [&](int j, const Acc* sums) {
-            const CT xj = x[j];
-            const CT bj = xj * itau - c_s[j] - CT(sums[0]);
-            a1.add_prod(bj, bj);
-            if (method == PDHCG_INNER_DIAG) {
-              const CT xt = clampv(bj / (qdiag[j] + itau), lv[j], uv[j]);
-              const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
-              xT[j] = xt;
-              xbar[j] = CT(2) * xt - xj;
-              xn[j] = xnj;
-              a2.add_prod(xt - xj, xt - xj);
-              a3.add_prod(xnj - xj, xnj - xj);
-            } else if (method == PDHCG_INNER_CG) {
-              const CT hx = CT(sums[1]) + xj * itau;
-              const CT rj = bj - hx;
-              rv[j] = rj;
-              xT[j] = xj;
-              a0.add_prod(rj, rj);
-            } else {
-              const CT hx = CT(sums[1]) + xj * itau;
-              const CT gj = hx - bj;
-              grad[j] = gj;
-              bvv[j] = bj;
-              xT[j] = xj;
-              const CT d = xj - clampv(xj - gj, lv[j], uv[j]);
-              a0.add_prod(d, d);
-            }
-          });
-      red1[0] = a0.get();
-      red1[1] = a1.get();
-      red1[2] = a2.get();
-      red1[3] = a3.get();
-      clk.mark(S.tm, 0);
-      if (!group_reduce<BS, 4>(g, red1, 0u)) { ok = false; break; }
-      clk.mark(S.tm, 5);
+      const Red<4> r = phase1<BS, LM>(I, prank, method, cur, sc, rc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red1[q] = r.v[q];
     }
+    clk.mark(S.tm, 0);
+    if (!group_reduce<BS, 4>(g, red1, 0u)) { ok = false; break; }
+    clk.mark(S.tm, 5);
 
     // adaptive inner tolerance (Sec. 3.3)
     if (S.K == 0) S.eps_in = P.eps_inner_first * fmax(1.0, sqrt(red1[1]));
@@ -201,7 +484,7 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
     // running to its step cap (FP64 vectors: the paper's rule unchanged).
     const double eps = sizeof(VecT) == 4 ? fmax(S.eps_in, 0x1p-20 * sqrt(red1[1])) : S.eps_in;
 
-    // ---------------- inner solve ----------------
+    // inner solve (Sec. 2.2)
     if (method == PDHCG_INNER_CG) {
       double rr = red1[0], beta = 0.0;
       int j = 0, pc = 0;
@@ -209,46 +492,16 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
         if (sqrt(rr) <= eps || j >= P.max_inner_iter) break;
         const VecT* pold = pc ? I.p1 : I.p0;
         VecT* pnew = pc ? I.p0 : I.p1;
-        const CT be = CT(beta);
-        const bool first = (j == 0);
-        // Phase A: p = r + beta p (gathered on the fly, bit-identical to the
-        // owner's write), q = H p, p^T q
-        double pq[1];
-        {
-          DotAcc<CT> apq;
-          space_rows<BS, LM, Acc>(
-              I.vsp, prank,
-              src(I.Qs, I.Q, [&](int k) { return first ? rv[k] : CT(fma(be, pold[k], rv[k])); }, use_q),
-              none, red, [&](int i, const Acc* sums) {
-                const CT pi = first ? rv[i] : CT(fma(be, pold[i], rv[i]));
-                pnew[i] = pi;
-                const CT qi = CT(sums[0]) + pi * itau;
-                qv[i] = qi;
-                apq.add_prod(pi, qi);
-              });
-          pq[0] = apq.get();
-          clk.mark(S.tm, 1);
-          if (!group_reduce<BS, 1>(g, pq, 0u)) { ok = false; break; }
-          clk.mark(S.tm, 5);
-        }
+        double pq[1] = {cg_phase_a<BS, LM>(I, prank, j == 0, CT(beta), pold, pnew, sc.itau, rc)};
+        clk.mark(S.tm, 1);
+        if (!group_reduce<BS, 1>(g, pq, 0u)) { ok = false; break; }
+        clk.mark(S.tm, 5);
         if (!(pq[0] > 0.0)) break;
         const double alpha = rr / pq[0];
-        const CT al = CT(alpha);
-        // Phase B: x += alpha p, r -= alpha q, r^T r
-        double rn[1];
-        {
-          DotAcc<CT> arr;
-          for_elems<BS>(vlo, vhi, [&](int i) {
-            xT[i] = xT[i] + al * pnew[i];
-            const CT ri = rv[i] - al * qv[i];
-            rv[i] = ri;
-            arr.add_prod(ri, ri);
-          });
-          rn[0] = arr.get();
-          clk.mark(S.tm, 2);
-          if (!group_reduce<BS, 1>(g, rn, 0u)) { ok = false; break; }
-          clk.mark(S.tm, 5);
-        }
+        double rn[1] = {cg_phase_b<BS>(I, vlo, vhi, CT(alpha), pnew)};
+        clk.mark(S.tm, 2);
+        if (!group_reduce<BS, 1>(g, rn, 0u)) { ok = false; break; }
+        clk.mark(S.tm, 5);
         beta = rn[0] / rr;
         rr = rn[0];
         pc ^= 1;
@@ -256,18 +509,17 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
       }
       if (!ok) break;
       S.inner_total += j;
-      for_elems<BS>(vlo, vhi, [&](int i) { xbar[i] = CT(2) * xT[i] - x[i]; });
+      write_xbar<BS>(I, vlo, vhi, I.xT, cur ? I.xb1 : I.xb0, false);
       if (!group_sync<BS>(g)) { ok = false; break; }
     } else if (method == PDHCG_INNER_BB) {
-      // x and grad alternate between two buffers each: (xT, xprev) and (grad, gprev);
-      // the previous step's pair is read where the oracle keeps copies.
+      // x and grad alternate between two buffers each: (xT, xprev) and (grad, gprev)
       const double alpha_min = 1.0 / (S.gersh + inv_tau), alpha_max = 1.0 / inv_tau;
       double nr = red1[0], ss = 0.0, sy = 0.0;
       int j = 0;
-      VecT* xc = xT;      // current inner iterate
-      VecT* xo = xprev;   // previous inner iterate
-      VecT* gc = grad;
-      VecT* go = gprev;
+      VecT* xc = I.xT;
+      VecT* xo = I.xprev;
+      VecT* gc = I.grad;
+      VecT* go = I.gprev;
       while (true) {
         if (sqrt(nr) <= eps || j >= P.max_inner_iter) break;
         double alpha = alpha_min;
@@ -275,43 +527,21 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
           alpha = sy > 0.0 ? ss / sy : alpha_max;
           alpha = fmin(fmax(alpha, alpha_min), alpha_max);
         }
-        const CT al = CT(alpha);
-        // Phase B': projected step into the other buffer
-        {
-          VecT* __restrict__ xn2 = xo;
-          const VecT* __restrict__ x1 = xc;
-          const VecT* __restrict__ g1 = gc;
-          for_elems<BS>(vlo, vhi, [&](int i) { xn2[i] = clampv(x1[i] - al * g1[i], lv[i], uv[i]); });
-        }
+        bb_phase_b<BS>(I, vlo, vhi, CT(alpha), xc, gc, xo);
         { VecT* t = xo; xo = xc; xc = t; }
         clk.mark(S.tm, 2);
         if (!group_sync<BS>(g)) { ok = false; break; }
         clk.mark(S.tm, 5);
-        // Phase A': gradient, BB quantities, natural residual
         double v3[3];
         {
-          DotAcc<CT> ass, asy, anr;
-          VecT* __restrict__ gn = go;
-          space_rows<BS, LM, Acc>(
-              I.vsp, prank, src(I.Qs, I.Q, [&](int k) { return xc[k]; }, use_q), none, red,
-              [&](int i, const Acc* sums) {
-                const CT xi = xc[i];
-                const CT gi = (CT(sums[0]) + xi * itau) - bvv[i];
-                gn[i] = gi;
-                const CT sv = xi - xo[i];
-                const CT yv = gi - gc[i];
-                ass.add_prod(sv, sv);
-                asy.add_prod(sv, yv);
-                const CT d = xi - clampv(xi - gi, lv[i], uv[i]);
-                anr.add_prod(d, d);
-              });
-          v3[0] = ass.get();
-          v3[1] = asy.get();
-          v3[2] = anr.get();
-          clk.mark(S.tm, 1);
-          if (!group_reduce<BS, 3>(g, v3, 0u)) { ok = false; break; }
-          clk.mark(S.tm, 5);
+          const Red<3> r = bb_phase_a<BS, LM>(I, prank, xc, xo, gc, go, sc.itau, rc);
+          v3[0] = r.v[0];
+          v3[1] = r.v[1];
+          v3[2] = r.v[2];
         }
+        clk.mark(S.tm, 1);
+        if (!group_reduce<BS, 3>(g, v3, 0u)) { ok = false; break; }
+        clk.mark(S.tm, 5);
         { VecT* t = go; go = gc; gc = t; }
         ss = v3[0];
         sy = v3[1];
@@ -321,48 +551,21 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
       if (!ok) break;
       S.inner_total += j;
       // the result must be in xT for Phase II and the checks; xbar = 2 x+ - x
-      if (xc != xT) {
-        for_elems<BS>(vlo, vhi, [&](int i) {
-          const CT xi = xc[i];
-          xT[i] = xi;
-          xbar[i] = CT(2) * xi - x[i];
-        });
-      } else {
-        for_elems<BS>(vlo, vhi, [&](int i) { xbar[i] = CT(2) * xT[i] - x[i]; });
-      }
+      write_xbar<BS>(I, vlo, vhi, xc, cur ? I.xb1 : I.xb0, xc != I.xT);
       if (!group_sync<BS>(g)) { ok = false; break; }
     }
 
-    // ---------------- Phase II: A xbar, dual step, Halpern ----------------
+    // Phase II
     double red2[3];
     {
-      DotAcc<CT> ady, adx, amv;
-      space_rows<BS, LM, Acc>(
-          I.csp, prank, src(I.As, I.A, [&](int j) { return xbar[j]; }), none, red,
-          [&](int i, const Acc* sums) {
-            const CT yi = y[i];
-            const CT v = yi * isig + CT(sums[0]);
-            const CT yt = sig * (v - clampv(v, lc[i], uc[i]));
-            yT[i] = yt;
-            yn[i] = wkc * (th1 * yt - th * yi) + akc * ya[i];
-            ady.add_prod(yt - yi, yt - yi);
-          });
-      if (method != PDHCG_INNER_DIAG) {
-        for_elems<BS>(vlo, vhi, [&](int j) {
-          const CT xt = xT[j], xj = x[j];
-          const CT xnj = wkc * (th1 * xt - th * xj) + akc * xa[j];
-          xn[j] = xnj;
-          adx.add_prod(xt - xj, xt - xj);
-          amv.add_prod(xnj - xj, xnj - xj);
-        });
-      }
-      red2[0] = ady.get();
-      red2[1] = adx.get();
-      red2[2] = amv.get();
-      clk.mark(S.tm, 3);
-      if (!group_reduce<BS, 3>(g, red2, 0u)) { ok = false; break; }
-      clk.mark(S.tm, 5);
+      const Red<3> r = phase2<BS, LM>(I, prank, method, cur, vlo, vhi, sc, rc);
+      red2[0] = r.v[0];
+      red2[1] = r.v[1];
+      red2[2] = r.v[2];
     }
+    clk.mark(S.tm, 3);
+    if (!group_reduce<BS, 3>(g, red2, 0u)) { ok = false; break; }
+    clk.mark(S.tm, 5);
     const double dy2 = red2[0];
     const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
     const double mvh2 = method == PDHCG_INNER_DIAG ? red1[3] : red2[2];
@@ -375,55 +578,12 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
     bool do_restart = false;
     const bool check = ((S.K + 1) % P.k_eval == 0) || (S.K + 1 >= P.max_iter);
     if (check) {
-      // ------------- check phase: KKT (Sec. 4.2) + infeasibility (Sec. 5) -------------
       double cv[18];
+      {
+        const Red<18> r = check_phase<BS, LM>(I, prank, cur, rc);
 #pragma unroll
-      for (int q = 0; q < 18; ++q) cv[q] = 0.0;
-      space_rows<BS, LM, double>(
-          I.csp, prank,
-          src2(I.As, I.A, [&](int j) { return double(xT[j]); },
-               [&](int j) { return double(xT[j]) - double(x[j]); }),
-          none, red, [&](int i, const double* sums) {
-            const double ax = sums[0], ad = sums[1];
-            const double axu = ax / I.E[i];
-            cv[0] = fmax(cv[0], fabs(axu - clampv(axu, I.lc_o[i], I.uc_o[i])));
-            const double yu = double(yT[i]) * I.E[i];
-            cv[7] += support_term(yu, I.lc_o[i], I.uc_o[i]);
-            const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]);
-            cv[9] += support_term(ytl, double(lc[i]), double(uc[i]));
-            cv[13] = fmax(cv[13], fabs(ad - proj_recc(ad, ctype[i])));
-            const double dya = double(yT[i]) - double(ya[i]);
-            cv[16] += dya * dya;
-          });
-      space_rows<BS, LM, double>(
-          I.vsp, prank,
-          src2(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
-               [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
-          src2(I.Qs, I.Q, [&](int k) { return double(xT[k]); },
-               [&](int k) { return double(xT[k]) - double(x[k]); }, use_q),
-          red, [&](int j, const double* sums) {
-            const double aty = sums[0], atyt = sums[1], qx = sums[2], qd = sums[3];
-            const double Dj = I.D[j];
-            const double xu = double(xT[j]) * Dj;
-            const double qxu = qx / Dj, atyu = aty / Dj;
-            const double rj = qxu + I.c_o[j] + atyu;
-            const double rh = proj_R(rj, vtype[j]);
-            cv[1] = fmax(cv[1], fabs(rj - rh));
-            cv[2] = fmax(cv[2], fabs(qxu));
-            cv[3] = fmax(cv[3], fabs(atyu));
-            cv[4] += xu * qxu;
-            cv[5] += I.c_o[j] * xu;
-            cv[6] += support_term(-rh, I.lv_o[j], I.uv_o[j]);
-            cv[8] = fmax(cv[8], fabs(atyt - proj_R(atyt, vtype[j])));
-            cv[9] += support_term(-atyt, double(lv[j]), double(uv[j]));
-            const double dx = double(xT[j]) - double(x[j]);
-            cv[10] = fmax(cv[10], fabs(dx));
-            cv[11] += double(c_s[j]) * dx;
-            cv[12] = fmax(cv[12], fabs(dx - proj_recc(dx, vtype[j])));
-            cv[14] = fmax(cv[14], fabs(qd));
-            const double dxa = double(xT[j]) - double(xa[j]);
-            cv[15] += dxa * dxa;
-          });
+        for (int q = 0; q < 18; ++q) cv[q] = r.v[q];
+      }
       cv[17] = double(globaltimer_ns());
       // max slots: 0 1 2 3 8 10 12 13 14 17
       const unsigned mm = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3) | (1u << 8) | (1u << 10) |
@@ -463,40 +623,15 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
       if (!status && cv[17] - S.t_start_ns >= P.time_limit_ns) status = PDHCG_TIME_LIMIT;
 
       if (status) {
-        // ---- output phase: unscale (x = D x+, y = E y+) or normalised rays ----
         const double dn = cv[10];
         double mx[2] = {0.0, 0.0};
         if (status == PDHCG_PRIMAL_INFEASIBLE || status == PDHCG_DUAL_INFEASIBLE) {
-          for_elems<BS>(clo, chi, [&](int i) {
-            const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]) * I.E[i];
-            mx[0] = fmax(mx[0], fabs(ytl));
-          });
-          for_elems<BS>(vlo, vhi, [&](int j) {
-            const double d = ((double(xT[j]) - double(x[j])) / dn) * I.D[j];
-            mx[1] = fmax(mx[1], fabs(d));
-          });
+          const Red<2> r = ray_norms<BS>(I, cur, vlo, vhi, clo, chi, dn);
+          mx[0] = r.v[0];
+          mx[1] = r.v[1];
           if (!group_reduce<BS, 2>(g, mx, 3u)) { ok = false; break; }
         }
-        if (I.x_out) {
-          for_elems<BS>(vlo, vhi, [&](int j) {
-            double v = double(xT[j]) * I.D[j];
-            if (status == PDHCG_DUAL_INFEASIBLE) {
-              const double d = ((double(xT[j]) - double(x[j])) / dn) * I.D[j];
-              v = mx[1] > 0.0 ? d / mx[1] : 0.0;
-            }
-            I.x_out[j] = v;
-          });
-        }
-        if (I.y_out) {
-          for_elems<BS>(clo, chi, [&](int i) {
-            double v = double(yT[i]) * I.E[i];
-            if (status == PDHCG_PRIMAL_INFEASIBLE) {
-              const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]) * I.E[i];
-              v = mx[0] > 0.0 ? ytl / mx[0] : 0.0;
-            }
-            I.y_out[i] = v;
-          });
-        }
+        write_outputs<BS>(I, cur, vlo, vhi, clo, chi, status, dn, mx[0], mx[1]);
         S.status = status;
         S.K += 1;
         S.t_end_ns = cv[17];
@@ -519,17 +654,7 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
     }
 
     if (do_restart) {
-      // new anchor and iterate: T(z)
-      for_elems<BS>(vlo, vhi, [&](int j) {
-        const VecT v = xT[j];
-        x[j] = v;
-        xa[j] = v;
-      });
-      for_elems<BS>(clo, chi, [&](int i) {
-        const VecT v = yT[i];
-        y[i] = v;
-        ya[i] = v;
-      });
+      restart_copy<BS>(I, cur, vlo, vhi, clo, chi);
       if (!group_sync<BS>(g)) { ok = false; break; }
       clk.mark(S.tm, 6);
       S.mv = sqrt(dx2);
@@ -545,6 +670,97 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
   }
   if (!ok) S.device_error = 1;
   if (g.rank == 0 && threadIdx.x == 0) *I.st = S;
+}
+
+// Offset of the vector area in dynamic shared memory (after the TMA stages, if any).
+template <int BS>
+__host__ __device__ constexpr size_t vec_smem_offset() {
+  return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (BS / 32) : 0;
+}
+
+// Solve one instance with every iteration vector held in shared memory.  The
+// iterate state (current x, y and the Halpern anchors) is copied in when the
+// solve resumes and copied back when it stops or pauses, so the global buffers
+// stay the state of record between launches.
+template <int BS, class MatT, class VecT>
+__device__ __noinline__ void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig,
+                                           const LaunchPlan& plan, const RowCtx& rc, char* base,
+                                           int method) {
+  Inst<MatT, VecT> I = Ig;
+  const int n = Ig.n, m = Ig.m;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += (bytes + 15) & ~size_t(15);
+    return p;
+  };
+  const size_t nb = size_t(n) * sizeof(VecT), mb = size_t(m) * sizeof(VecT);
+  VecT* xb0 = reinterpret_cast<VecT*>(take(nb));
+  VecT* xb1 = reinterpret_cast<VecT*>(take(nb));
+  VecT* xT = reinterpret_cast<VecT*>(take(nb));
+  VecT* xa = reinterpret_cast<VecT*>(take(nb));
+  VecT* xbar = reinterpret_cast<VecT*>(take(nb));
+  VecT* c = reinterpret_cast<VecT*>(take(nb));
+  VecT* lv = reinterpret_cast<VecT*>(take(nb));
+  VecT* uv = reinterpret_cast<VecT*>(take(nb));
+  VecT* qd = reinterpret_cast<VecT*>(take(nb));
+  if (method == PDHCG_INNER_CG || method == PDHCG_INNER_BB) {
+    VecT* e0 = reinterpret_cast<VecT*>(take(nb));
+    VecT* e1 = reinterpret_cast<VecT*>(take(nb));
+    VecT* e2 = reinterpret_cast<VecT*>(take(nb));
+    VecT* e3 = reinterpret_cast<VecT*>(take(nb));
+    if (method == PDHCG_INNER_CG) {
+      I.r = e0; I.p0 = e1; I.p1 = e2; I.q = e3;
+    } else {
+      I.bv = e0; I.grad = e1; I.gprev = e2; I.xprev = e3;
+    }
+  }
+  VecT* yb0 = reinterpret_cast<VecT*>(take(mb));
+  VecT* yb1 = reinterpret_cast<VecT*>(take(mb));
+  VecT* yT = reinterpret_cast<VecT*>(take(mb));
+  VecT* ya = reinterpret_cast<VecT*>(take(mb));
+  VecT* lc = reinterpret_cast<VecT*>(take(mb));
+  VecT* uc = reinterpret_cast<VecT*>(take(mb));
+  int8_t* vt = reinterpret_cast<int8_t*>(take(size_t(n)));
+  int8_t* ct = reinterpret_cast<int8_t*>(take(size_t(m)));
+  const SolverState& S0 = *Ig.st;
+  const bool started = S0.started != 0;
+  const int cur = S0.cur;
+  for (int i = threadIdx.x; i < n; i += BS) {
+    c[i] = Ig.c[i];
+    lv[i] = Ig.lv[i];
+    uv[i] = Ig.uv[i];
+    qd[i] = Ig.qdiag[i];
+    vt[i] = Ig.vtype[i];
+    if (started) {
+      (cur ? xb1 : xb0)[i] = (cur ? Ig.xb1 : Ig.xb0)[i];
+      xa[i] = Ig.xa[i];
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += BS) {
+    lc[i] = Ig.lc[i];
+    uc[i] = Ig.uc[i];
+    ct[i] = Ig.ctype[i];
+    if (started) {
+      (cur ? yb1 : yb0)[i] = (cur ? Ig.yb1 : Ig.yb0)[i];
+      ya[i] = Ig.ya[i];
+    }
+  }
+  I.xb0 = xb0; I.xb1 = xb1; I.xT = xT; I.xa = xa; I.xbar = xbar;
+  I.c = c; I.lv = lv; I.uv = uv; I.qdiag = qd; I.vtype = vt;
+  I.yb0 = yb0; I.yb1 = yb1; I.yT = yT; I.ya = ya; I.lc = lc; I.uc = uc; I.ctype = ct;
+  __syncthreads();
+  solve_instance<BS, Ld::Cached>(g, I, plan, rc);
+  __syncthreads();
+  const int cur2 = Ig.st->cur;
+  for (int i = threadIdx.x; i < n; i += BS) {
+    (cur2 ? Ig.xb1 : Ig.xb0)[i] = (cur2 ? xb1 : xb0)[i];
+    Ig.xa[i] = xa[i];
+  }
+  for (int i = threadIdx.x; i < m; i += BS) {
+    (cur2 ? Ig.yb1 : Ig.yb0)[i] = (cur2 ? yb1 : yb0)[i];
+    Ig.ya[i] = ya[i];
+  }
 }
 
 #ifndef PDHCG_MIN_BLOCKS
@@ -595,7 +811,14 @@ __global__ void __launch_bounds__(BS, PDHCG_MIN_BLOCKS) solve_kernel(const Inst<
     __syncthreads();
     if (idx >= plan.npool) break;
     g.epoch = 0;
-    solve_instance<BS, Ld::Cached>(g, insts[plan.pool_inst[idx]], plan, rc);
+    const Inst<MatT, VecT>& Ig = insts[plan.pool_inst[idx]];
+    const int method = Ig.st->method;
+    const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
+    if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
+      solve_in_smem<BS>(g, Ig, plan, rc, dsm + vec_smem_offset<BS>(), method);
+    } else {
+      solve_instance<BS, Ld::Cached>(g, Ig, plan, rc);
+    }
     __syncthreads();
   }
 }

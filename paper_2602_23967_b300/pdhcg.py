@@ -68,6 +68,12 @@ class Result(C.Structure):
         return d
 
 
+class ProblemData(C.Structure):
+    _fields_ = [("Q", C.POINTER(Csr)), ("A", C.POINTER(Csr)), ("c", C.POINTER(C.c_double)),
+                ("lc", C.POINTER(C.c_double)), ("uc", C.POINTER(C.c_double)),
+                ("lv", C.POINTER(C.c_double)), ("uv", C.POINTER(C.c_double))]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("rejected", C.c_uint64), ("launches", C.c_uint64), ("live", C.c_int32),
@@ -90,6 +96,8 @@ def lib():
         L.pdhcg_default_params.argtypes = [C.POINTER(Params)]
         L.pdhcg_create.argtypes = [C.POINTER(Csr), C.POINTER(Csr), _D, _D, _D, _D, _D,
                                    C.POINTER(Params), _P, C.POINTER(_P)]
+        L.pdhcg_create_batch.argtypes = [C.c_int, C.POINTER(ProblemData), C.POINTER(Params), _P,
+                                         C.POINTER(_P)]
         L.pdhcg_solve.argtypes = [_P, _D, _D, C.POINTER(Result), _D, _D]
         L.pdhcg_solve_dev.argtypes = [_P, _P, _P, C.POINTER(Result), _P, _P]
         L.pdhcg_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(Result), C.POINTER(_D),
@@ -170,10 +178,13 @@ def _qp_args(qp):
 class Problem:
     """A QP resident on the device (pdhcg_create)."""
 
-    def __init__(self, qp, params: Params | None = None, stream=None):
+    def __init__(self, qp, params: Params | None = None, stream=None, _handle=None):
         L = lib()
         self.n, self.m = int(qp.n), int(qp.m)
         self.params = params if params is not None else default_params()
+        if _handle is not None:
+            self.handle = _handle
+            return
         h = _qp_args(qp)
         handle = _P()
         rc = L.pdhcg_create(C.byref(h["Q"].s) if "Q" in h else None, C.byref(h["A"].s),
@@ -232,6 +243,20 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def create_batch(qps, params: Params | None = None, stream=None):
+    """Create many Problems at once (pdhcg_create_batch: shared allocation, one setup launch)."""
+    params = params if params is not None else default_params()
+    holds = [_qp_args(q) for q in qps]
+    data = (ProblemData * len(qps))()
+    for i, h in enumerate(holds):
+        data[i] = ProblemData(C.pointer(h["Q"].s) if "Q" in h else None, C.pointer(h["A"].s),
+                              _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]))
+    handles = (_P * len(qps))()
+    check(lib().pdhcg_create_batch(len(qps), data, C.byref(params), _P(stream) if stream else None,
+                                   handles), "pdhcg_create_batch")
+    return [Problem(q, params, _handle=_P(handles[i])) for i, q in enumerate(qps)]
 
 
 def solve_batch(problems, want_solutions=True):

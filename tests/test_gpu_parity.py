@@ -207,6 +207,26 @@ def test_batch_equals_single_solves():
             p.close()
 
 
+def test_create_batch_matches_single_create():
+    qps = [W.mpc_qp(seed=200 + i) for i in range(6)] + [W.random_qp(seed=40 + i) for i in range(3)]
+    probs = pdhcg.create_batch(qps, pdhcg.default_params())
+    try:
+        for q, p in zip(qps, probs):
+            single = pdhcg.Problem(q, pdhcg.default_params())
+            xs, ys, rs = single.solve()
+            eta_s = single.eta()
+            single.close()
+            xb, yb, rb = p.solve()
+            assert p.eta() == pytest.approx(eta_s, rel=1e-12)
+            assert rb["status_name"] == rs["status_name"] == "OPTIMAL"
+            assert np.max(np.abs(xb - xs)) <= 1e-12 * (1 + np.max(np.abs(xs)))
+        out = pdhcg.solve_batch(probs)
+        assert all(r["status_name"] == "OPTIMAL" for _, _, r in out)
+    finally:
+        for p in probs:
+            p.close()
+
+
 def test_warm_start_from_solution_is_immediate():
     qp = W.random_qp(seed=9)
     prob = pdhcg.Problem(qp, pdhcg.default_params(eps_tol=1e-7))
