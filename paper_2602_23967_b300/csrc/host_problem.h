@@ -60,6 +60,32 @@ struct PartitionSet {
 
 }  // namespace pdhcg
 
+struct pdhcg_problem;
+
+namespace pdhcg {
+
+struct CreateInput {
+  const pdhcg_csr *Q, *A;
+  const double *c, *lc, *uc, *lv, *uv;
+};
+
+// Create count handles (shared allocation when count > 1).  In pdhcg_api.cu.
+// pool_only: handles are solved by single CTAs only (no multi-CTA scratch).
+int create_impl(int count, const CreateInput* in, const pdhcg_params* params, void* stream,
+                pdhcg_problem** out, bool pool_only);
+// Device bytes the handle of `in` would hold (host-side preparation only).
+int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes);
+SolverState initial_state(const pdhcg_problem* P);
+void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res);
+// One pooled launch advancing every handle by at most iter_budget PDHG steps
+// (0 = to completion), with handle i's state at d_states[i] on the device and
+// its solution written to x_out[i] / y_out[i] (device, may be null).  Blocking.
+int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states,
+                      double* const* x_out, double* const* y_out, int64_t iter_budget);
+int check_params_c(const pdhcg_params* p);
+
+}  // namespace pdhcg
+
 // Opaque handle of the C ABI.
 struct pdhcg_problem {
   int device = 0;

@@ -681,11 +681,6 @@ static int check_params(const pdhcg_params* p) {
 
 namespace pdhcg {
 
-struct CreateInput {
-  const pdhcg_csr *Q, *A;
-  const double *c, *lc, *uc, *lv, *uv;
-};
-
 // Host side of creation: validate, canonicalise, choose the inner solver, build
 // the SELL layouts.  No device work.
 int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream, pdhcg_problem** out,
@@ -752,7 +747,7 @@ int cached_max_group_blocks(int precision) {
 // Create count handles: one device allocation, one staging transfer per handle,
 // and (count > 1) one pooled setup launch.
 int create_impl(int count, const CreateInput* in, const pdhcg_params* params, void* stream,
-                pdhcg_t** out) {
+                pdhcg_t** out, bool pool_only) {
   pdhcg_params prm;
   if (params) {
     int rc = check_params(params);
@@ -796,13 +791,15 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
     return mb;
   }
   const bool batch = count > 1;
+  const bool pooled = batch || pool_only;
   // sizes and offsets inside one allocation
   std::vector<size_t> off(static_cast<size_t>(count));
   size_t total = batch ? ((sizeof(SolverState) * size_t(count) + 255) & ~size_t(255)) : 0;
   size_t stage_total = 0;
   for (int i = 0; i < count; ++i) {
     P[size_t(i)]->device = dev;
-    P[size_t(i)]->max_blk = batch ? 1 : std::max(mb, 1);
+    P[size_t(i)]->max_blk = pooled ? 1 : std::max(mb, 1);
+    if (pooled) P[size_t(i)]->prm.group_blocks = 1;
     Carver sizing;
     carve(P[size_t(i)], sizing, batch);
     P[size_t(i)]->arena_bytes = (sizing.off + 255) & ~size_t(255);
@@ -914,6 +911,69 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
   return PDHCG_OK;
 }
 
+int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes) {
+  HostQP h;
+  pdhcg_problem* P = nullptr;
+  int rc = prepare_problem(in, prm, nullptr, &P, &h);
+  if (rc) return rc;
+  P->max_blk = 1;
+  Carver sizing;
+  carve(P, sizing, false);
+  *bytes = ((sizing.off + 255) & ~size_t(255)) + (1u << 12);
+  delete P;
+  return PDHCG_OK;
+}
+
+int check_params_c(const pdhcg_params* p) { return check_params(p); }
+
+int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states, double* const* x_out,
+                      double* const* y_out, int64_t iter_budget) {
+  if (count <= 0) return PDHCG_OK;
+  const pdhcg_problem* P0 = probs[0];
+  CK(cudaSetDevice(P0->device));
+  cudaStream_t s = P0->stream;
+  return dispatch_precision(P0->precision, [&](auto tag) -> int {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    std::vector<Inst<M, V>> hi(static_cast<size_t>(count));
+    std::vector<int32_t> order(static_cast<size_t>(count) + 8, 0);
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      hi[size_t(i)] = make_inst<M, V>(probs[i]);
+      hi[size_t(i)].st = d_states + i;
+      hi[size_t(i)].x_out = x_out ? x_out[i] : nullptr;
+      hi[size_t(i)].y_out = y_out ? y_out[i] : nullptr;
+      order[size_t(i)] = i;
+      const size_t b = smem_need(probs[i]);
+      if (b <= kSmemVecBudget) need = std::max(need, b);
+    }
+    const size_t ib = sizeof(Inst<M, V>) * size_t(count), ob = sizeof(int32_t) * order.size();
+    char* d = nullptr;
+    CK(cudaMalloc(&d, ib + ob));
+    std::unique_ptr<char, void (*)(char*)> guard(d, [](char* q) { cudaFree(q); });
+    CK(cudaMemcpyAsync(d, hi.data(), ib, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d + ib, order.data(), ob, cudaMemcpyHostToDevice, s));
+    int32_t* d_i32 = reinterpret_cast<int32_t*>(d + ib);
+    LaunchPlan plan;
+    plan.npool = count;
+    plan.pool_inst = d_i32;
+    plan.pool_next = d_i32 + count;
+    plan.err = d_i32 + count + 1;
+    plan.iter_budget = iter_budget;
+    plan.smem_vec_bytes = int64_t(need);
+    plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    const int grid = std::max(1, std::min(count, per_sm * sms));
+    cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d), plan, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "slice launch");
+    CK(cudaStreamSynchronize(s));
+    return PDHCG_OK;
+  });
+}
+
 }  // namespace pdhcg
 
 extern "C" {
@@ -927,7 +987,7 @@ int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const 
   }
   *out = nullptr;
   CreateInput in{Q, A, c, lc, uc, lv, uv};
-  return create_impl(1, &in, params, cuda_stream, out);
+  return create_impl(1, &in, params, cuda_stream, out, false);
 }
 
 int pdhcg_create_batch(int count, const pdhcg_problem_data* problems, const pdhcg_params* params,
@@ -942,7 +1002,7 @@ int pdhcg_create_batch(int count, const pdhcg_problem_data* problems, const pdhc
   for (int i = 0; i < count; ++i)
     in[size_t(i)] = CreateInput{problems[i].Q, problems[i].A, problems[i].c, problems[i].lc,
                                 problems[i].uc, problems[i].lv, problems[i].uv};
-  return create_impl(count, in.data(), params, cuda_stream, out);
+  return create_impl(count, in.data(), params, cuda_stream, out, false);
 }
 
 int pdhcg_solve(pdhcg_t* P, const double* x0, const double* y0, pdhcg_result* res, double* x_out,

@@ -1,1 +1,354 @@
-// pdhcg_server.cu — serving loop (continuous batching); filled in below.
+// pdhcg_server.cu — serving loop with continuous batching (pdhcg_server_*).
+//
+// A scheduler thread owns the device side.  Each round it
+//   1. admits queued requests while a slot is free and their device footprint
+//      fits the HBM budget (all admitted in one round are created together with
+//      the batched creation path: one allocation, one setup launch),
+//   2. advances every live solve by one slice of at most `slice_iters` PDHG
+//      steps in a single pooled launch (iterates, anchors, PID and restart state
+//      stay on the device between slices),
+//   3. retires the solves that stopped: copies their result and solution to host
+//      memory, frees their device memory and slot.
+// Requests that arrive while a slice runs are admitted at the next slice
+// boundary, so admission and retirement happen at iteration granularity.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "host_problem.h"
+
+namespace pdhcg {
+
+// Deep copy of one submitted problem.
+struct OwnedProblem {
+  bool has_q = false;
+  int32_t n = 0, m = 0;
+  std::vector<int64_t> qp, ap;
+  std::vector<int32_t> qc, ac;
+  std::vector<double> qv, av, c, lc, uc, lv, uv;
+  pdhcg_csr Q{}, A{};
+  void bind() {
+    Q = pdhcg_csr{n, n, int64_t(qc.size()), qp.data(), qc.data(), qv.data()};
+    A = pdhcg_csr{m, n, int64_t(ac.size()), ap.data(), ac.data(), av.data()};
+  }
+  CreateInput input() const {
+    return CreateInput{has_q ? &Q : nullptr, &A, c.data(), lc.data(), uc.data(), lv.data(), uv.data()};
+  }
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  OwnedProblem prob;
+  size_t bytes = 0;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Live {
+  uint64_t ticket = 0;
+  pdhcg_problem* P = nullptr;
+  size_t bytes = 0;
+  int slot = -1;
+};
+
+struct Done {
+  pdhcg_result res{};
+  std::vector<double> x, y;
+};
+
+}  // namespace pdhcg
+
+struct pdhcg_server {
+  size_t budget = 0;
+  int max_slots = 0;
+  size_t max_queue = 0;
+  int64_t slice_iters = 256;
+  pdhcg_params prm{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<pdhcg::Request> queue;
+  std::unordered_map<uint64_t, pdhcg::Done> done;
+  std::unordered_map<uint64_t, int> pending;  // ticket -> 1 (queued or live)
+  uint64_t next_ticket = 1;
+  pdhcg_server_stats stats{};
+  bool stop = false;
+  std::thread worker;
+  // device side (worker thread only)
+  pdhcg::SolverState* d_states = nullptr;  // max_slots
+  double* d_out = nullptr;                  // per-slot solution buffers live in each handle
+  std::vector<pdhcg::Live> live;
+  std::vector<int> free_slots;
+  std::string worker_error;
+};
+
+namespace pdhcg {
+
+static void copy_csr(const pdhcg_csr* M, std::vector<int64_t>& rp, std::vector<int32_t>& ci,
+                     std::vector<double>& v) {
+  rp.assign(M->rowptr, M->rowptr + M->nrows + 1);
+  ci.assign(M->col, M->col + M->nnz);
+  v.assign(M->val, M->val + M->nnz);
+}
+
+static void worker_loop(pdhcg_server* S) {
+  cudaSetDevice(S->device);
+  while (true) {
+    std::vector<Request> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->live.empty()) {
+        S->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || !S->queue.empty(); });
+      }
+      if (S->stop) break;
+      size_t in_use = S->stats.hbm_in_use;
+      int free_n = int(S->free_slots.size());
+      while (!S->queue.empty() && free_n > 0 && in_use + S->queue.front().bytes <= S->budget) {
+        in_use += S->queue.front().bytes;
+        admit.push_back(std::move(S->queue.front()));
+        S->queue.pop_front();
+        --free_n;
+      }
+      S->stats.queued = int32_t(S->queue.size());
+    }
+    // ---- admission: batched creation of everything admitted this round ----
+    if (!admit.empty()) {
+      std::vector<CreateInput> in;
+      in.reserve(admit.size());
+      for (auto& r : admit) {
+        r.prob.bind();
+        in.push_back(r.prob.input());
+      }
+      std::vector<pdhcg_problem*> handles(admit.size(), nullptr);
+      int rc = create_impl(int(admit.size()), in.data(), &S->prm, S->stream, handles.data(), true);
+      if (rc != PDHCG_OK && admit.size() > 1) {
+        // fall back to one-by-one so one bad request fails alone
+        for (size_t i = 0; i < admit.size(); ++i) {
+          rc = create_impl(1, &in[i], &S->prm, S->stream, &handles[i], true);
+          if (rc != PDHCG_OK) handles[i] = nullptr;
+        }
+      } else if (rc != PDHCG_OK) {
+        handles[0] = nullptr;
+      }
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (size_t i = 0; i < admit.size(); ++i) {
+        if (!handles[i]) {
+          Done d;
+          d.res.status = PDHCG_NUMERICAL_ERROR;
+          S->done[admit[i].ticket] = std::move(d);
+          S->pending.erase(admit[i].ticket);
+          S->stats.rejected++;
+          continue;
+        }
+        Live l;
+        l.ticket = admit[i].ticket;
+        l.P = handles[i];
+        l.bytes = admit[i].bytes;
+        l.slot = S->free_slots.back();
+        S->free_slots.pop_back();
+        SolverState st = initial_state(l.P);
+        cudaMemcpyAsync(S->d_states + l.slot, &st, sizeof(st), cudaMemcpyHostToDevice, S->stream);
+        S->stats.hbm_in_use += l.bytes;
+        S->stats.admitted++;
+        S->live.push_back(l);
+      }
+      S->stats.live = int32_t(S->live.size());
+    }
+    if (S->live.empty()) continue;
+    // ---- one slice over every live solve ----
+    std::vector<pdhcg_problem*> probs;
+    std::vector<double*> xo, yo;
+    std::vector<SolverState*> sts;
+    for (auto& l : S->live) {
+      probs.push_back(l.P);
+      xo.push_back(l.P->x_stage);
+      yo.push_back(l.P->y_stage);
+    }
+    // states must be contiguous in launch order: gather slots into launch order
+    const int count = int(S->live.size());
+    std::vector<SolverState> hst(static_cast<size_t>(count));
+    // the pool launch addresses states by launch index: use a compact device array
+    SolverState* d_tmp = nullptr;
+    if (cudaMalloc(&d_tmp, sizeof(SolverState) * size_t(count)) != cudaSuccess) {
+      S->worker_error = "out of device memory for a slice";
+      std::this_thread::sleep_for(std::chrono::milliseconds(1));
+      continue;
+    }
+    for (int i = 0; i < count; ++i)
+      cudaMemcpyAsync(d_tmp + i, S->d_states + S->live[size_t(i)].slot, sizeof(SolverState),
+                      cudaMemcpyDeviceToDevice, S->stream);
+    int rc = launch_pool_slice(probs.data(), count, d_tmp, xo.data(), yo.data(), S->slice_iters);
+    cudaMemcpyAsync(hst.data(), d_tmp, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, S->stream);
+    for (int i = 0; i < count; ++i)
+      cudaMemcpyAsync(S->d_states + S->live[size_t(i)].slot, d_tmp + i, sizeof(SolverState),
+                      cudaMemcpyDeviceToDevice, S->stream);
+    cudaStreamSynchronize(S->stream);
+    cudaFree(d_tmp);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stats.launches++;
+    }
+    // ---- retire finished solves ----
+    std::vector<Live> keep;
+    for (int i = 0; i < count; ++i) {
+      Live& l = S->live[size_t(i)];
+      const SolverState& st = hst[size_t(i)];
+      const bool finished = st.status != 0 || st.device_error || rc != PDHCG_OK;
+      if (!finished) {
+        keep.push_back(l);
+        continue;
+      }
+      Done d;
+      fill_result(l.P, st, &d.res);
+      if (st.device_error || rc != PDHCG_OK) d.res.status = PDHCG_NUMERICAL_ERROR;
+      d.x.resize(size_t(l.P->n));
+      d.y.resize(size_t(l.P->m));
+      cudaMemcpy(d.x.data(), l.P->x_stage, sizeof(double) * size_t(l.P->n), cudaMemcpyDeviceToHost);
+      if (l.P->m) cudaMemcpy(d.y.data(), l.P->y_stage, sizeof(double) * size_t(l.P->m), cudaMemcpyDeviceToHost);
+      pdhcg_destroy(l.P);
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->done[l.ticket] = std::move(d);
+      S->pending.erase(l.ticket);
+      S->stats.completed++;
+      S->stats.hbm_in_use -= l.bytes;
+      S->free_slots.push_back(l.slot);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->live.swap(keep);
+    S->stats.live = int32_t(S->live.size());
+  }
+}
+
+}  // namespace pdhcg
+
+using namespace pdhcg;
+
+extern "C" {
+
+int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_params* params,
+                        void* cuda_stream, pdhcg_server_t** out) {
+  if (!out || max_slots < 1 || hbm_budget_bytes == 0) {
+    set_error("server_create: bad arguments");
+    return PDHCG_E_INVALID;
+  }
+  *out = nullptr;
+  auto* S = new pdhcg_server();
+  if (params) {
+    int rc = check_params_c(params);
+    if (rc) {
+      delete S;
+      return rc;
+    }
+    S->prm = *params;
+  } else {
+    pdhcg_default_params(&S->prm);
+  }
+  S->budget = hbm_budget_bytes;
+  S->max_slots = max_slots;
+  S->max_queue = size_t(max_slots) * 64;
+  S->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&S->device);
+  if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
+    delete S;
+    set_error("server_create: cudaMalloc failed");
+    return PDHCG_E_OOM;
+  }
+  for (int i = max_slots - 1; i >= 0; --i) S->free_slots.push_back(i);
+  S->worker = std::thread(worker_loop, S);
+  *out = S;
+  return PDHCG_OK;
+}
+
+int pdhcg_submit(pdhcg_server_t* S, const pdhcg_csr* Q, const pdhcg_csr* A, const double* c,
+                 const double* lc, const double* uc, const double* lv, const double* uv, uint64_t* ticket) {
+  if (!S || !A || !ticket) {
+    set_error("submit: bad arguments");
+    return PDHCG_E_INVALID;
+  }
+  Request r;
+  CreateInput in{Q, A, c, lc, uc, lv, uv};
+  int rc = footprint_of(in, S->prm, &r.bytes);  // validates the problem, host side only
+  if (rc) return rc;
+  if (r.bytes > S->budget) {
+    set_error("submit: the problem alone exceeds the HBM budget");
+    return PDHCG_E_OOM;
+  }
+  OwnedProblem& p = r.prob;
+  p.n = A->ncols;
+  p.m = A->nrows;
+  p.has_q = Q != nullptr;
+  if (Q) copy_csr(Q, p.qp, p.qc, p.qv);
+  copy_csr(A, p.ap, p.ac, p.av);
+  p.c.assign(c, c + p.n);
+  p.lv.assign(lv, lv + p.n);
+  p.uv.assign(uv, uv + p.n);
+  if (p.m) {
+    p.lc.assign(lc, lc + p.m);
+    p.uc.assign(uc, uc + p.m);
+  }
+  r.t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->queue.size() >= S->max_queue) {
+      set_error("submit: queue full");
+      return PDHCG_E_BUSY;
+    }
+    r.ticket = S->next_ticket++;
+    *ticket = r.ticket;
+    S->pending[r.ticket] = 1;
+    S->queue.push_back(std::move(r));
+    S->stats.submitted++;
+    S->stats.queued = int32_t(S->queue.size());
+  }
+  S->cv.notify_one();
+  return PDHCG_OK;
+}
+
+int pdhcg_poll(pdhcg_server_t* S, uint64_t ticket, pdhcg_result* res, double* x_out, double* y_out) {
+  if (!S) return PDHCG_E_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) {
+    if (S->pending.count(ticket)) return PDHCG_PENDING;
+    set_error("poll: unknown ticket");
+    return PDHCG_E_NOT_FOUND;
+  }
+  if (res) *res = it->second.res;
+  if (x_out && !it->second.x.empty()) std::memcpy(x_out, it->second.x.data(), sizeof(double) * it->second.x.size());
+  if (y_out && !it->second.y.empty()) std::memcpy(y_out, it->second.y.data(), sizeof(double) * it->second.y.size());
+  S->done.erase(it);
+  return PDHCG_OK;
+}
+
+int pdhcg_server_get_stats(pdhcg_server_t* S, pdhcg_server_stats* st) {
+  if (!S || !st) return PDHCG_E_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *st = S->stats;
+  return PDHCG_OK;
+}
+
+void pdhcg_server_destroy(pdhcg_server_t* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  cudaSetDevice(S->device);
+  for (auto& l : S->live) pdhcg_destroy(l.P);
+  if (S->d_states) cudaFree(S->d_states);
+  delete S;
+}
+
+}  // extern "C"

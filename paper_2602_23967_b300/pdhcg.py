@@ -275,5 +275,54 @@ def solve_batch(problems, want_solutions=True):
     return out
 
 
+class Server:
+    """Continuous-batching serving loop (pdhcg_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, params: Params | None = None, stream=None):
+        self.params = params if params is not None else default_params()
+        h = _P()
+        check(lib().pdhcg_server_create(C.c_size_t(hbm_budget_bytes), int(max_slots), C.byref(self.params),
+                                        _P(stream) if stream else None, C.byref(h)), "pdhcg_server_create")
+        self.handle = h
+        self.sizes = {}
+
+    def submit(self, qp):
+        h = _qp_args(qp)
+        t = C.c_uint64()
+        check(lib().pdhcg_submit(self.handle, C.byref(h["Q"].s) if "Q" in h else None, C.byref(h["A"].s),
+                                 _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]),
+                                 C.byref(t)), "pdhcg_submit")
+        self.sizes[t.value] = (int(qp.n), int(qp.m))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (x, y, result dict)."""
+        n, m = self.sizes[ticket]
+        x = np.zeros(n)
+        y = np.zeros(max(m, 1))
+        res = Result()
+        rc = check(lib().pdhcg_poll(self.handle, C.c_uint64(ticket), C.byref(res), _dp(x), _dp(y)), "pdhcg_poll")
+        if rc == PENDING:
+            return None
+        del self.sizes[ticket]
+        return x, y[:m], res.as_dict()
+
+    def stats(self):
+        st = ServerStats()
+        check(lib().pdhcg_server_get_stats(self.handle, C.byref(st)), "pdhcg_server_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdhcg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def strerror(code):
     return lib().pdhcg_strerror(code).decode()

@@ -136,10 +136,12 @@ def test_factor_portfolio_with_long_row_multi_cta():
     assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
 
 
-def test_large_sparse_mid_size_fp64_fp32():
+def test_large_sparse_mid_size_fp64_mixed():
+    # FP32 iterates stall above 1e-5 on this class; FP32 matrix values with FP64
+    # vectors (mixed) reach the 1e-6 bar
     qp = W.large_sparse_qp(n=20000, m=10000, seed=0)
     check_optimal_parity(qp)
-    check_optimal_parity(qp, precision="fp32", eps=1e-5, obj_tol=1e-5, max_iter=200000)
+    check_optimal_parity(qp, precision="mixed", max_iter=200000)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

@@ -1,0 +1,102 @@
+"""Serving loop (pdhcg_server_*): continuous batching at iteration granularity.
+
+Each request's result is the same alone (pdhcg_solve) and in the mix: pausing a
+solve at a slice boundary and resuming it in a later launch changes nothing in
+its arithmetic, so the comparison is to 1e-12 (in practice bit-identical).
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2602_23967_b300 import pdhcg
+from paper_2602_23967_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def wait_all(srv, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            r = srv.poll(t)
+            if r is not None:
+                out[t] = r
+        if time.time() - t0 > timeout:
+            raise TimeoutError(f"{len(out)}/{len(tickets)} finished")
+        time.sleep(0.002)
+    return out
+
+
+def test_mix_results_equal_alone():
+    prm = pdhcg.default_params(precision="mixed", eps_tol=1e-6)
+    qps = ([W.mpc_qp(seed=300 + i) for i in range(10)] +
+           [W.random_qp(n=400, m=200, n_eq=100, m_rows=100, per_row=10, seed=50 + i) for i in range(3)] +
+           [W.infeasible_qp(n=8, m=4, seed=1)])
+    srv = pdhcg.Server(hbm_budget_bytes=2 << 30, max_slots=8, params=prm)
+    try:
+        tickets = []
+        for q in qps:
+            tickets.append(srv.submit(q))
+            time.sleep(0.001)          # arrivals while others run
+        got = wait_all(srv, tickets)
+        st = srv.stats()
+        assert st["completed"] == len(qps) and st["launches"] > 1
+        assert st["hbm_in_use"] == 0 and st["live"] == 0
+    finally:
+        srv.close()
+    for q, t in zip(qps, tickets):
+        p = pdhcg.Problem(q, prm)
+        xs, ys, rs = p.solve()
+        p.close()
+        xm, ym, rm = got[t]
+        assert rm["status_name"] == rs["status_name"]
+        assert rm["iterations"] == rs["iterations"]
+        assert np.max(np.abs(xm - xs)) <= 1e-12 * (1 + np.max(np.abs(xs)))
+        if q.m:
+            assert np.max(np.abs(ym - ys)) <= 1e-12 * (1 + np.max(np.abs(ys)))
+    assert got[tickets[-1]][2]["status_name"] == "PRIMAL_INFEASIBLE"
+
+
+def test_budget_and_slots_limit_admission():
+    prm = pdhcg.default_params(precision="mixed")
+    qps = [W.mpc_qp(T=40, seed=400 + i) for i in range(6)]
+    pair = pdhcg.create_batch(qps[:2], prm)       # pooled handles, as the server creates them
+    per = max(p.device_bytes() for p in pair) + 4096
+    for p in pair:
+        p.close()
+    budget = int(2.5 * per)
+    srv = pdhcg.Server(hbm_budget_bytes=budget, max_slots=4, params=prm)
+    try:
+        tickets = [srv.submit(q) for q in qps]
+        seen_live = 0
+        t0 = time.time()
+        while srv.stats()["completed"] < len(qps) and time.time() - t0 < 60:
+            st = srv.stats()
+            seen_live = max(seen_live, st["live"])
+            assert st["hbm_in_use"] <= budget
+            time.sleep(0.001)
+        assert 1 <= seen_live <= 2
+        got = wait_all(srv, tickets)
+        assert all(r[2]["status_name"] == "OPTIMAL" for r in got.values())
+    finally:
+        srv.close()
+
+
+def test_invalid_request_rejected_alone():
+    prm = pdhcg.default_params(precision="mixed")
+    srv = pdhcg.Server(hbm_budget_bytes=1 << 30, max_slots=4, params=prm)
+    try:
+        good = srv.submit(W.mpc_qp(seed=7))
+        bad = W.mpc_qp(seed=8)
+        bad.c = bad.c.copy()
+        bad.c[0] = np.nan
+        with pytest.raises(pdhcg.PdhcgError):
+            srv.submit(bad)
+        got = wait_all(srv, [good])
+        assert got[good][2]["status_name"] == "OPTIMAL"
+    finally:
+        srv.close()
