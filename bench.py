@@ -1,0 +1,387 @@
+"""Benchmark: batched MPC QPs solved to relative KKT 1e-6 on B300, QP solves/sec.
+
+Workload (default ``--workload mpc_batch``): 4,096 linear-MPC QPs, horizon
+T ~ U{10..50}, 12 states / 4 inputs (n = 16T, m = 12T), solved to relative KKT
+1e-6 by one persistent launch of the PDHCG-II kernel (pdhcg_solve_batch), FP32
+matrix values with FP64 vectors and reductions.  Also timed: the plain
+one-at-a-time solver on a sample of the same instances, the end-to-end path
+through the public API (problem upload + device setup + solve + result
+download), and the FP64 CPU oracle on a sample (cpu_baseline).
+
+``--impl reference`` times the CPU oracle alone on the same workload and metric.
+Multi-GPU (torchrun): every rank solves its own 4,096 instances (weak scaling,
+no collective in the data path; one barrier and a max over ranks for timing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_23967_b300 import workloads as W  # noqa: E402
+
+METRIC = "QP solves/sec and SpMV HBM GB/s at rel. KKT 1e-6, batched/served vs plain"
+UNIT = "solves/s"
+EPS = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mpc_batch", choices=["mpc_batch"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=96)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def instances(count, rank):
+    """Rank r solves its own ``count`` instances (seed 1000 r): weak scaling by instance."""
+    return W.mpc_batch(count=count, seed=1000 * rank)
+
+
+def config_of(args):
+    """The workload description both arms print."""
+    return {"workload": f"mpc_batch: {args.count} MPC QPs per GPU (T~U{{10..50}}, 12 states, "
+                        f"4 inputs, n=16T, m=12T), rel. KKT {EPS:g}, one persistent launch",
+            "l2": "inputs larger than L2 (whole batch ~0.5 GB)", "precision": args.precision}
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """Largest ``value`` over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, count, steps, total_ms):
+    """Whole-job solves/s: every rank solved ``count`` instances per step."""
+    return world * count * steps / (total_ms * 1e-3)
+
+
+def input_bytes(qp):
+    b = qp.A.nnz * 12 + (qp.m + 1) * 8 + 5 * 8 * qp.n + 2 * 8 * qp.m
+    if qp.Q is not None:
+        b += qp.Q.nnz * 12 + (qp.n + 1) * 8
+    return b
+
+
+def algorithmic_bytes(qp, iterations, mat_bytes=4, idx_bytes=4, vec_bytes=8):
+    """Algorithmic bytes of the batched kernel for one instance (diagonal Q, so no inner solver).
+
+    Per PDHG step: A x and A^T y streamed once (2 Z (v + i)), row pointers
+    (4 (n + m + 2)), vectors s (10 n + 7 m): Phase I reads x, c, lv, uv, diag Q,
+    anchor and gathers y, writes x+, xbar, x_new; Phase II gathers xbar, reads
+    y, lc, uc, anchor and writes y+, y_new.  Every 64 steps the check adds one
+    pass over A (two gathers), A^T and Q plus 8 n + 6 m vector reads."""
+    Z = qp.A.nnz
+    W_ = qp.Q.nnz if qp.Q is not None else 0
+    n, m = qp.n, qp.m
+    per_it = 2 * Z * (mat_bytes + idx_bytes) + 4 * (n + m + 2) + vec_bytes * (10 * n + 7 * m)
+    per_check = (2 * Z + W_) * (mat_bytes + idx_bytes) + vec_bytes * (8 * n + 6 * m)
+    return iterations * per_it + (iterations // 64) * per_check
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
+    """FP64 CPU oracle (single thread) on the first instances of the workload."""
+    import oracle
+    oracle.build()
+    t0 = time.time()
+    results = []
+    for q in qps[:sample]:
+        x, y, r = oracle.solve(q, oracle.default_params(eps_tol=EPS))
+        results.append(r)
+        if time.time() - t0 > time_budget_s:
+            break
+    dt = time.time() - t0
+    return len(results) / dt, results, dt
+
+
+# DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
+# (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
+# kernel sources it was taken on (hash below), else the roofline reports null.
+TRAFFIC_CAPTURE = {"bytes": 445_622_272, "instances": 512,
+                   "sources_sha256": "53f796a1275f0af3da5f783b420de2d1989783d8d82a21af6deba1da549c8228",
+                   "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
+KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "launch.h", "kernels_impl.cuh",
+                  "pdhcg_internal.h", "kernels_mixed.cu")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_23967_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(count):
+    """Measured DRAM bytes scaled to ``count`` instances, or None if the kernel changed."""
+    cap = TRAFFIC_CAPTURE
+    if cap["sources_sha256"] != kernel_sources_sha256():
+        return None
+    return cap["bytes"] * count / cap["instances"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    qps = instances(args.count, 0)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(qps, 4, 5.0)
+    vals = []
+    t_all = 0.0
+    done = 0
+    for k in range(args.steps):
+        sps, res, dt = cpu_oracle_sample(qps[k * 8:], max(8, args.cpu_sample // 4), 12.0)
+        vals.append(sps)
+        t_all += dt
+        done += len(res)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": config_of(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} instances solved to 1e-6 by the FP64 C oracle, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2602_23967_b300 import pdhcg
+    pdhcg.lib()
+    prm = pdhcg.default_params(precision=args.precision, eps_tol=EPS)
+    stream = torch.cuda.Stream()
+    qps = instances(args.count, rank)
+    probs = pdhcg.create_batch(qps, prm, stream=stream.cuda_stream)
+
+    def step():
+        return pdhcg.solve_batch(probs, want_solutions=False)
+
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.time()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+            out = step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(step_ms), world, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    value = job_throughput(world, args.count, args.steps, total_ms)
+    iters = np.array([r["iterations"] for r in out])
+    statuses = [r["status_name"] for r in out]
+    kkt = np.array([max(r["r_primal"], r["r_dual"], r["r_gap"]) for r in out])
+
+    # roofline of the batched solve kernel (algorithmic bytes / device time per launch)
+    alg = sum(algorithmic_bytes(q, int(r["iterations"])) for q, r in zip(qps, out))
+    launch_s = (total_ms / args.steps) * 1e-3
+    peaks, peak_kind = measured_peaks()
+    achieved = alg / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_per_launch(args.count),
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": alg,
+                "note": "algorithmic bytes count every matrix/vector pass of every PDHG step; each instance "
+                        "stays in shared memory / L1 inside its CTA, so measured DRAM traffic (from a "
+                        "512-instance ncu capture, scaled by instance count) is far below them"}
+
+    result = {}
+    if rank == 0:
+        # plain one-at-a-time solver on a sample of the same instances
+        plain = probs[: args.plain_sample]
+        xo = torch.empty(max(p.n for p in plain), dtype=torch.float64, device="cuda")
+        yo = torch.empty(max(max(p.m for p in plain), 1), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for p in plain:
+            p.solve_dev(xo, yo)
+        torch.cuda.synchronize()
+        plain_sps = len(plain) / (time.time() - t0)
+
+        # end to end through the public API: upload + setup + solve + download, from host data
+        h2d = sum(input_bytes(q) for q in qps)
+        d2h = sum(8 * (q.n + q.m) for q in qps) + len(qps) * 160
+        e2e_t = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            ps = pdhcg.create_batch(qps, prm, stream=stream.cuda_stream)
+            sol = pdhcg.solve_batch(ps, want_solutions=True)
+            torch.cuda.synchronize()
+            e2e_t.append(time.time() - t0)
+            for p in ps:
+                p.close()
+        e2e_sps = args.count / float(np.median(e2e_t))
+
+        # CPU oracle baseline on a bounded sample, and the error against it
+        cpu_sps, cpu_res, cpu_dt = cpu_oracle_sample(qps, args.cpu_sample)
+        objs = np.array([r["primal_obj"] for r in out[: len(cpu_res)]])
+        oobj = np.array([r["primal_obj"] for r in cpu_res])
+        obj_err = float(np.max(np.abs(objs - oobj) / (1 + np.abs(oobj)))) if len(cpu_res) else None
+        result = dict(plain_sps=plain_sps, e2e_sps=e2e_sps, h2d=h2d, d2h=d2h, cpu_sps=cpu_sps,
+                      cpu_n=len(cpu_res), cpu_dt=cpu_dt, obj_err=obj_err)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f32 matrix values, f64 vectors and reductions", "fp64": "f64",
+                      "fp32": "f32 (f64 reductions)"}[args.precision],
+            "data": "synthetic",
+            "config": config_of(args),
+            "plain_solves_per_s": result.get("plain_sps"),
+            "batched_vs_plain": value / world / result["plain_sps"] if result.get("plain_sps") else None,
+            "solved_optimal": statuses.count("OPTIMAL"), "instances": len(statuses),
+            "kkt_max": float(kkt.max()), "iterations_mean": float(iters.mean()),
+            "iterations_max": int(iters.max()),
+            "error_vs_fp64_oracle": {"objective_rel_max": result.get("obj_err"),
+                                     "sample": result.get("cpu_n")},
+            "roofline": roofline,
+            "cpu_baseline": {"value": result.get("cpu_sps"), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {result.get('cpu_n')} of the {args.count} instances, full FP64 "
+                                       f"oracle solves to 1e-6 ({result.get('cpu_dt', 0):.1f} s, one thread)"},
+            "e2e": {"value": result.get("e2e_sps"), "unit": UNIT, "h2d_bytes_per_step": result.get("h2d"),
+                    "d2h_bytes_per_step": result.get("d2h")},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    for p in probs:
+        p.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

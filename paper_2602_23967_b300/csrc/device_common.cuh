@@ -273,7 +273,7 @@ __device__ __forceinline__ bool group_arrive_wait(unsigned* bar, int rank, int n
 // hierarchical barrier; warp 0 then sums all CTAs' partials in a fixed order and
 // shares the totals through shared memory.
 template <int BS, int NV>
-__device__ __noinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsigned maxmask) {
+__device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsigned maxmask) {
   static_assert(NV <= kSlots, "too many reduction slots");
   constexpr int W = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

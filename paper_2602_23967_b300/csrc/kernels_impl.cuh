@@ -18,8 +18,12 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
   size_t want = solve_dyn_smem() + extra;
   const size_t static_part = 8192;  // group_reduce / row-engine shared arrays
   if (want + static_part > size_t(optin)) want = size_t(optin) - static_part;
-  return cudaFuncSetAttribute(solve_kernel<kGroupBS, MatT, VecT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(want));
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel<kGroupBS, MatT, VecT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
+  if (e == cudaSuccess && kPoolBS != kGroupBS)
+    e = cudaFuncSetAttribute(solve_kernel<kPoolBS, MatT, VecT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(want));
+  return e;
 }
 
 template <class MatT, class VecT>

@@ -11,8 +11,13 @@ template <class MatT, class VecT>
 struct SetupArgs;
 
 // CTA sizes: multi-CTA groups (one large instance) and pooled single-CTA solves.
+// Pool CTAs of 128 threads idle fewer lanes on small instances (an MPC block has
+// a few hundred rows) and halve the per-instance local-memory footprint.
 constexpr int kGroupBS = 256;
-constexpr int kPoolBS = 256;
+#ifndef PDHCG_POOL_BS
+#define PDHCG_POOL_BS 128
+#endif
+constexpr int kPoolBS = PDHCG_POOL_BS;
 
 struct KernelLimits {
   int max_coresident_group;  // CTAs of the solve kernel resident at once (SMs x occupancy)
