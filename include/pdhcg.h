@@ -180,6 +180,37 @@ int pdhcg_solve_dev(pdhcg_t* prob, const double* x0_dev, const double* y0_dev, p
 int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result* res, double* const* x_out,
                       double* const* y_out);
 
+/* Allocation-free form of pdhcg_solve_batch.  The paper has no counterpart: it
+ * solves one QP per call; this is a deployment interface of this library.
+ *
+ * For callers that must not allocate while solving: a real-time loop (e.g. a
+ * model-predictive controller re-solving every control period) cannot take the
+ * latency of cudaMalloc or the device-wide synchronisation of cudaFree, and a
+ * process whose device memory is fully reserved by its own pool or budget would
+ * see such an allocation fail.  The per-call scratch (solver states, instance
+ * descriptors, work queue) lives in one static device array of about 1.1 MB per
+ * device, so this call makes no cudaMalloc / cudaFree or other allocating call.
+ *
+ * probs, count: as pdhcg_solve_batch (same precision, device and stream);
+ *   0 <= count <= PDHCG_NOALLOC_MAX_INSTANCES, else PDHCG_E_INVALID with a
+ *   message naming the limit.
+ * res: count results in host memory, or NULL.
+ * x_out_dev / y_out_dev: arrays of count DEVICE pointers (double, n_i resp. m_i
+ *   elements on the handles' device; each may be NULL), or NULL.  The kernel
+ *   writes the solutions there directly; the caller owns these buffers.
+ * Blocking: returns after the launch finished.  The queue cursor and error flag
+ *   in the scratch must start at zero, and every call resets them (with the
+ *   states and descriptors) before its launch.
+ * Set-up: the first call on each device looks up the scratch's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture on that device.
+ * Concurrency: the scratch is one per device per process, so overlapping calls
+ *   would race on it; the library serialises calls on a process-wide lock.
+ * Results equal pdhcg_solve_batch's for the same handles. */
+#define PDHCG_NOALLOC_MAX_INSTANCES 1024
+int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* res,
+                              double* const* x_out_dev, double* const* y_out_dev);
+
 /* eta used by the iteration and the ||A||_2 estimate of the scaled A (Sec. 3.2). */
 int pdhcg_get_eta(const pdhcg_t* prob, double* eta, double* norm_A);
 

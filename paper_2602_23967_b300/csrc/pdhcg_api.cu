@@ -1253,3 +1253,160 @@ extern "C" int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result*
                                  double* const* x_out, double* const* y_out) {
   return pdhcg::solve_batch_impl(probs, count, res, x_out, y_out, 0);
 }
+
+// ---- batched solve with static device scratch (no allocation) ----
+//
+// pdhcg_solve_batch above keeps its per-call scratch (solver states, instance
+// descriptors, work queue, solution staging) in a device buffer that it grows
+// with cudaMalloc / cudaFree.  This variant serves callers that must not
+// allocate while solving: a real-time loop (a model-predictive controller
+// re-solving its QPs every control period) cannot take the latency of
+// cudaMalloc, nor the device-wide synchronisation of cudaFree; and a process
+// whose device memory is already reserved in full by its own pool or budget
+// would fail such an allocation with out-of-memory in mid-run.  Its scratch is
+// one file-scope device array of fixed size, so it allocates no device, pinned
+// or host-heap memory on the success path.
+namespace pdhcg {
+
+// At most this many instances per call (states + descriptors + queue words).
+constexpr int kNoAllocMaxInstances = PDHCG_NOALLOC_MAX_INSTANCES;
+constexpr size_t kNoAllocStateBytes = ((sizeof(SolverState) * kNoAllocMaxInstances + 255) / 256) * 256;
+constexpr size_t kNoAllocInstBytes =
+    ((sizeof(Inst<double, double>) * kNoAllocMaxInstances + 255) / 256) * 256;
+constexpr size_t kNoAllocQueueWords = size_t(kNoAllocMaxInstances) + 8;
+constexpr size_t kNoAllocScratchBytes = kNoAllocStateBytes + kNoAllocInstBytes + 4 * kNoAllocQueueWords;
+static_assert(sizeof(Inst<float, double>) == sizeof(Inst<double, double>) &&
+                  sizeof(Inst<float, float>) == sizeof(Inst<double, double>),
+              "one descriptor stride for every precision");
+
+// The scratch itself: about 1.1 MB per device for 1024 instances, laid out as
+// [SolverState x max][Inst x max][int32 order x max, cursor, error flag, pad].
+static __device__ __align__(256) char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;                     // one call at a time per process
+static char* g_noalloc_dev[kNoAllocMaxDevices];     // scratch address per device, set once
+// Host-side staging of the same layout (static, so the call touches no heap).
+static SolverState g_noalloc_hstate[kNoAllocMaxInstances];
+alignas(256) static unsigned char g_noalloc_hinst[kNoAllocInstBytes];
+static int32_t g_noalloc_horder[kNoAllocQueueWords];
+static int64_t g_noalloc_hwork[kNoAllocMaxInstances];
+
+// Set-up, once per device, with that device current: the device address of the
+// scratch symbol.  The first call on each device does this, so that call should
+// come before any stream capture the caller runs on that device.
+static int noalloc_scratch(int device, char** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) {
+    set_error("solve_batch_noalloc: device ordinal beyond the static table");
+    return PDHCG_E_INVALID;
+  }
+  if (!g_noalloc_dev[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_batch_noalloc: cudaGetSymbolAddress");
+    g_noalloc_dev[device] = static_cast<char*>(p);
+  }
+  *out = g_noalloc_dev[device];
+  return PDHCG_OK;
+}
+
+int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res,
+                             double* const* x_out_dev, double* const* y_out_dev) {
+  if (count < 0 || (count > 0 && !probs)) {
+    set_error("solve_batch_noalloc: bad arguments");
+    return PDHCG_E_INVALID;
+  }
+  if (count > kNoAllocMaxInstances) {
+    set_error("solve_batch_noalloc: count exceeds the static scratch limit of "
+              "PDHCG_NOALLOC_MAX_INSTANCES (1024) instances");
+    return PDHCG_E_INVALID;
+  }
+  if (count == 0) return PDHCG_OK;
+  const pdhcg_problem* P0 = probs[0];
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i] || probs[i]->precision != P0->precision || probs[i]->device != P0->device ||
+        probs[i]->stream != P0->stream) {
+      set_error("solve_batch_noalloc: handles must be non-NULL and share precision, device and stream");
+      return PDHCG_E_INVALID;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  CK(cudaSetDevice(P0->device));
+  char* base = nullptr;
+  int rc = noalloc_scratch(P0->device, &base);
+  if (rc) return rc;
+  cudaStream_t s = P0->stream;
+  SolverState* d_st = reinterpret_cast<SolverState*>(base);
+  char* d_inst = base + kNoAllocStateBytes;
+  int32_t* d_i32 = reinterpret_cast<int32_t*>(base + kNoAllocStateBytes + kNoAllocInstBytes);
+
+  // Longest-processing-time-first queue order (ties by index; std::sort needs no buffer).
+  for (int i = 0; i < count; ++i) {
+    g_noalloc_hstate[i] = initial_state(probs[i]);
+    g_noalloc_hwork[i] = (probs[i]->method != PDHCG_INNER_DIAG ? 4 * probs[i]->nnzQ : 0) +
+                         2 * probs[i]->nnzA + probs[i]->n + probs[i]->m;
+    g_noalloc_horder[i] = i;
+  }
+  std::sort(g_noalloc_horder, g_noalloc_horder + count, [](int32_t a, int32_t b) {
+    return g_noalloc_hwork[a] != g_noalloc_hwork[b] ? g_noalloc_hwork[a] > g_noalloc_hwork[b] : a < b;
+  });
+  // The words after the order must start at zero on every call: [count] is the
+  // queue cursor the CTAs advance atomically, [count + 1] the device error flag.
+  for (size_t w = size_t(count); w < kNoAllocQueueWords; ++w) g_noalloc_horder[w] = 0;
+
+  rc = dispatch_precision(P0->precision, [&](auto tag) {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    Inst<M, V>* hi = reinterpret_cast<Inst<M, V>*>(g_noalloc_hinst);
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      new (&hi[i]) Inst<M, V>(make_inst<M, V>(probs[i]));  // placement into the static staging
+      hi[i].st = d_st + i;
+      hi[i].x_out = x_out_dev ? x_out_dev[i] : nullptr;
+      hi[i].y_out = (y_out_dev && probs[i]->m) ? y_out_dev[i] : nullptr;
+      const size_t b = smem_need(probs[i]);
+      if (b <= kSmemVecBudget) need = std::max(need, b);
+    }
+    CK(cudaMemcpyAsync(d_st, g_noalloc_hstate, sizeof(SolverState) * size_t(count), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_inst, hi, sizeof(Inst<M, V>) * size_t(count), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_i32, g_noalloc_horder, sizeof(int32_t) * kNoAllocQueueWords, cudaMemcpyHostToDevice,
+                       s));
+    LaunchPlan plan;
+    plan.npool = count;
+    plan.pool_inst = d_i32;
+    plan.pool_next = d_i32 + count;
+    plan.err = d_i32 + count + 1;
+    plan.iter_budget = 0;
+    plan.smem_vec_bytes = int64_t(need);
+    plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P0->device));
+    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    const int grid = std::max(1, std::min(count, per_sm * sms));
+    cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_batch_noalloc launch");
+    CK(cudaMemcpyAsync(g_noalloc_hstate, d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
+    return PDHCG_OK;
+  });
+  if (rc) return rc;
+  // Returns only after the launch and the state read-back finished, so the next
+  // call (which holds the same lock) never overwrites scratch in use.
+  CK(cudaStreamSynchronize(s));
+  bool dev_err = false;
+  for (int i = 0; i < count; ++i) {
+    if (g_noalloc_hstate[i].device_error) dev_err = true;
+    if (res) fill_result(probs[i], g_noalloc_hstate[i], res + i);
+  }
+  if (dev_err) {
+    set_error("solve_batch_noalloc: a bounded device wait gave up");
+    return PDHCG_E_DEVICE_TIMEOUT;
+  }
+  return PDHCG_OK;
+}
+
+}  // namespace pdhcg
+
+extern "C" int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* res,
+                                         double* const* x_out_dev, double* const* y_out_dev) {
+  return pdhcg::solve_batch_noalloc_impl(probs, count, res, x_out_dev, y_out_dev);
+}

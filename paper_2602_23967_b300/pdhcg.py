@@ -102,6 +102,8 @@ def lib():
         L.pdhcg_solve_dev.argtypes = [_P, _P, _P, C.POINTER(Result), _P, _P]
         L.pdhcg_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(Result), C.POINTER(_D),
                                         C.POINTER(_D)]
+        L.pdhcg_solve_batch_noalloc.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(Result),
+                                                C.POINTER(_P), C.POINTER(_P)]
         L.pdhcg_get_eta.argtypes = [_P, _D, _D]
         L.pdhcg_get_scaling.argtypes = [_P, _D, _D]
         L.pdhcg_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -273,6 +275,24 @@ def solve_batch(problems, want_solutions=True):
     if want_solutions:
         return [(xs[i], ys[i][: problems[i].m], out[i]) for i in range(count)]
     return out
+
+
+NOALLOC_MAX_INSTANCES = 1024  # PDHCG_NOALLOC_MAX_INSTANCES
+
+
+def solve_batch_noalloc(problems, x_out=None, y_out=None):
+    """pdhcg_solve_batch_noalloc: the batched solve with static device scratch.
+
+    ``x_out`` / ``y_out``: lists of float64 CUDA tensors (n_i / m_i elements; an
+    entry may be None), or None.  Returns the result dicts."""
+    count = len(problems)
+    handles = (_P * max(count, 1))(*[p.handle for p in problems])
+    res = (Result * max(count, 1))()
+    ptr = (lambda t: _P(t.data_ptr()) if t is not None else None)
+    xp = (_P * count)(*[ptr(t) for t in x_out]) if x_out is not None else None
+    yp = (_P * count)(*[ptr(t) for t in y_out]) if y_out is not None else None
+    check(lib().pdhcg_solve_batch_noalloc(handles, count, res, xp, yp), "pdhcg_solve_batch_noalloc")
+    return [res[i].as_dict() for i in range(count)]
 
 
 class Server:
