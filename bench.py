@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mpc_batch", choices=["mpc_batch"])
     ap.add_argument("--count", type=int, default=4096)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--precision", default="dfloat", choices=["dfloat", "mixed", "fp64", "fp32"])
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96)
@@ -347,6 +347,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "f32 matrix values, f64 vectors and reductions", "fp64": "f64",
+                      "dfloat": "f32x2 (double-float) vectors on the FP32 pipe, f32 matrix values, f64 reductions",
                       "fp32": "f32 (f64 reductions)"}[args.precision],
             "data": "synthetic",
             "config": config_of(args),

@@ -64,6 +64,9 @@ extern "C" {
 #define PDHCG_FP32 1   /* FP32 matrix values, vectors and SpMV accumulation; FP64 inner
                           products, KKT norms, restart/PID decisions and certificates       */
 #define PDHCG_MIXED 2  /* FP32 matrix values, FP64 vectors and accumulation                 */
+#define PDHCG_DFLOAT 3 /* FP32 matrix values; vectors and accumulation in double-float (an
+                          unevaluated sum of two FP32 values, ~48-bit significand) on the
+                          FP32 pipe; FP64 inner products, KKT norms and decisions as above  */
 
 /* ---- primal subproblem solver (Sec. 2.2) ---- */
 #define PDHCG_INNER_AUTO 0  /* diagonal Q: closed form; else finite bounds: BB; else CG */
@@ -83,7 +86,7 @@ typedef struct {
  * checked so that older callers keep working when fields are appended. */
 typedef struct {
   uint32_t struct_size;
-  int32_t precision;          /* PDHCG_FP64 (default) / PDHCG_FP32 / PDHCG_MIXED            */
+  int32_t precision;          /* PDHCG_FP64 (default) / PDHCG_FP32 / PDHCG_MIXED / PDHCG_DFLOAT */
   double eps_tol;             /* KKT tolerance, Sec. 4.2 (1e-6)                              */
   double eps_inf;             /* infeasibility tolerance eps_inf, Sec. 5 (1e-8)              */
   double time_limit_s;        /* wall-clock limit measured on the device timer (3600)        */

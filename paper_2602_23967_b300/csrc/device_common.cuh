@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "pdhcg_internal.h"
 
 namespace pdhcg {
@@ -322,31 +323,10 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
       buf[lane * g.nblk + g.rank] = bp;
     }
     __syncwarp();
-    bool ok = true;
     if (lane == 0) {
-      ok = group_arrive_wait(g.bar32, g.rank, g.nblk, g.epoch, g.timeout_ns, g.err);
-      if (!ok) {
+      if (!group_arrive_wait(g.bar32, g.rank, g.nblk, g.epoch, g.timeout_ns, g.err)) {
         atomicExch(g.err, 1);
         *g.sm_flag = 1;
-      }
-    }
-    ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
-    if (ok) {
-#pragma unroll
-      for (int j = 0; j < NV; ++j) {
-        const bool mx = (maxmask >> j) & 1u;
-        double t = 0.0;
-        const double* src = buf + (size_t)j * g.nblk;
-        for (int b = lane; b < g.nblk; b += 32) {
-          const double o = __ldcg(src + b);
-          t = mx ? fmax(t, o) : t + o;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const double o = __shfl_xor_sync(kFull, t, off);
-          t = mx ? fmax(t, o) : t + o;
-        }
-        if (lane == 0) tot_sm[j] = t;
       }
     }
   }
@@ -355,6 +335,42 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
     g.failed = true;
     return false;
   }
+  // Every thread loads its CTAs' partials of all slots at once (one round trip
+  // to L2), then a fixed-order tree: lanes, warps.  The same in every CTA.
+  {
+    double t[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t[j] = 0.0;
+    for (int b = threadIdx.x; b < g.nblk; b += BS) {
+      double o[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) o[j] = __ldcg(buf + (size_t)j * g.nblk + b);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) t[j] = ((maxmask >> j) & 1u) ? fmax(t[j], o[j]) : t[j] + o[j];
+    }
+    double* sw2 = g.sm_warp + ((g.epoch + 1ull) & 1ull) * (W * kSlots);  // free half until the next epoch
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      const bool mx = (maxmask >> j) & 1u;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_xor_sync(kFull, t[j], off);
+        t[j] = mx ? fmax(t[j], o) : t[j] + o;
+      }
+      if (lane == 0) sw2[warp * kSlots + j] = t[j];
+    }
+    __syncthreads();
+    if (warp == 0 && lane < NV) {
+      const bool mx = (maxmask >> lane) & 1u;
+      double a = 0.0;
+      for (int w = 0; w < W; ++w) {
+        const double o = sw2[w * kSlots + lane];
+        a = mx ? fmax(a, o) : a + o;
+      }
+      tot_sm[lane] = a;
+    }
+  }
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = tot_sm[j];
   g.epoch++;
@@ -512,11 +528,11 @@ __device__ __forceinline__ void slice_finish(const X& x, int lane, const SlicePr
           if (u < p.W) g2v[u] = Acc(x.g2(p.c[u]));
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-          if (u < p.W) sums[1] += Acc(p.v[u]) * g2v[u];
+          if (u < p.W) madd(sums[1], p.v[u], g2v[u]);
       }
 #pragma unroll
       for (int u = 0; u < CH; ++u)
-        if (u < p.W) sums[0] += Acc(p.v[u]) * g1v[u];
+        if (u < p.W) madd(sums[0], p.v[u], g1v[u]);
     }
     const int* cp = x.S.col + p.b + lane;
     const MatT* vp = x.S.val + p.b + lane;
@@ -540,14 +556,20 @@ __device__ __forceinline__ void slice_finish(const X& x, int lane, const SlicePr
           if (j0 + u < p.W) g2v[u] = Acc(x.g2(c[u]));
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-          if (j0 + u < p.W) sums[1] += Acc(v[u]) * g2v[u];
+          if (j0 + u < p.W) madd(sums[1], v[u], g2v[u]);
       }
 #pragma unroll
       for (int u = 0; u < CH; ++u)
-        if (j0 + u < p.W) sums[0] += Acc(v[u]) * g1v[u];
+        if (j0 + u < p.W) madd(sums[0], v[u], g1v[u]);
     }
   }
 }
+
+// Columns of a slice whose loads are issued together (memory-level parallelism).
+#ifndef PDHCG_SLICE_UNROLL
+#define PDHCG_SLICE_UNROLL 4
+#endif
+constexpr int kSliceUnroll = PDHCG_SLICE_UNROLL;
 
 // Accumulate slot `lane` of slice s of source X into sums[0..NG) in column order.
 template <Ld LM, class Acc, class X>
@@ -558,12 +580,12 @@ __device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums
     const int W = int((e - b) >> 5);
     const int* cp = x.S.col + b + lane;
     const auto* vp = x.S.val + b + lane;
-#pragma unroll 4
+#pragma unroll kSliceUnroll
     for (int j = 0; j < W; ++j) {
       const int c = ldm<LM>(cp + 32 * j);
-      const Acc v = Acc(ldm<LM>(vp + 32 * j));
-      sums[0] += v * Acc(x.g1(c));
-      if constexpr (X::NG == 2) sums[1] += v * Acc(x.g2(c));
+      const auto v = ldm<LM>(vp + 32 * j);
+      madd(sums[0], v, Acc(x.g1(c)));
+      if constexpr (X::NG == 2) madd(sums[1], v, Acc(x.g2(c)));
     }
   }
 }
@@ -602,11 +624,11 @@ __device__ __forceinline__ void csr_part(const X& x, int row, int first, int ste
           if (k0 + u * step < e) g2v[u] = Acc(x.g2(c[u]));
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (k0 + u * step < e) sums[1] += Acc(v[u]) * g2v[u];
+          if (k0 + u * step < e) madd(sums[1], v[u], g2v[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (k0 + u * step < e) sums[0] += Acc(v[u]) * g1v[u];
+        if (k0 + u * step < e) madd(sums[0], v[u], g1v[u]);
     }
   }
 }
@@ -732,11 +754,11 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
                 if (u < na) g2v[u] = Acc(A.g2(cs[32 * u]));
 #pragma unroll
               for (int u = 0; u < CC; ++u)
-                if (u < na) sums[1] += Acc(vs[32 * u]) * g2v[u];
+                if (u < na) madd(sums[1], vs[32 * u], g2v[u]);
             }
 #pragma unroll
             for (int u = 0; u < CC; ++u)
-              if (u < na) sums[0] += Acc(vs[32 * u]) * g1v[u];
+              if (u < na) madd(sums[0], vs[32 * u], g1v[u]);
           }
         if constexpr (NB > 0)
           if (onB && ch * CC < wb) {
@@ -754,11 +776,11 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
                 if (u < nb) g2v[u] = Acc(B.g2(cs[32 * u]));
 #pragma unroll
               for (int u = 0; u < CC; ++u)
-                if (u < nb) sums[NA + 1] += Acc(vs[32 * u]) * g2v[u];
+                if (u < nb) madd(sums[NA + 1], vs[32 * u], g2v[u]);
             }
 #pragma unroll
             for (int u = 0; u < CC; ++u)
-              if (u < nb) sums[NA] += Acc(vs[32 * u]) * g1v[u];
+              if (u < nb) madd(sums[NA], vs[32 * u], g1v[u]);
           }
         __syncwarp();  // every lane is done with stage st before it is refilled
         st ^= 1;
@@ -767,6 +789,8 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
         continue;
       }
       // slice done
+#pragma unroll
+      for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
       if (row >= 0) epi(row, sums);
       if (sn >= s1) break;
       s = sn;
@@ -803,6 +827,8 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
     for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
     slice_dot<LM, Acc>(A, s, lane, sums);
     slice_dot<LM, Acc>(B, s, lane, sums + NA);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
     if (row >= 0) epi(row, sums);
   }
 #endif
@@ -815,9 +841,11 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
     csr_part<LM, Acc>(A, row, lane, 32, sums);
     csr_part<LM, Acc>(B, row, lane, 32, sums + NA);
 #pragma unroll
-    for (int q = 0; q < NS; ++q)
+    for (int q = 0; q < NS; ++q) {
+      acc_finish(sums[q]);
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) sums[q] += __shfl_xor_sync(kFull, sums[q], off);
+      for (int off = 16; off > 0; off >>= 1) sums[q] += shfl_xor(sums[q], off);
+    }
     if (lane == 0) epi(row, sums);
   }
   // huge rows: the whole CTA per row
@@ -830,8 +858,9 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
     csr_part<LM, Acc>(B, row, threadIdx.x, BS, sums + NA);
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
+      acc_finish(sums[q]);
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) sums[q] += __shfl_xor_sync(kFull, sums[q], off);
+      for (int off = 16; off > 0; off >>= 1) sums[q] += shfl_xor(sums[q], off);
       if (lane == 0) red[warp * 4 + q] = double(sums[q]);
     }
     __syncthreads();

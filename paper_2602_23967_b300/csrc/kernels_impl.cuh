@@ -33,6 +33,7 @@ int pool_blocks_per_sm(size_t smem_vec_bytes) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT>, kPoolBS,
                                                     solve_dyn_smem() + smem_vec_bytes) != cudaSuccess)
     return 0;
+  if (PDHCG_POOL_MAX_PER_SM > 0) nb = std::min(nb, int(PDHCG_POOL_MAX_PER_SM));
   return nb;
 }
 

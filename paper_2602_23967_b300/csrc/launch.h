@@ -18,6 +18,10 @@ constexpr int kGroupBS = 256;
 #define PDHCG_POOL_BS 128
 #endif
 constexpr int kPoolBS = PDHCG_POOL_BS;
+// Upper bound on resident pool CTAs per SM (0: as many as fit).
+#ifndef PDHCG_POOL_MAX_PER_SM
+#define PDHCG_POOL_MAX_PER_SM 0
+#endif
 
 struct KernelLimits {
   int max_coresident_group;  // CTAs of the solve kernel resident at once (SMs x occupancy)

@@ -32,6 +32,7 @@ int dispatch_precision(int precision, F&& f) {
     case PDHCG_FP64: return f(Prec<double, double>{});
     case PDHCG_FP32: return f(Prec<float, float>{});
     case PDHCG_MIXED: return f(Prec<float, double>{});
+    case PDHCG_DFLOAT: return f(Prec<float, dfloat>{});
     default: set_error("unknown precision"); return PDHCG_E_INVALID;
   }
 }
@@ -449,7 +450,10 @@ int max_group_blocks(int precision) {
 }
 
 // Largest per-instance vector footprint a pool CTA keeps in shared memory.
-constexpr size_t kSmemVecBudget = 110 * 1024;
+#ifndef PDHCG_SMEM_VEC_BUDGET_KB
+#define PDHCG_SMEM_VEC_BUDGET_KB 110
+#endif
+constexpr size_t kSmemVecBudget = size_t(PDHCG_SMEM_VEC_BUDGET_KB) * 1024;
 
 size_t smem_need(const pdhcg_problem* P) {
   return smem_vector_bytes(P->n, P->m, P->method, vec_bytes(P->precision));
@@ -667,7 +671,7 @@ static int check_params(const pdhcg_params* p) {
     set_error("params: struct_size mismatch (call pdhcg_default_params first)");
     return PDHCG_E_INVALID;
   }
-  if (p->precision < 0 || p->precision > 2 || p->k_eval < 1 || p->max_iter < 1 ||
+  if (p->precision < 0 || p->precision > 3 || p->k_eval < 1 || p->max_iter < 1 ||
       !(p->eps_tol > 0) || !(p->eps_inf > 0) || p->max_inner_iter < 0 || p->ruiz_iters < 0 ||
       p->inner < 0 || p->inner > 3 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
       (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1))))) {
@@ -734,7 +738,7 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
 
 int cached_max_group_blocks(int precision) {
   static std::mutex mu;
-  static int cache[3][64] = {};
+  static int cache[4][64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
@@ -1276,7 +1280,8 @@ constexpr size_t kNoAllocInstBytes =
 constexpr size_t kNoAllocQueueWords = size_t(kNoAllocMaxInstances) + 8;
 constexpr size_t kNoAllocScratchBytes = kNoAllocStateBytes + kNoAllocInstBytes + 4 * kNoAllocQueueWords;
 static_assert(sizeof(Inst<float, double>) == sizeof(Inst<double, double>) &&
-                  sizeof(Inst<float, float>) == sizeof(Inst<double, double>),
+                  sizeof(Inst<float, float>) == sizeof(Inst<double, double>) &&
+                  sizeof(Inst<float, dfloat>) == sizeof(Inst<double, double>),
               "one descriptor stride for every precision");
 
 // The scratch itself: about 1.1 MB per device for 1024 instances, laid out as

@@ -24,6 +24,18 @@
 
 namespace pdhcg {
 
+// Phase functions are separate device functions by default (smaller code, one
+// register allocation per phase); PDHCG_INLINE_PHASES=1 inlines them into the
+// control loop.
+#ifndef PDHCG_INLINE_PHASES
+#define PDHCG_INLINE_PHASES 0
+#endif
+#if PDHCG_INLINE_PHASES
+#define PDHCG_PHASE_ATTR __forceinline__
+#else
+#define PDHCG_PHASE_ATTR __noinline__
+#endif
+
 // Thread-local inner-product accumulator.
 template <class T>
 struct DotAcc;
@@ -46,6 +58,24 @@ struct DotAcc<float> {
     float s = hi + p;
     float bb = s - hi;
     float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e + pe;
+  }
+  __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+};
+
+// Double-float values: the products of the leading parts are summed exactly as
+// for FP32 (TwoProduct, TwoSum); the cross terms hi*lo enter the low word.
+template <>
+struct DotAcc<dfloat> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(dfloat a, dfloat b) {
+    const float p = a.hi * b.hi;
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    float s, e;
+    two_sum(hi, p, s, e);
     hi = s;
     lo += e + pe;
   }
@@ -98,7 +128,7 @@ struct StepScalars {
 // ---- Phase I: g = A^T y, b = x/tau - c - g, inner-solver start (Eq. primal_update) ----
 // returns {inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2}
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
+__device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
                                       StepScalars<VecT> sc, const RowCtx& rc) {
   using CT = VecT;
   using Acc = VecT;
@@ -154,7 +184,7 @@ __device__ __noinline__ Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int 
 // ---- CG Phase A: p = r + beta p_old (gathered on the fly, bit-identical to the
 // owner's write), q = H p; returns p^T q ----
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ double cg_phase_a(const Inst<MatT, VecT>& I, int prank, bool first, VecT be,
+__device__ PDHCG_PHASE_ATTR double cg_phase_a(const Inst<MatT, VecT>& I, int prank, bool first, VecT be,
                                           const VecT* __restrict__ pold, VecT* __restrict__ pnew, VecT itau,
                                           const RowCtx& rc) {
   using CT = VecT;
@@ -177,7 +207,7 @@ __device__ __noinline__ double cg_phase_a(const Inst<MatT, VecT>& I, int prank, 
 
 // ---- CG Phase B: x += alpha p, r -= alpha q; returns r^T r ----
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ double cg_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
+__device__ PDHCG_PHASE_ATTR double cg_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
                                           const VecT* __restrict__ pnew) {
   using CT = VecT;
   VecT* __restrict__ xT = I.xT;
@@ -195,7 +225,7 @@ __device__ __noinline__ double cg_phase_b(const Inst<MatT, VecT>& I, int lo, int
 
 // ---- xbar = 2 x+ - x, optionally copying x+ from another buffer into xT ----
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void write_xbar(const Inst<MatT, VecT>& I, int lo, int hi, const VecT* __restrict__ xp,
+__device__ PDHCG_PHASE_ATTR void write_xbar(const Inst<MatT, VecT>& I, int lo, int hi, const VecT* __restrict__ xp,
                                         const VecT* __restrict__ x, bool copy) {
   VecT* __restrict__ xT = I.xT;
   VecT* __restrict__ xbar = I.xbar;
@@ -208,7 +238,7 @@ __device__ __noinline__ void write_xbar(const Inst<MatT, VecT>& I, int lo, int h
 
 // ---- BB Phase B': projected step x_new = proj(x - alpha grad) ----
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void bb_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
+__device__ PDHCG_PHASE_ATTR void bb_phase_b(const Inst<MatT, VecT>& I, int lo, int hi, VecT al,
                                         const VecT* __restrict__ xc, const VecT* __restrict__ gc,
                                         VecT* __restrict__ xo) {
   const VecT* __restrict__ lv = I.lv;
@@ -219,7 +249,7 @@ __device__ __noinline__ void bb_phase_b(const Inst<MatT, VecT>& I, int lo, int h
 // ---- BB Phase A': gradient, BB quantities and natural residual at xc ----
 // returns {s^T s, s^T (g - g_prev), ||x - proj(x - g)||^2}
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int prank, const VecT* __restrict__ xc,
+__device__ PDHCG_PHASE_ATTR Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int prank, const VecT* __restrict__ xc,
                                           const VecT* __restrict__ xo, const VecT* __restrict__ gc,
                                           VecT* __restrict__ gn, VecT itau, const RowCtx& rc) {
   using CT = VecT;
@@ -246,7 +276,7 @@ __device__ __noinline__ Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int prank, 
 // ---- Phase II: A xbar, dual step (Eq. dual_update), reflected Halpern (Sec. 3.1) ----
 // returns {||y+ - y||^2, ||x+ - x||^2, ||x_new - x||^2} (the x terms only for CG / BB)
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int method, int cur, int vlo,
+__device__ PDHCG_PHASE_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int method, int cur, int vlo,
                                       int vhi, StepScalars<VecT> sc, const RowCtx& rc) {
   using CT = VecT;
   using Acc = VecT;
@@ -287,7 +317,7 @@ __device__ __noinline__ Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int 
 // ---- check phase: KKT residual pieces on the original data (Sec. 4.2) and the
 // infeasibility tests' pieces (Sec. 5.1, 5.2), with Delta = T(z) - z ----
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
+__device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
   const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
   const VecT* __restrict__ xT = I.xT;
@@ -353,7 +383,7 @@ __device__ __noinline__ Red<18> check_phase(const Inst<MatT, VecT>& I, int prank
 
 // ---- output: unscaled solution (x = D x+, y = E y+) or normalised rays ----
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ Red<2> ray_norms(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
+__device__ PDHCG_PHASE_ATTR Red<2> ray_norms(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
                                          double dn) {
   const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
@@ -370,7 +400,7 @@ __device__ __noinline__ Red<2> ray_norms(const Inst<MatT, VecT>& I, int cur, int
 }
 
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void write_outputs(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
+__device__ PDHCG_PHASE_ATTR void write_outputs(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi,
                                            int status, double dn, double mxy, double mxx) {
   const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
@@ -398,7 +428,7 @@ __device__ __noinline__ void write_outputs(const Inst<MatT, VecT>& I, int cur, i
 
 // ---- restart: new anchor and iterate T(z) ----
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void restart_copy(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi) {
+__device__ PDHCG_PHASE_ATTR void restart_copy(const Inst<MatT, VecT>& I, int cur, int vlo, int vhi, int clo, int chi) {
   VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
   VecT* __restrict__ xa = I.xa;
@@ -418,7 +448,7 @@ __device__ __noinline__ void restart_copy(const Inst<MatT, VecT>& I, int cur, in
 }
 
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void init_point(const Inst<MatT, VecT>& I, int vlo, int vhi, int clo, int chi) {
+__device__ PDHCG_PHASE_ATTR void init_point(const Inst<MatT, VecT>& I, int vlo, int vhi, int clo, int chi) {
   for_elems<BS>(vlo, vhi, [&](int j) {
     double x0 = I.x_init ? I.x_init[j] / I.D[j] : 0.0;
     VecT xv = VecT(clampv(x0, double(I.lv[j]), double(I.uv[j])));
@@ -435,7 +465,7 @@ __device__ __noinline__ void init_point(const Inst<MatT, VecT>& I, int vlo, int 
 // The control loop: scalar state, decisions and group reductions; the row and
 // elementwise work is in the phase functions above.
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
+__device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
                                             const RowCtx& rc) {
   using CT = VecT;
   SolverState S = *I.st;
@@ -484,10 +514,16 @@ __device__ __noinline__ void solve_instance(Group<BS>& g, const Inst<MatT, VecT>
     // adaptive inner tolerance (Sec. 3.3)
     if (S.K == 0) S.eps_in = P.eps_inner_first * fmax(1.0, sqrt(red1[1]));
     else S.eps_in = fmin(S.eps_in, fmax(P.gamma_inner * S.omega * S.mv * inv_tau, P.eps_inner_min));
-    // With FP32 vectors the subproblem residual cannot be resolved below a few
-    // units in the last place of b: the inner solve stops there instead of
-    // running to its step cap (FP64 vectors: the paper's rule unchanged).
-    const double eps = sizeof(VecT) == 4 ? fmax(S.eps_in, 0x1p-20 * sqrt(red1[1])) : S.eps_in;
+    // With FP32 or double-float vectors the subproblem residual cannot be
+    // resolved below the rounding error of the gradient H x - b: the inner solve
+    // stops there instead of running to its step cap (FP64 vectors: the paper's
+    // rule unchanged).  FP32: a few units in the last place of b.  Double-float:
+    // 16 units of 2^-48 times ||H|| ||x|| + ||b||, bounded with ||x|| <= tau ||b||
+    // and ||H|| <= gersh + 1/tau by (1 + gersh tau) ||b||.
+    double floor_abs = 0.0;
+    if (sizeof(VecT) == 4) floor_abs = 0x1p-20 * sqrt(red1[1]);
+    else if (std::is_same<VecT, dfloat>::value) floor_abs = 0x1p-44 * (1.0 + S.gersh * S.tau) * sqrt(red1[1]);
+    const double eps = fmax(S.eps_in, floor_abs);
 
     // inner solve (Sec. 2.2)
     if (method == PDHCG_INNER_CG) {
@@ -699,7 +735,7 @@ __device__ __forceinline__ void copy_inst(Inst<MatT, VecT>& dst, const Inst<MatT
 }
 
 template <int BS, class MatT, class VecT>
-__device__ __noinline__ void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig, Inst<MatT, VecT>& I,
+__device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig, Inst<MatT, VecT>& I,
                                            const LaunchPlan& plan, const RowCtx& rc, char* base,
                                            int method) {
   const int n = Ig.n, m = Ig.m;
@@ -791,8 +827,11 @@ __device__ __noinline__ void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>&
 #ifndef PDHCG_MIN_BLOCKS
 #define PDHCG_MIN_BLOCKS 2
 #endif
+#ifndef PDHCG_POOL_MIN_BLOCKS
+#define PDHCG_POOL_MIN_BLOCKS PDHCG_MIN_BLOCKS
+#endif
 template <int BS, class MatT, class VecT>
-__global__ void __launch_bounds__(BS, PDHCG_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
+__global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_POOL_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
   __shared__ double sm_red[(BS / 32) * 4];

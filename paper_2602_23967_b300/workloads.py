@@ -326,6 +326,11 @@ def unbounded_qp(n=6, seed=0) -> QP:
     P = np.eye(n) - np.outer(d, d) / (d @ d)
     Qd = P @ (B.T @ B / n + np.eye(n)) @ P
     Qd = 0.5 * (Qd + Qd.T)
+    # Q d = 0 bit for bit (column 1 = -column 0), so that it also holds after any
+    # scaling that treats the two mirrored columns alike, and in FP32 storage
+    Qd[:, 1] = -Qd[:, 0]
+    Qd[1, :] = -Qd[0, :]
+    Qd[1, 1] = Qd[0, 0]
     Qd[np.abs(Qd) < 1e-14] = 0.0
     A = rng.standard_normal((2, n))
     A[:, 1] = -A[:, 0]                      # A d = 0
