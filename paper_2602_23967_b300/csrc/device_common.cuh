@@ -273,7 +273,8 @@ __device__ __forceinline__ bool group_arrive_wait(unsigned* bar, int rank, int n
 // several CTAs, warp 0 publishes the CTA partial and thread 0 passes the
 // hierarchical barrier; warp 0 then sums all CTAs' partials in a fixed order and
 // shares the totals through shared memory.
-template <int BS, int NV>
+// kWarpTotals: v already holds this warp's totals (the same in every lane).
+template <int BS, int NV, bool kWarpTotals = false>
 __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsigned maxmask) {
   static_assert(NV <= kSlots, "too many reduction slots");
   constexpr int W = BS / 32;
@@ -282,11 +283,13 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     double t = v[j];
-    const bool mx = (maxmask >> j) & 1u;
+    if constexpr (!kWarpTotals) {
+      const bool mx = (maxmask >> j) & 1u;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      double o = __shfl_xor_sync(kFull, t, off);
-      t = mx ? fmax(t, o) : t + o;
+      for (int off = 16; off > 0; off >>= 1) {
+        double o = __shfl_xor_sync(kFull, t, off);
+        t = mx ? fmax(t, o) : t + o;
+      }
     }
     if (lane == 0) sw[warp * kSlots + j] = t;
   }

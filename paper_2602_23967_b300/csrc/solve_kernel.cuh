@@ -36,6 +36,11 @@ namespace pdhcg {
 #define PDHCG_PHASE_ATTR __noinline__
 #endif
 
+template <int NV>
+struct Red {
+  double v[NV];
+};
+
 // Thread-local inner-product accumulator.
 template <class T>
 struct DotAcc;
@@ -82,6 +87,45 @@ struct DotAcc<dfloat> {
   __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
 };
 
+// Thread partials -> values handed to group_reduce.  FP64 / FP32 accumulators
+// hand over their thread partials (group_reduce sums them across the warp).
+// Double-float partials are summed across the warp here, in double-float on the
+// FP32 pipe, and lane j converts total j to FP64, so the warp issues one
+// conversion for all NV values; group_reduce then skips its warp stage
+// (kWarpTotals below).
+template <class T>
+struct WarpTotals : std::false_type {};
+template <>
+struct WarpTotals<dfloat> : std::true_type {};
+
+template <int NV, class T>
+__device__ __forceinline__ Red<NV> finish_dots(const DotAcc<T> (&a)[NV]) {
+  Red<NV> r;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) r.v[j] = a[j].get();
+  return r;
+}
+template <int NV>
+__device__ __forceinline__ Red<NV> finish_dots(const DotAcc<dfloat> (&a)[NV]) {
+  static_assert(NV <= 32, "one lane per value");
+  const int ln = threadIdx.x & 31;
+  dfloat mine(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float h, l;
+    two_sum(a[j].hi, a[j].lo, h, l);
+    dfloat t(h, l);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += shfl_xor(t, off);
+    if (ln == j) mine = t;
+  }
+  const double conv = double(mine);
+  Red<NV> r;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) r.v[j] = __shfl_sync(0xffffffffu, conv, j);
+  return r;
+}
+
 // PID update of log(omega) at the end of a restarted round (Eq. pid).  Skipped
 // when either movement is below 1e-10; omega kept within omega0 * [1/c, c].
 __device__ __forceinline__ void pid_update(SolverState& S, const DevParams& P, double dx,
@@ -114,10 +158,6 @@ struct PhaseClock {
   }
 };
 
-template <int NV>
-struct Red {
-  double v[NV];
-};
 
 // Scalars of one PDHG step in the vector arithmetic type.
 template <class CT>
@@ -178,7 +218,8 @@ __device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, 
           a0.add_prod(d, d);
         }
       });
-  return Red<4>{{a0.get(), a1.get(), a2.get(), a3.get()}};
+  const DotAcc<CT> acc[4] = {a0, a1, a2, a3};
+  return finish_dots<4>(acc);
 }
 
 // ---- CG Phase A: p = r + beta p_old (gathered on the fly, bit-identical to the
@@ -202,7 +243,8 @@ __device__ PDHCG_PHASE_ATTR double cg_phase_a(const Inst<MatT, VecT>& I, int pra
         qv[i] = qi;
         apq.add_prod(pi, qi);
       });
-  return apq.get();
+  const DotAcc<CT> acc[1] = {apq};
+  return finish_dots<1>(acc).v[0];
 }
 
 // ---- CG Phase B: x += alpha p, r -= alpha q; returns r^T r ----
@@ -220,7 +262,8 @@ __device__ PDHCG_PHASE_ATTR double cg_phase_b(const Inst<MatT, VecT>& I, int lo,
     rv[i] = ri;
     arr.add_prod(ri, ri);
   });
-  return arr.get();
+  const DotAcc<CT> acc[1] = {arr};
+  return finish_dots<1>(acc).v[0];
 }
 
 // ---- xbar = 2 x+ - x, optionally copying x+ from another buffer into xT ----
@@ -270,7 +313,8 @@ __device__ PDHCG_PHASE_ATTR Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int pra
                             const CT d = xi - clampv(xi - gi, lv[i], uv[i]);
                             anr.add_prod(d, d);
                           });
-  return Red<3>{{ass.get(), asy.get(), anr.get()}};
+  const DotAcc<CT> acc[3] = {ass, asy, anr};
+  return finish_dots<3>(acc);
 }
 
 // ---- Phase II: A xbar, dual step (Eq. dual_update), reflected Halpern (Sec. 3.1) ----
@@ -311,7 +355,8 @@ __device__ PDHCG_PHASE_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, 
       amv.add_prod(xnj - xj, xnj - xj);
     });
   }
-  return Red<3>{{ady.get(), adx.get(), amv.get()}};
+  const DotAcc<CT> acc[3] = {ady, adx, amv};
+  return finish_dots<3>(acc);
 }
 
 // ---- check phase: KKT residual pieces on the original data (Sec. 4.2) and the
@@ -468,6 +513,7 @@ template <int BS, Ld LM, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
                                             const RowCtx& rc) {
   using CT = VecT;
+  constexpr bool kWT = WarpTotals<VecT>::value;  // phase dots arrive as warp totals
   SolverState S = *I.st;
   if (S.status != 0) return;
   const DevParams& P = I.prm;
@@ -496,9 +542,31 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
 
   while (ok) {
     const int cur = S.cur;
-    const double inv_tau = 1.0 / S.tau, inv_sigma = 1.0 / S.sigma;
-    const double wk = double(S.k + 1) / double(S.k + 2), ak = 1.0 / double(S.k + 2);
-    StepScalars<CT> sc{CT(inv_tau), CT(inv_sigma), CT(S.sigma), CT(wk), CT(ak), CT(P.theta), CT(1.0 + P.theta)};
+    // The step's scalars 1/tau, 1/sigma, sigma, (k+1)/(k+2), 1/(k+2), theta,
+    // 1 + theta: lane q computes scalar q as one quotient and converts it to the
+    // vector type, so the warp issues one FP64 division and one conversion for
+    // all seven (the FP64 pipe is narrow); the values are the same as computing
+    // each on its own.  Every lane then takes them by shuffle.
+    double inv_tau, inv_sigma;
+    StepScalars<CT> sc;
+    {
+      const int ln = threadIdx.x & 31;
+      const double kp2 = double(S.k + 2);
+      const double num = ln == 2 ? S.sigma : ln == 3 ? double(S.k + 1) : ln == 5 ? P.theta
+                       : ln == 6 ? 1.0 + P.theta : 1.0;
+      const double den = ln == 0 ? S.tau : ln == 1 ? S.sigma : (ln == 3 || ln == 4) ? kp2 : 1.0;
+      const double q = num / den;
+      const CT qc = CT(q);
+      inv_tau = __shfl_sync(kFull, q, 0);
+      inv_sigma = __shfl_sync(kFull, q, 1);
+      sc.itau = shfl_idx(qc, 0);
+      sc.isig = shfl_idx(qc, 1);
+      sc.sig = shfl_idx(qc, 2);
+      sc.wk = shfl_idx(qc, 3);
+      sc.ak = shfl_idx(qc, 4);
+      sc.th = shfl_idx(qc, 5);
+      sc.th1 = shfl_idx(qc, 6);
+    }
 
     // Phase I
     double red1[4];
@@ -508,7 +576,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       for (int q = 0; q < 4; ++q) red1[q] = r.v[q];
     }
     PDHCG_CLK(0);
-    if (!group_reduce<BS, 4>(g, red1, 0u)) { ok = false; break; }
+    if (!group_reduce<BS, 4, kWT>(g, red1, 0u)) { ok = false; break; }
     PDHCG_CLK(5);
 
     // adaptive inner tolerance (Sec. 3.3)
@@ -521,8 +589,10 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     // 16 units of 2^-48 times ||H|| ||x|| + ||b||, bounded with ||x|| <= tau ||b||
     // and ||H|| <= gersh + 1/tau by (1 + gersh tau) ||b||.
     double floor_abs = 0.0;
-    if (sizeof(VecT) == 4) floor_abs = 0x1p-20 * sqrt(red1[1]);
-    else if (std::is_same<VecT, dfloat>::value) floor_abs = 0x1p-44 * (1.0 + S.gersh * S.tau) * sqrt(red1[1]);
+    if (method != PDHCG_INNER_DIAG) {
+      if (sizeof(VecT) == 4) floor_abs = 0x1p-20 * sqrt(red1[1]);
+      else if (std::is_same<VecT, dfloat>::value) floor_abs = 0x1p-44 * (1.0 + S.gersh * S.tau) * sqrt(red1[1]);
+    }
     const double eps = fmax(S.eps_in, floor_abs);
 
     // inner solve (Sec. 2.2)
@@ -535,13 +605,13 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
         VecT* pnew = pc ? I.p0 : I.p1;
         double pq[1] = {cg_phase_a<BS, LM>(I, prank, j == 0, CT(beta), pold, pnew, sc.itau, rc)};
         PDHCG_CLK(1);
-        if (!group_reduce<BS, 1>(g, pq, 0u)) { ok = false; break; }
+        if (!group_reduce<BS, 1, kWT>(g, pq, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
         if (!(pq[0] > 0.0)) break;
         const double alpha = rr / pq[0];
         double rn[1] = {cg_phase_b<BS>(I, vlo, vhi, CT(alpha), pnew)};
         PDHCG_CLK(2);
-        if (!group_reduce<BS, 1>(g, rn, 0u)) { ok = false; break; }
+        if (!group_reduce<BS, 1, kWT>(g, rn, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
         beta = rn[0] / rr;
         rr = rn[0];
@@ -581,7 +651,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
           v3[2] = r.v[2];
         }
         PDHCG_CLK(1);
-        if (!group_reduce<BS, 3>(g, v3, 0u)) { ok = false; break; }
+        if (!group_reduce<BS, 3, kWT>(g, v3, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
         { VecT* t = go; go = gc; gc = t; }
         ss = v3[0];
@@ -605,7 +675,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       red2[2] = r.v[2];
     }
     PDHCG_CLK(3);
-    if (!group_reduce<BS, 3>(g, red2, 0u)) { ok = false; break; }
+    if (!group_reduce<BS, 3, kWT>(g, red2, 0u)) { ok = false; break; }
     PDHCG_CLK(5);
     const double dy2 = red2[0];
     const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
