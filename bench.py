@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="length of the arrival trace")
     return ap.parse_args()
 
 
@@ -214,6 +216,52 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def serving_leg(args, prm, stream):
+    """Serving loop under Poisson arrivals of MPC requests: each request is
+    submitted at its arrival time through pdhcg_submit and collected with
+    pdhcg_poll; latency is the server's submit-to-ready wall time."""
+    from paper_2602_23967_b300 import pdhcg
+    trace = W.serving_trace(rate_per_s=args.serve_rate, duration_s=args.serve_seconds, seed=7,
+                            mix=(1.0, 0.0, 0.0))
+    qps = [W.build_request(k, s, n) for _, k, s, n in trace]
+    srv = pdhcg.Server(hbm_budget_bytes=100 << 30, max_slots=2 * 148, params=prm, stream=stream)
+    t_sub, out, pending = {}, {}, []
+    try:
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(trace) or pending:
+            now = time.perf_counter() - t0
+            while i < len(trace) and trace[i][0] <= now:
+                tk = srv.submit(qps[i])
+                t_sub[tk] = time.perf_counter() - t0
+                pending.append(tk)
+                i += 1
+            still = []
+            for tk in pending:
+                r = srv.poll(tk)
+                if r is None:
+                    still.append(tk)
+                else:
+                    out[tk] = r[2]
+            pending = still
+            if now > args.serve_seconds + 120.0:
+                break
+            time.sleep(0.0005)
+    finally:
+        srv.close()
+    lat = np.array([out[tk]["latency_seconds"] for tk in out])
+    ready = np.array([t_sub[tk] + out[tk]["latency_seconds"] for tk in out])
+    span = float(ready.max() - min(t_sub.values())) if len(out) else float("nan")
+    return {"arrivals": "Poisson, MPC requests (T~U{10..50})", "arrival_rate_per_s": args.serve_rate,
+            "requests": len(trace), "completed": len(out),
+            "optimal": sum(r["status_name"] == "OPTIMAL" for r in out.values()),
+            "solves_per_s": len(out) / span if len(out) else None,
+            "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if len(out) else None,
+            "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if len(out) else None,
+            "latency_max_ms": float(lat.max() * 1e3) if len(out) else None,
+            "hbm_budget_gb": 100, "max_slots": 2 * 148, "slice_iterations": 256}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -338,8 +386,11 @@ def run_ours(args):
         objs = np.array([r["primal_obj"] for r in out[: len(cpu_res)]])
         oobj = np.array([r["primal_obj"] for r in cpu_res])
         obj_err = float(np.max(np.abs(objs - oobj) / (1 + np.abs(oobj)))) if len(cpu_res) else None
+        serving = serving_leg(args, prm, stream.cuda_stream) if args.serve_seconds > 0 else None
+        if serving and serving.get("solves_per_s"):
+            serving["served_vs_plain"] = serving["solves_per_s"] / plain_sps
         result = dict(plain_sps=plain_sps, e2e_sps=e2e_sps, h2d=h2d, d2h=d2h, cpu_sps=cpu_sps,
-                      cpu_n=len(cpu_res), cpu_dt=cpu_dt, obj_err=obj_err)
+                      cpu_n=len(cpu_res), cpu_dt=cpu_dt, obj_err=obj_err, serving=serving)
 
     if rank == 0:
         line = {
@@ -364,6 +415,7 @@ def run_ours(args):
                                        f"oracle solves to 1e-6 ({result.get('cpu_dt', 0):.1f} s, one thread)"},
             "e2e": {"value": result.get("e2e_sps"), "unit": UNIT, "h2d_bytes_per_step": result.get("h2d"),
                     "d2h_bytes_per_step": result.get("d2h")},
+            "serving": result.get("serving"),
             "gpu_launches": args.steps,
             "clocks": clk,
             "wall_s_timed": wall,

@@ -125,6 +125,7 @@ typedef struct {
   double solve_seconds;       /* device-timer duration of the solve                          */
   int32_t power_iters;
   int32_t precision;
+  double latency_seconds;     /* serving loop: pdhcg_submit to result ready (wall clock); 0 otherwise */
 } pdhcg_result;
 
 typedef struct pdhcg_problem pdhcg_t;

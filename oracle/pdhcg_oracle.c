@@ -12,7 +12,7 @@
  *   PDHG step (primal prox solve, extrapolation, dual) .. Sec. 2.1, Eq. (pdhcg_update)
  *   primal subproblem: diagonal closed form, CG, BB-PG . Sec. 2.2 and Sec. 3.3
  *   reflected Halpern scheme ............................ Sec. 3.1
- *   tau = eta/omega, sigma = eta*omega, eta = 0.998/||A|| Sec. 3.2
+ *   tau = eta/omega, sigma = eta*omega, eta = 0.998/||A|| Sec. 3.2 (||A|| by Lanczos: reading)
  *   PID primal-weight update ............................ Sec. 3.2, Eq. (pid)
  *   adaptive inner tolerance ............................ Sec. 3.3
  *   KKT residuals r_primal, r_dual, r_gap ............... Sec. 4.2
@@ -188,31 +188,91 @@ void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
   free(rn);
 }
 
-/* ||A||_2 by power iteration on A^T A (reading: the paper fixes eta = 0.998/||A||
- * but not how ||A|| is computed).  Start at ones/sqrt(n); stop when the
- * Rayleigh estimate changes by at most tol relative, or after max_iter. */
+/* Number of eigenvalues below x of the symmetric tridiagonal matrix with
+ * diagonal a[0..k) and off-diagonal b[0..k-1): the number of negative pivots
+ * of the LDL^T factorisation of T - x I (Sturm count). */
+static int32_t sturm_below(const double* a, const double* b, int32_t k, double x) {
+  int32_t c = 0;
+  double d = 1.0;
+  for (int32_t i = 0; i < k; ++i) {
+    d = (a[i] - x) - (i > 0 ? (b[i - 1] * b[i - 1]) / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++c;
+  }
+  return c;
+}
+
+/* Largest eigenvalue of that tridiagonal matrix by bisection on the Sturm
+ * count, from [max diagonal, Gershgorin bound] down to adjacent doubles.
+ * Returns the upper end of the final interval. */
+static double tridiag_max_eig(const double* a, const double* b, int32_t k) {
+  double lo = a[0], hi = a[0];
+  for (int32_t i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = fmax(lo, a[i]);
+    hi = fmax(hi, a[i] + r);
+  }
+  hi = hi + 1e-12 * (fabs(hi) + 1e-300);
+  for (int32_t it = 0; it < 2000; ++it) {
+    const double x = 0.5 * (lo + hi);
+    if (!(x > lo && x < hi)) break;
+    if (sturm_below(a, b, k, x) == k) hi = x;
+    else lo = x;
+  }
+  return hi;
+}
+
+/* ||A||_2 (reading: the paper fixes eta = 0.998/||A|| but not how ||A|| is
+ * computed).  Lanczos on A^T A from v_1 = ones/sqrt(n), without
+ * reorthogonalisation (its largest Ritz value still converges from below):
+ *   t = A v_k, w = A^T t, alpha_k = ||t||^2, w -= alpha_k v_k + beta_{k-1} v_{k-1},
+ *   beta_k = ||w||, v_{k+1} = w / beta_k.
+ * The largest eigenvalue of the tridiagonal T_k (alpha, beta) is taken at
+ * k = 8, 16, 24, 36, 54, ... (each check k + max(8, k/2) after the last) and at
+ * max_iter; stop when two such values agree to tol relative, or when beta_k
+ * vanishes (the Krylov space is invariant and T_k is exact).  *iters_out:
+ * Lanczos steps taken. */
 double oracle_norm_estimate(const oracle_csr* A, const double* val, int32_t max_iter, double tol,
                             int32_t* iters_out) {
   int32_t n = A->ncols, m = A->nrows;
-  double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-  double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  double* v = (double*)malloc(sizeof(double) * nn);
+  double* vp = (double*)calloc(nn, sizeof(double));
+  double* w = (double*)malloc(sizeof(double) * nn);
   double* t = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  double* al = (double*)malloc(sizeof(double) * (size_t)(max_iter > 0 ? max_iter : 1));
+  double* be = (double*)malloc(sizeof(double) * (size_t)(max_iter > 0 ? max_iter : 1));
   for (int32_t j = 0; j < n; ++j) v[j] = 1.0 / sqrt((double)n);
-  double lam = 0.0, lam_prev = 0.0;
-  int32_t it = 0;
-  for (it = 1; it <= max_iter; ++it) {
+  double lam = 0.0, lam_prev = -1.0, bprev = 0.0;
+  int32_t next_check = 8, k = 0;
+  for (k = 1; k <= max_iter; ++k) {
     spmv(A, val, v, t);
     spmv_t(A, val, t, w);
-    lam = norm2(w, n);
-    if (!(lam > 0.0)) { lam = 0.0; break; }
-    for (int32_t j = 0; j < n; ++j) v[j] = w[j] / lam;
-    if (it > 1 && fabs(lam - lam_prev) <= tol * lam) break;
-    lam_prev = lam;
+    const double alpha = dot(t, t, m);
+    for (int32_t j = 0; j < n; ++j) w[j] = w[j] - alpha * v[j] - bprev * vp[j];
+    const double beta = norm2(w, n);
+    al[k - 1] = alpha;
+    be[k - 1] = beta;
+    const int invariant = !(beta > 1e-13 * sqrt(alpha * alpha + bprev * bprev));
+    if (k == next_check || invariant || k == max_iter) {
+      lam = tridiag_max_eig(al, be, k);
+      if (invariant || (lam_prev >= 0.0 && fabs(lam - lam_prev) <= tol * lam)) break;
+      lam_prev = lam;
+      next_check += next_check / 2 > 8 ? next_check / 2 : 8;
+    }
+    for (int32_t j = 0; j < n; ++j) {
+      vp[j] = v[j];
+      v[j] = w[j] / beta;
+    }
+    bprev = beta;
   }
-  if (iters_out) *iters_out = it > max_iter ? max_iter : it;
+  if (iters_out) *iters_out = k > max_iter ? max_iter : k;
   free(v);
+  free(vp);
   free(w);
   free(t);
+  free(al);
+  free(be);
   return sqrt(lam);
 }
 
@@ -461,7 +521,7 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
     gersh = fmax(gersh, s);
   }
 
-  /* --- step size eta = 0.998 / ||A|| (Sec. 3.2); norm by power iteration (reading) --- */
+  /* --- step size eta = 0.998 / ||A|| (Sec. 3.2); norm by Lanczos (reading) --- */
   int32_t piters = 0;
   double normA = m > 0 ? oracle_norm_estimate(A, av, prm->power_max_iter, prm->power_tol, &piters) : 0.0;
   double eta = normA > 0.0 ? 0.998 / normA : 1.0;

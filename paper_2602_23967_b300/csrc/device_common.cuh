@@ -155,6 +155,8 @@ struct Group {
   int* err;
   uint64_t timeout_ns;
   bool failed;
+  double* lz = nullptr;         // shared Lanczos coefficients (setup kernels only)
+  double* lz_out = nullptr;     // shared: the warp-computed eigenvalue
 
   // Row range of this CTA in a space whose partition table is `part`
   // (nblk+1 offsets), or the whole space for a single-CTA group.

@@ -118,7 +118,7 @@ struct pdhcg_problem {
   double *Qv_o = nullptr, *Av_o = nullptr, *ATv_o = nullptr;
   void *Qs = nullptr, *As = nullptr, *ATs = nullptr;  // MatT
   double *c_o = nullptr, *lv_o = nullptr, *uv_o = nullptr, *lc_o = nullptr, *uc_o = nullptr;
-  double *D = nullptr, *E = nullptr, *Dn = nullptr, *En = nullptr, *pv = nullptr, *pw = nullptr,
+  double *D = nullptr, *E = nullptr, *Dn = nullptr, *En = nullptr, *pv = nullptr, *pu = nullptr, *pw = nullptr,
          *pt = nullptr;
   void *c = nullptr, *lv = nullptr, *uv = nullptr, *lc = nullptr, *uc = nullptr, *qdiag = nullptr;
   int8_t *vtype = nullptr, *ctype = nullptr;

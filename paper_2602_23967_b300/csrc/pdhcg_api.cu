@@ -119,6 +119,7 @@ void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
   P->Dn = cv.take<double>(n);
   P->En = cv.take<double>(m);
   P->pv = cv.take<double>(n);
+  P->pu = cv.take<double>(n);
   P->pw = cv.take<double>(n);
   P->pt = cv.take<double>(m);
   P->c = cv.take_bytes(n, vb);
@@ -500,6 +501,7 @@ SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) 
   a.Dn = P->Dn;
   a.En = P->En;
   a.pv = P->pv;
+  a.pu = P->pu;
   a.pw = P->pw;
   a.pt = P->pt;
   a.Qs = static_cast<M*>(P->Qs);

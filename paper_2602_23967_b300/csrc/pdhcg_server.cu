@@ -58,7 +58,12 @@ struct Live {
   pdhcg_problem* P = nullptr;
   size_t bytes = 0;
   int slot = -1;
+  std::chrono::steady_clock::time_point t_submit;
 };
+
+static double seconds_since(std::chrono::steady_clock::time_point t) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+}
 
 struct Done {
   pdhcg_result res{};
@@ -85,7 +90,8 @@ struct pdhcg_server {
   bool stop = false;
   std::thread worker;
   // device side (worker thread only)
-  pdhcg::SolverState* d_states = nullptr;  // max_slots
+  pdhcg::SolverState* d_states = nullptr;  // max_slots, indexed by slot
+  pdhcg::SolverState* d_launch = nullptr;  // max_slots, in launch order for one slice
   double* d_out = nullptr;                  // per-slot solution buffers live in each handle
   std::vector<pdhcg::Live> live;
   std::vector<int> free_slots;
@@ -145,6 +151,7 @@ static void worker_loop(pdhcg_server* S) {
         if (!handles[i]) {
           Done d;
           d.res.status = PDHCG_NUMERICAL_ERROR;
+          d.res.latency_seconds = seconds_since(admit[i].t_submit);
           S->done[admit[i].ticket] = std::move(d);
           S->pending.erase(admit[i].ticket);
           S->stats.rejected++;
@@ -154,6 +161,7 @@ static void worker_loop(pdhcg_server* S) {
         l.ticket = admit[i].ticket;
         l.P = handles[i];
         l.bytes = admit[i].bytes;
+        l.t_submit = admit[i].t_submit;
         l.slot = S->free_slots.back();
         S->free_slots.pop_back();
         SolverState st = initial_state(l.P);
@@ -177,13 +185,9 @@ static void worker_loop(pdhcg_server* S) {
     // states must be contiguous in launch order: gather slots into launch order
     const int count = int(S->live.size());
     std::vector<SolverState> hst(static_cast<size_t>(count));
-    // the pool launch addresses states by launch index: use a compact device array
-    SolverState* d_tmp = nullptr;
-    if (cudaMalloc(&d_tmp, sizeof(SolverState) * size_t(count)) != cudaSuccess) {
-      S->worker_error = "out of device memory for a slice";
-      std::this_thread::sleep_for(std::chrono::milliseconds(1));
-      continue;
-    }
+    // the pool launch addresses states by launch index: a compact device array
+    // (allocated with the server, max_slots entries)
+    SolverState* d_tmp = S->d_launch;
     for (int i = 0; i < count; ++i)
       cudaMemcpyAsync(d_tmp + i, S->d_states + S->live[size_t(i)].slot, sizeof(SolverState),
                       cudaMemcpyDeviceToDevice, S->stream);
@@ -193,7 +197,6 @@ static void worker_loop(pdhcg_server* S) {
       cudaMemcpyAsync(S->d_states + S->live[size_t(i)].slot, d_tmp + i, sizeof(SolverState),
                       cudaMemcpyDeviceToDevice, S->stream);
     cudaStreamSynchronize(S->stream);
-    cudaFree(d_tmp);
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->stats.launches++;
@@ -216,6 +219,7 @@ static void worker_loop(pdhcg_server* S) {
       cudaMemcpy(d.x.data(), l.P->x_stage, sizeof(double) * size_t(l.P->n), cudaMemcpyDeviceToHost);
       if (l.P->m) cudaMemcpy(d.y.data(), l.P->y_stage, sizeof(double) * size_t(l.P->m), cudaMemcpyDeviceToHost);
       pdhcg_destroy(l.P);
+      d.res.latency_seconds = seconds_since(l.t_submit);
       std::lock_guard<std::mutex> lk(S->mu);
       S->done[l.ticket] = std::move(d);
       S->pending.erase(l.ticket);
@@ -258,7 +262,9 @@ int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_para
   S->max_queue = size_t(max_slots) * 64;
   S->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&S->device);
-  if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
+  if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
+      cudaMalloc(&S->d_launch, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
+    if (S->d_states) cudaFree(S->d_states);
     delete S;
     set_error("server_create: cudaMalloc failed");
     return PDHCG_E_OOM;
@@ -348,6 +354,7 @@ void pdhcg_server_destroy(pdhcg_server_t* S) {
   cudaSetDevice(S->device);
   for (auto& l : S->live) pdhcg_destroy(l.P);
   if (S->d_states) cudaFree(S->d_states);
+  if (S->d_launch) cudaFree(S->d_launch);
   delete S;
 }
 

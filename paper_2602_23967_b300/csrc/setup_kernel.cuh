@@ -7,8 +7,15 @@
 //  2. Scaled data in the iteration's types: Q, A, A^T values, c = D c,
 //     lv = lv / D, uv = uv / D, lc = E lc, uc = E uc, diag(Q), the Gershgorin
 //     bound of Q (BB step range), ||c||, ||finite(lc, uc)|| (initial primal weight).
-//  3. ||A||_2 of the scaled A by power iteration on A^T A in FP64 (Sec. 3.2 fixes
-//     eta = 0.998/||A|| but not how ||A|| is obtained).
+//  3. ||A||_2 of the scaled A (the values the iteration uses) by Lanczos on
+//     A^T A in FP64 (Sec. 3.2 fixes eta = 0.998/||A|| but not how ||A|| is
+//     obtained): t = A v_k, w = A^T t, alpha_k = ||t||^2,
+//     w -= alpha_k v_k + beta_{k-1} v_{k-1}, beta_k = ||w||, v_{k+1} = w / beta_k,
+//     from v_1 = ones/sqrt(n), without reorthogonalisation (the largest Ritz
+//     value converges from below regardless).  The largest eigenvalue of the
+//     tridiagonal T_k is taken at k = 8, 16, 24, 36, 54, ... (k + max(8, k/2))
+//     and at the step cap; the estimate stops when two agree to power_tol
+//     relative or when beta_k vanishes (invariant Krylov space, T_k exact).
 #pragma once
 #include "device_common.cuh"
 
@@ -23,7 +30,7 @@ struct SetupArgs {
   const double *c_o, *lv_o, *uv_o, *lc_o, *uc_o;
   const int32_t *var_part, *con_part;
   double *D, *E, *Dn, *En;            // scaling work (D, E hold the result)
-  double *pv, *pw, *pt;               // power-iteration work (n, n, m)
+  double *pv, *pu, *pw, *pt;          // Lanczos work: v_k, v_{k-1}, w (n each), t (m)
   MatT *Qs, *As, *ATs;                // scaled values (outputs)
   VecT *c, *lv, *uv, *lc, *uc, *qdiag;
   SolverState* st;
@@ -53,6 +60,54 @@ template <int BS, class F>
 __device__ __forceinline__ void rows_loop(int lo, int hi, int L, F f) {
   const int sub = threadIdx.x / L, sl = threadIdx.x & (L - 1), nsub = BS / L;
   for (int base = lo; base < hi; base += nsub) f(base + sub, base + sub < hi, sl);
+}
+
+// Lanczos steps kept per estimate (tridiagonal coefficients in shared memory).
+constexpr int kLanczosCap = 1024;
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..k) and off-diagonal b[0..k-1): negative pivots of T - x I.
+__device__ __forceinline__ int sturm_below(const double* a, const double* b, int k, double x) {
+  int c = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    d = (a[i] - x) - (i > 0 ? (b[i - 1] * b[i - 1]) / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++c;
+  }
+  return c;
+}
+
+// Largest eigenvalue of that matrix by 33-way multisection over the lanes of one
+// warp (every lane a different shift per round, 5 bits per round), from
+// [max diagonal, Gershgorin bound] down to adjacent doubles; returns the upper
+// end of the final interval.  Called by all 32 lanes of one warp.
+__device__ __forceinline__ double tridiag_max_eig_warp(const double* a, const double* b, int k) {
+  const int lane = threadIdx.x & 31;
+  double lo = a[0], hi = a[0];
+  for (int i = lane; i < k; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = fmax(lo, a[i]);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = fmax(lo, __shfl_xor_sync(kFull, lo, off));
+    hi = fmax(hi, __shfl_xor_sync(kFull, hi, off));
+  }
+  hi = hi + 1e-12 * (fabs(hi) + 1e-300);
+  for (int round = 0; round < 24; ++round) {
+    const double x = lo + (hi - lo) * (double(lane + 1) * (1.0 / 33.0));
+    const bool above = x > lo && x < hi && sturm_below(a, b, k, x) == k;
+    const unsigned mask = __ballot_sync(kFull, above);
+    const int f = mask ? __ffs(mask) - 1 : 32;
+    const double nhi = f < 32 ? __shfl_sync(kFull, x, f & 31) : hi;
+    const double nlo = f > 0 ? __shfl_sync(kFull, x, (f - 1) & 31) : lo;
+    const bool done = !(nhi - nlo > 0x1p-52 * fabs(nhi)) || (nhi == hi && nlo == lo);
+    lo = nlo;
+    hi = nhi;
+    if (done) break;
+  }
+  return hi;
 }
 
 template <int BS, class MatT, class VecT>
@@ -153,44 +208,68 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
     if (!group_reduce<BS, 5>(g, red, (1u << 2) | (1u << 3) | (1u << 4))) return;
   }
 
-  // ---- 3. ||A||_2 by power iteration on A^T A (FP64, scaled values on the fly) ----
-  double lam = 0.0, lam_prev = 0.0;
+  // ---- 3. ||A||_2 by Lanczos on A^T A (FP64 vectors, the scaled values) ----
+  double lam = 0.0, lam_prev = -1.0, bprev = 0.0;
   int it = 0;
   if (a.m > 0) {
+    const int kmax = a.power_max_iter < kLanczosCap ? a.power_max_iter : kLanczosCap;
     const double v0 = 1.0 / sqrt(double(a.n));
-    for (it = 1; it <= a.power_max_iter; ++it) {
-      const bool first = (it == 1);
-      const double lp = lam;
+    for_elems<BS>(vlo, vhi, [&](int j) {
+      a.pv[j] = v0;
+      a.pu[j] = 0.0;
+    });
+    if (!group_sync<BS>(g)) return;
+    int next_check = 8;
+    for (it = 1; it <= kmax; ++it) {
+      double tt[1] = {0.0};
       rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
-        double t = sub_row_sum(a.Ap, i, valid, sl, Lc, [&](int k) {
-          const int j = a.Ac[k];
-          const double vj = first ? v0 : a.pw[j] / lp;
-          return ((a.Av_o[k] * E[i]) * D[j]) * vj;
-        });
-        if (valid && sl == 0) a.pt[i] = t;
-      });
-      if (!group_sync<BS>(g)) return;
-      double w2[1] = {0.0};
-      rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
-        double w = sub_row_sum(a.ATp, j, valid, sl, Lv, [&](int k) {
-          const int i = a.ATc[k];
-          return ((a.ATv_o[k] * E[i]) * D[j]) * a.pt[i];
-        });
+        const double t = sub_row_sum(a.Ap, i, valid, sl, Lc,
+                                     [&](int k) { return double(a.As[k]) * a.pv[a.Ac[k]]; });
         if (valid && sl == 0) {
-          a.pw[j] = w;
-          w2[0] += w * w;
+          a.pt[i] = t;
+          tt[0] += t * t;
         }
       });
-      if (!group_reduce<BS, 1>(g, w2, 0u)) return;
-      lam = sqrt(w2[0]);
-      if (!(lam > 0.0)) {
-        lam = 0.0;
-        break;
+      if (!group_reduce<BS, 1>(g, tt, 0u)) return;
+      const double alpha = tt[0];
+      double ww[1] = {0.0};
+      rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
+        const double w = sub_row_sum(a.ATp, j, valid, sl, Lv,
+                                     [&](int k) { return double(a.ATs[k]) * a.pt[a.ATc[k]]; });
+        if (valid && sl == 0) {
+          const double wj = w - alpha * a.pv[j] - bprev * a.pu[j];
+          a.pw[j] = wj;
+          ww[0] += wj * wj;
+        }
+      });
+      if (!group_reduce<BS, 1>(g, ww, 0u)) return;
+      const double beta = sqrt(ww[0]);
+      if (threadIdx.x == 0) {
+        g.lz[it - 1] = alpha;
+        g.lz[kLanczosCap + it - 1] = beta;
       }
-      if (it > 1 && fabs(lam - lam_prev) <= a.power_tol * lam) break;
-      lam_prev = lam;
+      const bool invariant = !(beta > 1e-13 * sqrt(alpha * alpha + bprev * bprev));
+      if (it == next_check || invariant || it == kmax) {
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) {
+          const double l = tridiag_max_eig_warp(g.lz, g.lz + kLanczosCap, it);
+          if (threadIdx.x == 0) g.lz_out[0] = l;
+        }
+        __syncthreads();
+        lam = g.lz_out[0];
+        if (invariant || (lam_prev >= 0.0 && fabs(lam - lam_prev) <= a.power_tol * lam)) break;
+        lam_prev = lam;
+        next_check += next_check / 2 > 8 ? next_check / 2 : 8;
+      }
+      const double ib = 1.0 / beta;
+      for_elems<BS>(vlo, vhi, [&](int j) {
+        a.pu[j] = a.pv[j];
+        a.pv[j] = a.pw[j] * ib;
+      });
+      if (!group_sync<BS>(g)) return;
+      bprev = beta;
     }
-    if (it > a.power_max_iter) it = a.power_max_iter;
+    if (it > kmax) it = kmax;
   }
   if (g.rank == 0 && threadIdx.x == 0) {
     SolverState& S = *a.st;
@@ -213,8 +292,11 @@ __global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsi
                                                    double* part, int32_t* err, uint64_t timeout_ns) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
+  __shared__ double sm_lz[2 * kLanczosCap + 1];
   __shared__ int sm_flag;
   Group<BS> g;
+  g.lz = sm_lz;
+  g.lz_out = sm_lz + 2 * kLanczosCap;
   g.nblk = gridDim.x;
   g.rank = blockIdx.x;
   g.bar32 = reinterpret_cast<unsigned*>(bar);
@@ -238,9 +320,12 @@ __global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, Ve
                                                         int* next, int32_t* err, uint64_t timeout_ns) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
+  __shared__ double sm_lz[2 * kLanczosCap + 1];
   __shared__ int sm_flag;
   __shared__ int sm_idx;
   Group<BS> g;
+  g.lz = sm_lz;
+  g.lz_out = sm_lz + 2 * kLanczosCap;
   g.nblk = 1;
   g.rank = 0;
   g.bar32 = nullptr;

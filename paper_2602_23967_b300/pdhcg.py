@@ -60,6 +60,7 @@ class Result(C.Structure):
         ("primal_obj", C.c_double), ("dual_obj", C.c_double),
         ("eta", C.c_double), ("omega", C.c_double), ("norm_A", C.c_double),
         ("solve_seconds", C.c_double), ("power_iters", C.c_int32), ("precision", C.c_int32),
+        ("latency_seconds", C.c_double),
     ]
 
     def as_dict(self):

@@ -349,7 +349,7 @@ def unbounded_qp(n=6, seed=0) -> QP:
 
 
 def serving_trace(rate_per_s=200.0, duration_s=2.0, seed=0, n_range=(1_000, 100_000),
-                  factor_n=100_000, max_requests=None):
+                  factor_n=100_000, max_requests=None, mix=(0.70, 0.25, 0.05)):
     """Poisson arrival trace of a request mix: 70 % MPC (as ``mpc_qp``), 25 % random QPs as
     ``random_qp`` with n ~ U{1e3..1e5}, m = n/2, ~10 nonzeros per row (2 % of them made
     infeasible by a contradictory equality row), 5 % factor-model QPs with n = 1e5.
@@ -364,9 +364,9 @@ def serving_trace(rate_per_s=200.0, duration_s=2.0, seed=0, n_range=(1_000, 100_
             break
         u = rng.random()
         s = int(rng.integers(0, 2**31 - 1))
-        if u < 0.70:
+        if u < mix[0]:
             out.append((t, "mpc", s, 0))
-        elif u < 0.95:
+        elif u < mix[0] + mix[1]:
             nsz = int(rng.integers(n_range[0], n_range[1] + 1))
             kind = "random_infeasible" if rng.random() < 0.02 else "random"
             out.append((t, kind, s, nsz))

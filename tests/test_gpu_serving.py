@@ -53,6 +53,9 @@ def test_mix_results_equal_alone():
         xs, ys, rs = p.solve()
         p.close()
         xm, ym, rm = got[t]
+        # wall-clock submit-to-ready latency covers at least the device solve
+        assert rm["latency_seconds"] >= rm["solve_seconds"] > 0
+        assert rs["latency_seconds"] == 0.0
         assert rm["status_name"] == rs["status_name"]
         assert rm["iterations"] == rs["iterations"]
         assert np.max(np.abs(xm - xs)) <= 1e-12 * (1 + np.max(np.abs(xs)))
