@@ -247,6 +247,7 @@ def serving_leg(args, prm, stream):
             if now > args.serve_seconds + 120.0:
                 break
             time.sleep(0.0005)
+        st = srv.stats()
     finally:
         srv.close()
     lat = np.array([out[tk]["latency_seconds"] for tk in out])
@@ -259,7 +260,10 @@ def serving_leg(args, prm, stream):
             "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if len(out) else None,
             "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if len(out) else None,
             "latency_max_ms": float(lat.max() * 1e3) if len(out) else None,
-            "hbm_budget_gb": 100, "max_slots": 2 * 148, "slice_iterations": 256}
+            "hbm_budget_gb": 100, "max_slots": 2 * 148, "slice_iterations": 256,
+            "launches": st["launches"], "scheduler_seconds": {"admit": st["admit_seconds"],
+                                                             "slices": st["slice_seconds"],
+                                                             "retire": st["retire_seconds"]}}
 
 
 def run_reference(args):

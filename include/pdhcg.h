@@ -246,6 +246,9 @@ typedef struct {
   uint64_t launches;
   int32_t live, queued;
   size_t hbm_in_use;
+  /* scheduler wall time so far: admission (creation and device setup of the
+   * admitted problems), slices (launch to end), retirement (results back) */
+  double admit_seconds, slice_seconds, retire_seconds;
 } pdhcg_server_stats;
 
 int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_params* params,

@@ -933,7 +933,8 @@ int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes) 
 int check_params_c(const pdhcg_params* p) { return check_params(p); }
 
 int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states, double* const* x_out,
-                      double* const* y_out, int64_t iter_budget) {
+                      double* const* y_out, int64_t iter_budget, const int* slots, void* scratch,
+                      size_t scratch_bytes) {
   if (count <= 0) return PDHCG_OK;
   const pdhcg_problem* P0 = probs[0];
   CK(cudaSetDevice(P0->device));
@@ -946,7 +947,7 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
     size_t need = 0;
     for (int i = 0; i < count; ++i) {
       hi[size_t(i)] = make_inst<M, V>(probs[i]);
-      hi[size_t(i)].st = d_states + i;
+      hi[size_t(i)].st = d_states + (slots ? slots[i] : i);
       hi[size_t(i)].x_out = x_out ? x_out[i] : nullptr;
       hi[size_t(i)].y_out = y_out ? y_out[i] : nullptr;
       order[size_t(i)] = i;
@@ -954,9 +955,12 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
       if (b <= kSmemVecBudget) need = std::max(need, b);
     }
     const size_t ib = sizeof(Inst<M, V>) * size_t(count), ob = sizeof(int32_t) * order.size();
-    char* d = nullptr;
-    CK(cudaMalloc(&d, ib + ob));
-    std::unique_ptr<char, void (*)(char*)> guard(d, [](char* q) { cudaFree(q); });
+    char* d = static_cast<char*>(scratch);
+    std::unique_ptr<char, void (*)(char*)> guard(nullptr, [](char* q) { cudaFree(q); });
+    if (!d || scratch_bytes < ib + ob) {
+      CK(cudaMalloc(&d, ib + ob));
+      guard.reset(d);
+    }
     CK(cudaMemcpyAsync(d, hi.data(), ib, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d + ib, order.data(), ob, cudaMemcpyHostToDevice, s));
     int32_t* d_i32 = reinterpret_cast<int32_t*>(d + ib);
@@ -975,7 +979,9 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
     const int grid = std::max(1, std::min(count, per_sm * sms));
     cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d), plan, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "slice launch");
-    CK(cudaStreamSynchronize(s));
+    // the descriptors must outlive the launch: synchronise before a temporary
+    // buffer is freed (a caller's scratch stays valid until it synchronises)
+    if (guard) CK(cudaStreamSynchronize(s));
     return PDHCG_OK;
   });
 }

@@ -91,7 +91,11 @@ struct pdhcg_server {
   std::thread worker;
   // device side (worker thread only)
   pdhcg::SolverState* d_states = nullptr;  // max_slots, indexed by slot
-  pdhcg::SolverState* d_launch = nullptr;  // max_slots, in launch order for one slice
+  void* d_launch = nullptr;                 // launch descriptors of one slice
+  size_t launch_bytes = 0;
+  pdhcg::SolverState* h_states = nullptr;   // pinned copy of d_states
+  double* h_sol = nullptr;                  // pinned staging of finished solutions
+  size_t h_sol_len = 0;
   double* d_out = nullptr;                  // per-slot solution buffers live in each handle
   std::vector<pdhcg::Live> live;
   std::vector<int> free_slots;
@@ -129,6 +133,7 @@ static void worker_loop(pdhcg_server* S) {
     }
     // ---- admission: batched creation of everything admitted this round ----
     if (!admit.empty()) {
+      const auto t_adm0 = std::chrono::steady_clock::now();
       std::vector<CreateInput> in;
       in.reserve(admit.size());
       for (auto& r : admit) {
@@ -171,63 +176,98 @@ static void worker_loop(pdhcg_server* S) {
         S->live.push_back(l);
       }
       S->stats.live = int32_t(S->live.size());
+      S->stats.admit_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adm0).count();
     }
     if (S->live.empty()) continue;
-    // ---- one slice over every live solve ----
-    std::vector<pdhcg_problem*> probs;
-    std::vector<double*> xo, yo;
-    std::vector<SolverState*> sts;
-    for (auto& l : S->live) {
-      probs.push_back(l.P);
-      xo.push_back(l.P->x_stage);
-      yo.push_back(l.P->y_stage);
-    }
-    // states must be contiguous in launch order: gather slots into launch order
+    // ---- one slice over every live solve (states addressed by slot) ----
+    const auto t_slice0 = std::chrono::steady_clock::now();
     const int count = int(S->live.size());
-    std::vector<SolverState> hst(static_cast<size_t>(count));
-    // the pool launch addresses states by launch index: a compact device array
-    // (allocated with the server, max_slots entries)
-    SolverState* d_tmp = S->d_launch;
-    for (int i = 0; i < count; ++i)
-      cudaMemcpyAsync(d_tmp + i, S->d_states + S->live[size_t(i)].slot, sizeof(SolverState),
-                      cudaMemcpyDeviceToDevice, S->stream);
-    int rc = launch_pool_slice(probs.data(), count, d_tmp, xo.data(), yo.data(), S->slice_iters);
-    cudaMemcpyAsync(hst.data(), d_tmp, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, S->stream);
-    for (int i = 0; i < count; ++i)
-      cudaMemcpyAsync(S->d_states + S->live[size_t(i)].slot, d_tmp + i, sizeof(SolverState),
-                      cudaMemcpyDeviceToDevice, S->stream);
-    cudaStreamSynchronize(S->stream);
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      S->stats.launches++;
+    std::vector<pdhcg_problem*> probs(static_cast<size_t>(count));
+    std::vector<double*> xo(static_cast<size_t>(count)), yo(static_cast<size_t>(count));
+    std::vector<int> slots(static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) {
+      const Live& l = S->live[size_t(i)];
+      probs[size_t(i)] = l.P;
+      xo[size_t(i)] = l.P->x_stage;
+      yo[size_t(i)] = l.P->y_stage;
+      slots[size_t(i)] = l.slot;
     }
-    // ---- retire finished solves ----
+    int rc = launch_pool_slice(probs.data(), count, S->d_states, xo.data(), yo.data(), S->slice_iters,
+                               slots.data(), S->d_launch, S->launch_bytes);
+    cudaMemcpyAsync(S->h_states, S->d_states, sizeof(SolverState) * size_t(S->max_slots),
+                    cudaMemcpyDeviceToHost, S->stream);
+    cudaStreamSynchronize(S->stream);
+    const auto t_slice1 = std::chrono::steady_clock::now();
+    // ---- retire finished solves: their solutions come back in one batch ----
+    std::vector<int> fin;
+    size_t need = 0;
+    for (int i = 0; i < count; ++i) {
+      const SolverState& st = S->h_states[S->live[size_t(i)].slot];
+      if (st.status != 0 || st.device_error || rc != PDHCG_OK) {
+        fin.push_back(i);
+        need += size_t(S->live[size_t(i)].P->n) + size_t(S->live[size_t(i)].P->m);
+      }
+    }
+    if (need > S->h_sol_len) {
+      if (S->h_sol) cudaFreeHost(S->h_sol);
+      S->h_sol = nullptr;
+      S->h_sol_len = 0;
+      if (cudaMallocHost(&S->h_sol, sizeof(double) * need * 2) == cudaSuccess) S->h_sol_len = need * 2;
+    }
+    size_t off = 0;
+    if (S->h_sol) {
+      for (int i : fin) {
+        const pdhcg_problem* P = S->live[size_t(i)].P;
+        cudaMemcpyAsync(S->h_sol + off, P->x_stage, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost,
+                        S->stream);
+        off += size_t(P->n);
+        if (P->m)
+          cudaMemcpyAsync(S->h_sol + off, P->y_stage, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToHost,
+                          S->stream);
+        off += size_t(P->m);
+      }
+      cudaStreamSynchronize(S->stream);
+    }
     std::vector<Live> keep;
+    keep.reserve(size_t(count));
+    std::vector<char> done_flag(static_cast<size_t>(count), 0);
+    for (int i : fin) done_flag[size_t(i)] = 1;
+    off = 0;
+    std::vector<std::pair<uint64_t, Done>> out;
+    out.reserve(fin.size());
     for (int i = 0; i < count; ++i) {
       Live& l = S->live[size_t(i)];
-      const SolverState& st = hst[size_t(i)];
-      const bool finished = st.status != 0 || st.device_error || rc != PDHCG_OK;
-      if (!finished) {
+      if (!done_flag[size_t(i)]) {
         keep.push_back(l);
         continue;
       }
+      const SolverState& st = S->h_states[l.slot];
       Done d;
       fill_result(l.P, st, &d.res);
-      if (st.device_error || rc != PDHCG_OK) d.res.status = PDHCG_NUMERICAL_ERROR;
-      d.x.resize(size_t(l.P->n));
-      d.y.resize(size_t(l.P->m));
-      cudaMemcpy(d.x.data(), l.P->x_stage, sizeof(double) * size_t(l.P->n), cudaMemcpyDeviceToHost);
-      if (l.P->m) cudaMemcpy(d.y.data(), l.P->y_stage, sizeof(double) * size_t(l.P->m), cudaMemcpyDeviceToHost);
+      if (st.device_error || rc != PDHCG_OK || !S->h_sol) d.res.status = PDHCG_NUMERICAL_ERROR;
+      const size_t n = size_t(l.P->n), m = size_t(l.P->m);
+      if (S->h_sol) {
+        d.x.assign(S->h_sol + off, S->h_sol + off + n);
+        d.y.assign(S->h_sol + off + n, S->h_sol + off + n + m);
+      }
+      off += n + m;
       pdhcg_destroy(l.P);
       d.res.latency_seconds = seconds_since(l.t_submit);
-      std::lock_guard<std::mutex> lk(S->mu);
-      S->done[l.ticket] = std::move(d);
-      S->pending.erase(l.ticket);
+      out.emplace_back(l.ticket, std::move(d));
+    }
+    const auto t_retire1 = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t k = 0; k < out.size(); ++k) {
+      const Live& l = S->live[size_t(fin[k])];
+      S->done[out[k].first] = std::move(out[k].second);
+      S->pending.erase(out[k].first);
       S->stats.completed++;
       S->stats.hbm_in_use -= l.bytes;
       S->free_slots.push_back(l.slot);
     }
-    std::lock_guard<std::mutex> lk(S->mu);
+    S->stats.launches++;
+    S->stats.slice_seconds += std::chrono::duration<double>(t_slice1 - t_slice0).count();
+    S->stats.retire_seconds += std::chrono::duration<double>(t_retire1 - t_slice1).count();
     S->live.swap(keep);
     S->stats.live = int32_t(S->live.size());
   }
@@ -262,11 +302,14 @@ int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_para
   S->max_queue = size_t(max_slots) * 64;
   S->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&S->device);
+  S->launch_bytes = sizeof(Inst<double, double>) * size_t(max_slots) + sizeof(int32_t) * (size_t(max_slots) + 8);
   if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
-      cudaMalloc(&S->d_launch, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
+      cudaMalloc(&S->d_launch, S->launch_bytes) != cudaSuccess ||
+      cudaMallocHost(&S->h_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
     if (S->d_states) cudaFree(S->d_states);
+    if (S->d_launch) cudaFree(S->d_launch);
     delete S;
-    set_error("server_create: cudaMalloc failed");
+    set_error("server_create: allocation failed");
     return PDHCG_E_OOM;
   }
   for (int i = max_slots - 1; i >= 0; --i) S->free_slots.push_back(i);
@@ -355,6 +398,8 @@ void pdhcg_server_destroy(pdhcg_server_t* S) {
   for (auto& l : S->live) pdhcg_destroy(l.P);
   if (S->d_states) cudaFree(S->d_states);
   if (S->d_launch) cudaFree(S->d_launch);
+  if (S->h_states) cudaFreeHost(S->h_states);
+  if (S->h_sol) cudaFreeHost(S->h_sol);
   delete S;
 }
 

@@ -78,7 +78,8 @@ class ProblemData(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("rejected", C.c_uint64), ("launches", C.c_uint64), ("live", C.c_int32),
-                ("queued", C.c_int32), ("hbm_in_use", C.c_size_t)]
+                ("queued", C.c_int32), ("hbm_in_use", C.c_size_t), ("admit_seconds", C.c_double),
+                ("slice_seconds", C.c_double), ("retire_seconds", C.c_double)]
 
 
 _lib = None
