@@ -69,10 +69,21 @@ struct CreateInput {
   const double *c, *lc, *uc, *lv, *uv;
 };
 
+// Memory sources a long-running caller (the serving loop) hands to creation so
+// that it neither allocates nor frees synchronously: the arena comes from
+// `pool` in stream order on the creation stream and is freed with
+// cudaFreeAsync on that stream; the pinned staging buffer is reused (grown
+// only when too small).
+struct CreateAlloc {
+  cudaMemPool_t pool = nullptr;
+  void** pinned = nullptr;
+  size_t* pinned_bytes = nullptr;
+};
+
 // Create count handles (shared allocation when count > 1).  In pdhcg_api.cu.
 // pool_only: handles are solved by single CTAs only (no multi-CTA scratch).
 int create_impl(int count, const CreateInput* in, const pdhcg_params* params, void* stream,
-                pdhcg_problem** out, bool pool_only);
+                pdhcg_problem** out, bool pool_only, const CreateAlloc* alloc = nullptr);
 // Device bytes the handle of `in` would hold (host-side preparation only).
 int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes);
 SolverState initial_state(const pdhcg_problem* P);

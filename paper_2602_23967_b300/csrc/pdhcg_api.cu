@@ -753,7 +753,7 @@ int cached_max_group_blocks(int precision) {
 // Create count handles: one device allocation, one staging transfer per handle,
 // and (count > 1) one pooled setup launch.
 int create_impl(int count, const CreateInput* in, const pdhcg_params* params, void* stream,
-                pdhcg_t** out, bool pool_only) {
+                pdhcg_t** out, bool pool_only, const CreateAlloc* alloc) {
   pdhcg_params prm;
   if (params) {
     int rc = check_params(params);
@@ -814,12 +814,15 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
     stage_total += P[size_t(i)]->input_bytes;
   }
   void* raw = nullptr;
-  cudaError_t e = cudaMalloc(&raw, total);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool from_pool = alloc && alloc->pool;
+  cudaError_t e = from_pool ? cudaMallocFromPoolAsync(&raw, total, alloc->pool, s) : cudaMalloc(&raw, total);
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cudaMalloc(arena)");
   }
-  std::shared_ptr<void> owner(raw, [](void* q) { cudaFree(q); });
+  std::shared_ptr<void> owner = from_pool ? std::shared_ptr<void>(raw, [s](void* q) { cudaFreeAsync(q, s); })
+                                          : std::shared_ptr<void>(raw, [](void* q) { cudaFree(q); });
   SolverState* states = batch ? static_cast<SolverState*>(raw) : nullptr;
   for (int i = 0; i < count; ++i) {
     pdhcg_problem* Pi = P[size_t(i)];
@@ -830,13 +833,27 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
     real.base = static_cast<char*>(Pi->arena);
     carve(Pi, real, batch);
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // stage the inputs in pinned memory and copy each handle's prefix
   void* stage = nullptr;
-  e = cudaMallocHost(&stage, std::max<size_t>(stage_total, 1));
-  if (e != cudaSuccess) {
-    cleanup();
-    return cuda_fail(e, "cudaMallocHost(stage)");
+  const bool reuse = alloc && alloc->pinned && alloc->pinned_bytes;
+  if (reuse && *alloc->pinned_bytes >= stage_total && *alloc->pinned) {
+    stage = *alloc->pinned;
+  } else {
+    if (reuse && *alloc->pinned) {
+      cudaFreeHost(*alloc->pinned);
+      *alloc->pinned = nullptr;
+      *alloc->pinned_bytes = 0;
+    }
+    const size_t want = reuse ? std::max<size_t>(2 * stage_total, size_t(64) << 20) : std::max<size_t>(stage_total, 1);
+    e = cudaMallocHost(&stage, want);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "cudaMallocHost(stage)");
+    }
+    if (reuse) {
+      *alloc->pinned = stage;
+      *alloc->pinned_bytes = want;
+    }
   }
   size_t soff = 0;
   std::vector<SolverState> hstates(batch ? size_t(count) : 0);
@@ -854,7 +871,7 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
   if (batch && e == cudaSuccess)
     e = cudaMemcpyAsync(states, hstates.data(), sizeof(SolverState) * size_t(count), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFreeHost(stage);
+  if (!reuse) cudaFreeHost(stage);
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "upload");
@@ -879,8 +896,18 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       }
       const size_t abytes = sizeof(SetupArgs<M, V>) * args.size(), fbytes = sizeof(FillDesc) * fills.size();
       char* dscratch = nullptr;
-      CK(cudaMalloc(&dscratch, abytes + fbytes + 256));
-      std::unique_ptr<char, void (*)(char*)> guard(dscratch, [](char* q) { cudaFree(q); });
+      struct ScratchGuard {
+        char* p;
+        cudaStream_t s;
+        bool async;
+        ~ScratchGuard() {
+          if (p) async ? (void)cudaFreeAsync(p, s) : (void)cudaFree(p);
+        }
+      };
+      if (from_pool) CK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dscratch), abytes + fbytes + 256,
+                                                alloc->pool, s));
+      else CK(cudaMalloc(&dscratch, abytes + fbytes + 256));
+      ScratchGuard guard{dscratch, s, from_pool};
       int32_t* ctl = reinterpret_cast<int32_t*>(dscratch + abytes + fbytes);
       CK(cudaMemcpyAsync(dscratch, args.data(), abytes, cudaMemcpyHostToDevice, s));
       CK(cudaMemcpyAsync(dscratch + abytes, fills.data(), fbytes, cudaMemcpyHostToDevice, s));

@@ -1,16 +1,19 @@
 // pdhcg_server.cu — serving loop with continuous batching (pdhcg_server_*).
 //
-// A scheduler thread owns the device side.  Each round it
-//   1. admits queued requests while a slot is free and their device footprint
-//      fits the HBM budget (all admitted in one round are created together with
-//      the batched creation path: one allocation, one setup launch),
-//   2. advances every live solve by one slice of at most `slice_iters` PDHG
-//      steps in a single pooled launch (iterates, anchors, PID and restart state
-//      stay on the device between slices),
-//   3. retires the solves that stopped: copies their result and solution to host
-//      memory, frees their device memory and slot.
-// Requests that arrive while a slice runs are admitted at the next slice
-// boundary, so admission and retirement happen at iteration granularity.
+// Two host threads own the device side.
+//   Admission thread: takes queued requests while a slot is free and their
+//     device footprint fits the HBM budget, and creates everything it took
+//     together with the batched creation path (one allocation, one setup
+//     launch) on its own stream, so creation and device setup of new requests
+//     overlap the slices of the running ones.  Finished handles go to a ready list.
+//   Slice thread: at each slice boundary moves ready handles into free slots,
+//     advances every live solve by one slice of at most `slice_iters` PDHG steps
+//     in a single pooled launch (iterates, anchors, PID and restart state stay
+//     on the device between slices), then retires the solves that stopped:
+//     copies their results and solutions to host memory in one batch and frees
+//     their device memory and slot.
+// Requests join and leave the running set at slice boundaries, i.e. at
+// iteration granularity.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,8 +84,16 @@ struct pdhcg_server {
   cudaStream_t stream = nullptr;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv;
+  std::condition_variable cv;       // admission thread: new requests, freed capacity, stop
+  std::condition_variable cv_work;  // slice thread: ready handles, stop
   std::deque<pdhcg::Request> queue;
+  std::vector<pdhcg::Live> ready;   // created and set up, waiting for a slot
+  int reserved = 0;                 // requests taken for creation, ready or live (<= max_slots)
+  cudaStream_t admit_stream = nullptr;
+  std::thread admitter;
+  cudaMemPool_t pool = nullptr;     // device arenas of admitted requests (stream-ordered)
+  void* pinned_stage = nullptr;     // creation's host staging, reused
+  size_t pinned_stage_bytes = 0;
   std::unordered_map<uint64_t, pdhcg::Done> done;
   std::unordered_map<uint64_t, int> pending;  // ticket -> 1 (queued or live)
   uint64_t next_ticket = 1;
@@ -94,6 +105,7 @@ struct pdhcg_server {
   void* d_launch = nullptr;                 // launch descriptors of one slice
   size_t launch_bytes = 0;
   pdhcg::SolverState* h_states = nullptr;   // pinned copy of d_states
+  pdhcg::SolverState* h_init = nullptr;     // pinned initial states, by slot
   double* h_sol = nullptr;                  // pinned staging of finished solutions
   size_t h_sol_len = 0;
   double* d_out = nullptr;                  // per-slot solution buffers live in each handle
@@ -111,46 +123,54 @@ static void copy_csr(const pdhcg_csr* M, std::vector<int64_t>& rp, std::vector<i
   v.assign(M->val, M->val + M->nnz);
 }
 
-static void worker_loop(pdhcg_server* S) {
+static void admit_loop(pdhcg_server* S) {
   cudaSetDevice(S->device);
   while (true) {
     std::vector<Request> admit;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      if (S->live.empty()) {
-        S->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || !S->queue.empty(); });
-      }
+      auto can_take = [&] {
+        return !S->queue.empty() && S->reserved < S->max_slots &&
+               S->stats.hbm_in_use + S->queue.front().bytes <= S->budget;
+      };
+      S->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || can_take(); });
       if (S->stop) break;
-      size_t in_use = S->stats.hbm_in_use;
-      int free_n = int(S->free_slots.size());
-      while (!S->queue.empty() && free_n > 0 && in_use + S->queue.front().bytes <= S->budget) {
-        in_use += S->queue.front().bytes;
+      while (can_take()) {
+        S->stats.hbm_in_use += S->queue.front().bytes;  // reserved until retirement
+        S->reserved++;
         admit.push_back(std::move(S->queue.front()));
         S->queue.pop_front();
-        --free_n;
       }
       S->stats.queued = int32_t(S->queue.size());
     }
-    // ---- admission: batched creation of everything admitted this round ----
-    if (!admit.empty()) {
-      const auto t_adm0 = std::chrono::steady_clock::now();
-      std::vector<CreateInput> in;
-      in.reserve(admit.size());
-      for (auto& r : admit) {
-        r.prob.bind();
-        in.push_back(r.prob.input());
+    if (admit.empty()) continue;
+    // ---- batched creation and device setup on the admission stream ----
+    const auto t_adm0 = std::chrono::steady_clock::now();
+    std::vector<CreateInput> in;
+    in.reserve(admit.size());
+    for (auto& r : admit) {
+      r.prob.bind();
+      in.push_back(r.prob.input());
+    }
+    std::vector<pdhcg_problem*> handles(admit.size(), nullptr);
+    CreateAlloc al;
+    al.pool = S->pool;
+    al.pinned = &S->pinned_stage;
+    al.pinned_bytes = &S->pinned_stage_bytes;
+    int rc = create_impl(int(admit.size()), in.data(), &S->prm, S->admit_stream, handles.data(), true, &al);
+    if (rc != PDHCG_OK && admit.size() > 1) {
+      // fall back to one-by-one so one bad request fails alone
+      for (size_t i = 0; i < admit.size(); ++i) {
+        rc = create_impl(1, &in[i], &S->prm, S->admit_stream, &handles[i], true, &al);
+        if (rc != PDHCG_OK) handles[i] = nullptr;
       }
-      std::vector<pdhcg_problem*> handles(admit.size(), nullptr);
-      int rc = create_impl(int(admit.size()), in.data(), &S->prm, S->stream, handles.data(), true);
-      if (rc != PDHCG_OK && admit.size() > 1) {
-        // fall back to one-by-one so one bad request fails alone
-        for (size_t i = 0; i < admit.size(); ++i) {
-          rc = create_impl(1, &in[i], &S->prm, S->stream, &handles[i], true);
-          if (rc != PDHCG_OK) handles[i] = nullptr;
-        }
-      } else if (rc != PDHCG_OK) {
-        handles[0] = nullptr;
-      }
+    } else if (rc != PDHCG_OK) {
+      handles[0] = nullptr;
+    }
+    // creation synchronised its stream; the solves run on the slice stream
+    for (auto* h : handles)
+      if (h) h->stream = S->stream;
+    {
       std::lock_guard<std::mutex> lk(S->mu);
       for (size_t i = 0; i < admit.size(); ++i) {
         if (!handles[i]) {
@@ -160,6 +180,8 @@ static void worker_loop(pdhcg_server* S) {
           S->done[admit[i].ticket] = std::move(d);
           S->pending.erase(admit[i].ticket);
           S->stats.rejected++;
+          S->stats.hbm_in_use -= admit[i].bytes;
+          S->reserved--;
           continue;
         }
         Live l;
@@ -167,16 +189,34 @@ static void worker_loop(pdhcg_server* S) {
         l.P = handles[i];
         l.bytes = admit[i].bytes;
         l.t_submit = admit[i].t_submit;
+        S->ready.push_back(l);
+        S->stats.admitted++;
+      }
+      S->stats.admit_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adm0).count();
+    }
+    S->cv_work.notify_one();
+  }
+}
+
+static void worker_loop(pdhcg_server* S) {
+  cudaSetDevice(S->device);
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->live.empty())
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || !S->ready.empty(); });
+      if (S->stop) break;
+      // ---- ready handles take free slots (their initial state goes to the slot) ----
+      for (auto& l : S->ready) {
         l.slot = S->free_slots.back();
         S->free_slots.pop_back();
-        SolverState st = initial_state(l.P);
-        cudaMemcpyAsync(S->d_states + l.slot, &st, sizeof(st), cudaMemcpyHostToDevice, S->stream);
-        S->stats.hbm_in_use += l.bytes;
-        S->stats.admitted++;
+        S->h_init[l.slot] = initial_state(l.P);
+        cudaMemcpyAsync(S->d_states + l.slot, S->h_init + l.slot, sizeof(SolverState), cudaMemcpyHostToDevice,
+                        S->stream);
         S->live.push_back(l);
       }
+      S->ready.clear();
       S->stats.live = int32_t(S->live.size());
-      S->stats.admit_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adm0).count();
     }
     if (S->live.empty()) continue;
     // ---- one slice over every live solve (states addressed by slot) ----
@@ -263,8 +303,10 @@ static void worker_loop(pdhcg_server* S) {
       S->pending.erase(out[k].first);
       S->stats.completed++;
       S->stats.hbm_in_use -= l.bytes;
+      S->reserved--;
       S->free_slots.push_back(l.slot);
     }
+    if (!out.empty()) S->cv.notify_one();
     S->stats.launches++;
     S->stats.slice_seconds += std::chrono::duration<double>(t_slice1 - t_slice0).count();
     S->stats.retire_seconds += std::chrono::duration<double>(t_retire1 - t_slice1).count();
@@ -305,15 +347,33 @@ int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_para
   S->launch_bytes = sizeof(Inst<double, double>) * size_t(max_slots) + sizeof(int32_t) * (size_t(max_slots) + 8);
   if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
       cudaMalloc(&S->d_launch, S->launch_bytes) != cudaSuccess ||
-      cudaMallocHost(&S->h_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess) {
+      cudaMallocHost(&S->h_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
+      cudaMallocHost(&S->h_init, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (S->d_states) cudaFree(S->d_states);
     if (S->d_launch) cudaFree(S->d_launch);
+    if (S->h_states) cudaFreeHost(S->h_states);
+    if (S->h_init) cudaFreeHost(S->h_init);
     delete S;
     set_error("server_create: allocation failed");
     return PDHCG_E_OOM;
   }
+  {
+    // a pool of its own that keeps freed arenas for reuse (no release at syncs)
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) == cudaSuccess) {
+      uint64_t keep = uint64_t(hbm_budget_bytes);
+      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      S->pool = nullptr;  // fall back to cudaMalloc / cudaFree
+    }
+  }
   for (int i = max_slots - 1; i >= 0; --i) S->free_slots.push_back(i);
   S->worker = std::thread(worker_loop, S);
+  S->admitter = std::thread(admit_loop, S);
   *out = S;
   return PDHCG_OK;
 }
@@ -393,9 +453,17 @@ void pdhcg_server_destroy(pdhcg_server_t* S) {
     S->stop = true;
   }
   S->cv.notify_all();
+  S->cv_work.notify_all();
+  if (S->admitter.joinable()) S->admitter.join();
   if (S->worker.joinable()) S->worker.join();
   cudaSetDevice(S->device);
   for (auto& l : S->live) pdhcg_destroy(l.P);
+  for (auto& l : S->ready) pdhcg_destroy(l.P);
+  if (S->admit_stream) cudaStreamSynchronize(S->admit_stream);
+  if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
+  if (S->pinned_stage) cudaFreeHost(S->pinned_stage);
+  if (S->h_init) cudaFreeHost(S->h_init);
   if (S->d_states) cudaFree(S->d_states);
   if (S->d_launch) cudaFree(S->d_launch);
   if (S->h_states) cudaFreeHost(S->h_states);
