@@ -574,7 +574,12 @@ __device__ __forceinline__ void slice_finish(const X& x, int lane, const SlicePr
 #ifndef PDHCG_SLICE_UNROLL
 #define PDHCG_SLICE_UNROLL 4
 #endif
-constexpr int kSliceUnroll = PDHCG_SLICE_UNROLL;
+#ifndef PDHCG_GROUP_SLICE_UNROLL
+#define PDHCG_GROUP_SLICE_UNROLL PDHCG_SLICE_UNROLL
+#endif
+// multi-CTA groups (streamed matrices, global vectors) / single-CTA solves
+template <Ld LM>
+__host__ __device__ constexpr int slice_unroll() { return LM == Ld::Stream ? PDHCG_GROUP_SLICE_UNROLL : PDHCG_SLICE_UNROLL; }
 
 // Accumulate slot `lane` of slice s of source X into sums[0..NG) in column order.
 template <Ld LM, class Acc, class X>
@@ -585,7 +590,7 @@ __device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums
     const int W = int((e - b) >> 5);
     const int* cp = x.S.col + b + lane;
     const auto* vp = x.S.val + b + lane;
-#pragma unroll kSliceUnroll
+#pragma unroll slice_unroll<LM>()
     for (int j = 0; j < W; ++j) {
       const int c = ldm<LM>(cp + 32 * j);
       const auto v = ldm<LM>(vp + 32 * j);
