@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--large-iters", type=int, default=128,
+                    help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="length of the arrival trace")
     return ap.parse_args()
@@ -216,6 +218,50 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def large_bytes(qp, iterations, inner, mat_bytes=4, idx_bytes=4, vec_bytes=8, k_eval=64):
+    """Algorithmic bytes of `iterations` PDHG steps with `inner` BB/CG steps on a
+    QP with a general Q: per PDHG step A^T y, Q x and A xbar streamed once plus
+    s (10 n + 7 m) of vectors; per inner step one pass over Q plus 6 s n; per
+    check (every k_eval steps) A twice, A^T and Q once, s (8 n + 6 m)."""
+    Z, Wq, n, m = qp.A.nnz, qp.Q.nnz, qp.n, qp.m
+    v = mat_bytes + idx_bytes
+    per_it = (2 * Z + Wq) * v + 4 * (2 * n + m + 3) + vec_bytes * (10 * n + 7 * m)
+    per_inner = Wq * v + 4 * (n + 1) + 6 * vec_bytes * n
+    per_check = (3 * Z + Wq) * v + vec_bytes * (8 * n + 6 * m)
+    return iterations * per_it + inner * per_inner + (iterations // k_eval) * per_check
+
+
+def large_instance_leg(args, stream, peak_gbs):
+    """One large sparse QP (n = 2e6, m = 1e6, ~10 nnz/row in Q, ~8 in A with
+    power-law column degrees) on a multi-CTA group: device time of a fixed
+    number of PDHG steps, and the algorithmic bytes they stream."""
+    import torch
+    from paper_2602_23967_b300 import pdhcg
+    qp = W.large_sparse_qp(seed=0)
+    prm = pdhcg.default_params(precision=args.precision, eps_tol=1e-12, max_iter=args.large_iters)
+    p = pdhcg.Problem(qp, prm, stream=stream.cuda_stream)
+    try:
+        x = torch.empty(qp.n, dtype=torch.float64, device="cuda")
+        y = torch.empty(qp.m, dtype=torch.float64, device="cuda")
+        p.solve_dev(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = p.solve_dev(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        p.close()
+    mb, vb = {"fp64": (8, 8), "fp32": (4, 4)}.get(args.precision, (4, 8))
+    alg = large_bytes(qp, r["iterations"], r["inner_iterations"], mat_bytes=mb, vec_bytes=vb)
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"workload": f"large sparse QP n={qp.n}, m={qp.m}, nnz(Q)={qp.Q.nnz}, nnz(A)={qp.A.nnz}, "
+                        f"{r['iterations']} PDHG steps ({r['inner_iterations']} BB steps), one multi-CTA group",
+            "us_per_step": ms * 1e3 / r["iterations"], "algorithmic_bytes": alg,
+            "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak_gbs}
+
+
 def serving_leg(args, prm, stream):
     """Serving loop under Poisson arrivals of MPC requests: each request is
     submitted at its arrival time through pdhcg_submit and collected with
@@ -266,30 +312,49 @@ def serving_leg(args, prm, stream):
                                                              "retire": st["retire_seconds"]}}
 
 
+def _oracle_solve_one(qp):
+    """One full FP64 oracle solve (runs in a spawned worker process)."""
+    import oracle
+    _, _, r = oracle.solve(qp, oracle.default_params(eps_tol=EPS))
+    return r["status_name"]
+
+
 def run_reference(args):
+    """The FP64 C oracle on the host's cores: one solve per worker process at a
+    time over consecutive instances of the same workload; each step is a
+    bounded sample of 4 instances per core."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
     qps = instances(args.count, 0)
-    for _ in range(args.warmup):
-        cpu_oracle_sample(qps, 4, 5.0)
-    vals = []
-    t_all = 0.0
-    done = 0
-    for k in range(args.steps):
-        sps, res, dt = cpu_oracle_sample(qps[k * 8:], max(8, args.cpu_sample // 4), 12.0)
-        vals.append(sps)
-        t_all += dt
-        done += len(res)
-    value = float(np.mean(vals))
+    per_step = min(len(qps), 4 * cores)
+    vals, t_all, done, off = [], 0.0, 0, 0
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_solve_one, qps[:cores], chunksize=1)
+        for _ in range(args.steps):
+            batch = [qps[(off + i) % len(qps)] for i in range(per_step)]
+            off += per_step
+            t0 = time.perf_counter()
+            pool.map(_oracle_solve_one, batch, chunksize=1)
+            dt = time.perf_counter() - t0
+            vals.append(len(batch) / dt)
+            t_all += dt
+            done += len(batch)
+    value = done / t_all
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": config_of(args),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} instances solved to 1e-6 by the FP64 C oracle, one thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} instances ({per_step} per step) solved to 1e-6 by the FP64 C "
+                                   f"oracle, {cores} worker processes"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -391,10 +456,11 @@ def run_ours(args):
         oobj = np.array([r["primal_obj"] for r in cpu_res])
         obj_err = float(np.max(np.abs(objs - oobj) / (1 + np.abs(oobj)))) if len(cpu_res) else None
         serving = serving_leg(args, prm, stream.cuda_stream) if args.serve_seconds > 0 else None
+        large = large_instance_leg(args, stream, peaks["hbm_gbs"]) if args.large_iters > 0 else None
         if serving and serving.get("solves_per_s"):
             serving["served_vs_plain"] = serving["solves_per_s"] / plain_sps
         result = dict(plain_sps=plain_sps, e2e_sps=e2e_sps, h2d=h2d, d2h=d2h, cpu_sps=cpu_sps,
-                      cpu_n=len(cpu_res), cpu_dt=cpu_dt, obj_err=obj_err, serving=serving)
+                      cpu_n=len(cpu_res), cpu_dt=cpu_dt, obj_err=obj_err, serving=serving, large=large)
 
     if rank == 0:
         line = {
@@ -420,6 +486,7 @@ def run_ours(args):
             "e2e": {"value": result.get("e2e_sps"), "unit": UNIT, "h2d_bytes_per_step": result.get("h2d"),
                     "d2h_bytes_per_step": result.get("d2h")},
             "serving": result.get("serving"),
+            "large_instance_spmv": result.get("large"),
             "gpu_launches": args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
