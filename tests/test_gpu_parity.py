@@ -239,3 +239,10 @@ def test_warm_start_from_solution_is_immediate():
         assert r2["iterations"] <= r["iterations"]
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat"])
+def test_lasso_matches_oracle(precision):
+    # LASSO in the QP form of Sec. 6.4 (diagonal Q, free variables, one-sided rows)
+    qp = W.lasso_qp(rows=4000, cols=400, density=0.01, seed=2)
+    check_optimal_parity(qp, precision=precision, max_iter=500000)

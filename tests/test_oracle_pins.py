@@ -352,3 +352,24 @@ def test_ruiz_equilibrates():
     K = np.block([[Q, A.T], [A, np.zeros((qp.m, qp.m))]])
     cn = np.max(np.abs(K), axis=0)
     assert np.all(np.abs(cn - 1.0) <= 1e-3)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_lasso_matches_sklearn(seed):
+    # LASSO as the QP of Sec. 6.4 (y = A x - b, -t <= x <= t): the oracle's x
+    # attains scikit-learn's coordinate-descent optimum of ||Ax - b||^2 + lam ||x||_1
+    from sklearn.linear_model import Lasso
+    rows, cols = 300, 40
+    qp = W.lasso_qp(rows=rows, cols=cols, density=0.1, seed=seed)
+    lam = qp.meta["lam"]
+    x, y, r = oracle.solve(qp, oracle.default_params(eps_tol=1e-9, max_iter=2_000_000))
+    assert r["status_name"] == "OPTIMAL"
+    A = qp.A[:rows, :cols].toarray()
+    b = qp.lc[:rows]
+
+    def f(w):
+        return np.sum((A @ w - b) ** 2) + lam * np.sum(np.abs(w))
+
+    ref = Lasso(alpha=lam / (2 * rows), fit_intercept=False, tol=1e-14, max_iter=10**6).fit(A, b).coef_
+    assert f(x[:cols]) == pytest.approx(f(ref), rel=1e-8)
+    assert r["primal_obj"] == pytest.approx(f(ref), rel=1e-8)
