@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--ablation", default=None, choices=["inner-tolerance"],
+                    help="instead of the benchmark: the adaptive inner tolerance (Sec. 3.3) against fixed ones")
     ap.add_argument("--large-iters", type=int, default=128,
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
@@ -499,8 +501,37 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ablation_inner_tolerance(args):
+    """Sec. 6.3's question on this build: outer steps, inner steps and device time
+    to relative KKT 1e-6 with the adaptive inner tolerance of Sec. 3.3 against
+    fixed inner tolerances (gamma = 0: eps_k = eps_min from the second step)."""
+    import torch
+    from paper_2602_23967_b300 import pdhcg
+    torch.cuda.set_device(0)
+    cases = [(f"random_qp n=200 seed {s}", W.random_qp(seed=s)) for s in range(8)]
+    cases += [("large sparse n=2e5", W.large_sparse_qp(n=200_000, m=100_000, seed=0))]
+    rules = {"adaptive (Sec. 3.3)": {}, "fixed 1e-9": dict(gamma_inner=0.0, eps_inner_min=1e-9),
+             "fixed 1e-6": dict(gamma_inner=0.0, eps_inner_min=1e-6)}
+    rows = []
+    for name, qp in cases:
+        for rule, kw in rules.items():
+            p = pdhcg.Problem(qp, pdhcg.default_params(precision=args.precision, eps_tol=EPS,
+                                                       max_iter=200_000, time_limit_s=120.0, **kw))
+            try:
+                _, _, r = p.solve()
+            finally:
+                p.close()
+            rows.append({"instance": name, "rule": rule, "status": r["status_name"],
+                         "outer": r["iterations"], "inner": r["inner_iterations"],
+                         "seconds": r["solve_seconds"]})
+    print(json.dumps({"ablation": "inner-tolerance", "precision": args.precision, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.ablation == "inner-tolerance":
+        run_ablation_inner_tolerance(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
