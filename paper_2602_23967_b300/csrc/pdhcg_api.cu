@@ -833,7 +833,21 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
     real.base = static_cast<char*>(Pi->arena);
     carve(Pi, real, batch);
   }
-  // stage the inputs in pinned memory and copy each handle's prefix
+  // stage the inputs in pinned memory and copy each handle's prefix.  Without a
+  // caller-owned buffer, the process-wide staging buffer is reused (grown when
+  // too small; pinning hundreds of MB per call costs more than the copy).
+  static std::mutex g_stage_mu;
+  static void* g_stage = nullptr;
+  static size_t g_stage_bytes = 0;
+  std::unique_lock<std::mutex> stage_lock(g_stage_mu, std::defer_lock);
+  CreateAlloc shared_stage;
+  if (!(alloc && alloc->pinned && alloc->pinned_bytes)) {
+    stage_lock.lock();
+    shared_stage.pool = alloc ? alloc->pool : nullptr;
+    shared_stage.pinned = &g_stage;
+    shared_stage.pinned_bytes = &g_stage_bytes;
+    alloc = &shared_stage;
+  }
   void* stage = nullptr;
   const bool reuse = alloc && alloc->pinned && alloc->pinned_bytes;
   if (reuse && *alloc->pinned_bytes >= stage_total && *alloc->pinned) {
@@ -844,7 +858,8 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       *alloc->pinned = nullptr;
       *alloc->pinned_bytes = 0;
     }
-    const size_t want = reuse ? std::max<size_t>(2 * stage_total, size_t(64) << 20) : std::max<size_t>(stage_total, 1);
+    const size_t want = reuse ? std::max<size_t>(stage_total + stage_total / 4, size_t(64) << 20)
+                              : std::max<size_t>(stage_total, 1);
     e = cudaMallocHost(&stage, want);
     if (e != cudaSuccess) {
       cleanup();
@@ -855,14 +870,27 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       *alloc->pinned_bytes = want;
     }
   }
-  size_t soff = 0;
+  std::vector<size_t> soff(static_cast<size_t>(count) + 1, 0);
+  for (int i = 0; i < count; ++i) soff[size_t(i) + 1] = soff[size_t(i)] + P[size_t(i)]->input_bytes;
+  {
+    // pack in parallel (host memory bandwidth), copy in order
+    const int nth = std::max(1, std::min<int>(count / 64 + 1, int(std::thread::hardware_concurrency())));
+    std::atomic<int> nextp(0);
+    auto work = [&]() {
+      for (int i = nextp++; i < count; i = nextp++)
+        pack_inputs(P[size_t(i)], H[size_t(i)], static_cast<char*>(stage) + soff[size_t(i)]);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nth; ++t) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+  }
   std::vector<SolverState> hstates(batch ? size_t(count) : 0);
   for (int i = 0; i < count; ++i) {
     pdhcg_problem* Pi = P[size_t(i)];
-    char* dst = static_cast<char*>(stage) + soff;
-    pack_inputs(Pi, H[size_t(i)], dst);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Pi->arena, dst, Pi->input_bytes, cudaMemcpyHostToDevice, s);
-    soff += Pi->input_bytes;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Pi->arena, static_cast<char*>(stage) + soff[size_t(i)], Pi->input_bytes,
+                          cudaMemcpyHostToDevice, s);
     if (batch) {
       hstates[size_t(i)] = SolverState{};
       hstates[size_t(i)].method = Pi->method;

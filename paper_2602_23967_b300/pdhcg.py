@@ -253,10 +253,13 @@ def create_batch(qps, params: Params | None = None, stream=None):
     """Create many Problems at once (pdhcg_create_batch: shared allocation, one setup launch)."""
     params = params if params is not None else default_params()
     holds = [_qp_args(q) for q in qps]
-    data = (ProblemData * len(qps))()
-    for i, h in enumerate(holds):
-        data[i] = ProblemData(C.pointer(h["Q"].s) if "Q" in h else None, C.pointer(h["A"].s),
-                              _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]))
+    # the pdhcg_problem_data array: seven pointers per problem, filled as integers
+    addr = np.array([(C.addressof(h["Q"].s) if "Q" in h else 0, C.addressof(h["A"].s), h["c"].ctypes.data,
+                      h["lc"].ctypes.data if h["lc"].size else 0, h["uc"].ctypes.data if h["uc"].size else 0,
+                      h["lv"].ctypes.data, h["uv"].ctypes.data) for h in holds],
+                    dtype=np.uint64).reshape(len(qps), 7)
+    assert C.sizeof(ProblemData) == 7 * 8
+    data = addr.ctypes.data_as(C.POINTER(ProblemData))
     handles = (_P * len(qps))()
     check(lib().pdhcg_create_batch(len(qps), data, C.byref(params), _P(stream) if stream else None,
                                    handles), "pdhcg_create_batch")
