@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96)
-    ap.add_argument("--ablation", default=None, choices=["inner-tolerance"],
+    ap.add_argument("--ablation", default=None, choices=["inner-tolerance", "inner-solver"],
                     help="instead of the benchmark: the adaptive inner tolerance (Sec. 3.3) against fixed ones")
     ap.add_argument("--large-iters", type=int, default=128,
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
@@ -527,10 +527,37 @@ def run_ablation_inner_tolerance(args):
     print(json.dumps({"ablation": "inner-tolerance", "precision": args.precision, "rows": rows}), flush=True)
 
 
+def run_ablation_inner_solver(args):
+    """Reading D1's two inner solvers for a non-diagonal Q with finite bounds:
+    projected BB gradient (AUTO) against CG on the lifted problem (bounds as rows
+    of A), to relative KKT 1e-6."""
+    import torch
+    from paper_2602_23967_b300 import pdhcg
+    torch.cuda.set_device(0)
+    cases = [(f"random_qp n=200 seed {s}", W.random_qp(seed=s)) for s in range(8)]
+    cases += [("large sparse n=2e5", W.large_sparse_qp(n=200_000, m=100_000, seed=0))]
+    rows = []
+    for name, qp in cases:
+        for inner in ("bb", "cg_lifted"):
+            p = pdhcg.Problem(qp, pdhcg.default_params(precision=args.precision, eps_tol=EPS, inner=inner,
+                                                       max_iter=200_000, time_limit_s=120.0))
+            try:
+                _, _, r = p.solve()
+            finally:
+                p.close()
+            rows.append({"instance": name, "inner": inner, "status": r["status_name"],
+                         "outer": r["iterations"], "inner_steps": r["inner_iterations"],
+                         "seconds": r["solve_seconds"]})
+    print(json.dumps({"ablation": "inner-solver", "precision": args.precision, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.ablation == "inner-tolerance":
         run_ablation_inner_tolerance(args)
+        return
+    if args.ablation == "inner-solver":
+        run_ablation_inner_solver(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -73,6 +73,12 @@ extern "C" {
 #define PDHCG_INNER_DIAG 1  /* closed form; only valid for diagonal Q                    */
 #define PDHCG_INNER_CG 2    /* conjugate gradients; only valid when no bound is finite   */
 #define PDHCG_INNER_BB 3    /* projected gradient with Barzilai-Borwein steps            */
+#define PDHCG_INNER_CG_LIFTED 4 /* every finite variable bound becomes a row e_j^T x of A
+                                   (with that bound as its row bounds) and the variables
+                                   become free, so the subproblem is an unconstrained SPD
+                                   solve: closed form for diagonal Q, else CG.  The
+                                   solution's y holds the original rows' duals only;
+                                   residuals and iterations refer to the lifted problem */
 
 typedef struct {
   int32_t nrows, ncols;

@@ -180,7 +180,29 @@ int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const
     if (h->vtype[j] != kFree) h->any_box = true;
   }
   for (int32_t i = 0; i < m; ++i) h->ctype[i] = bound_type(lc[i], uc[i]);
+  h->m_user = m;
   return PDHCG_OK;
+}
+
+void lift_box_rows(HostQP* h) {
+  const int32_t n = h->n;
+  int32_t added = 0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (h->vtype[size_t(j)] == kFree) continue;
+    h->Ap.push_back(h->Ap.back() + 1);
+    h->Ac.push_back(j);
+    h->Av.push_back(1.0);
+    h->lc.push_back(h->lv[size_t(j)]);
+    h->uc.push_back(h->uv[size_t(j)]);
+    h->ctype.push_back(h->vtype[size_t(j)]);
+    h->lv[size_t(j)] = -INFINITY;
+    h->uv[size_t(j)] = INFINITY;
+    h->vtype[size_t(j)] = kFree;
+    ++added;
+  }
+  h->m += added;
+  h->any_box = false;
+  transpose(h->m, n, h->Ap, h->Ac, h->Av, h->ATp, h->ATc, h->ATv);
 }
 
 void build_sell(int32_t nrows, int nmat, const std::vector<int32_t>* rp[2],

@@ -18,6 +18,7 @@ void set_error(const std::string& msg);
 // method's arithmetic all runs on the device).
 struct HostQP {
   int32_t n = 0, m = 0;
+  int32_t m_user = 0;  // rows of the caller's problem (m also counts lifted bound rows)
   bool has_q = false, diag_q = true, any_box = false;
   std::vector<int32_t> Qp, Qc, Ap, Ac, ATp, ATc;
   std::vector<double> Qv, Av, ATv;
@@ -28,6 +29,9 @@ struct HostQP {
 // Validate and canonicalise; returns PDHCG_OK or PDHCG_E_INVALID (with set_error).
 int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
                   const double* uc, const double* lv, const double* uv, HostQP* out);
+// PDHCG_INNER_CG_LIFTED: append a row e_j^T for every variable with a finite
+// bound (row bounds = that variable's bounds) and make every variable free.
+void lift_box_rows(HostQP* h);
 
 // SELL-C-sigma layout of a row space with up to two matrices (integer part;
 // values are filled on the device from the scaled CSR values).
@@ -109,6 +113,7 @@ struct pdhcg_problem {
   int precision = PDHCG_FP64;
   int method = PDHCG_INNER_DIAG;
   int32_t n = 0, m = 0;
+  int32_t m_user = 0;  // rows the caller sees (m may add lifted bound rows)
   int64_t nnzQ = 0, nnzA = 0;
   bool has_q = false;
   int lanes_var = 4, lanes_con = 4;

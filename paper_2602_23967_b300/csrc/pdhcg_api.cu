@@ -675,7 +675,7 @@ static int check_params(const pdhcg_params* p) {
   }
   if (p->precision < 0 || p->precision > 3 || p->k_eval < 1 || p->max_iter < 1 ||
       !(p->eps_tol > 0) || !(p->eps_inf > 0) || p->max_inner_iter < 0 || p->ruiz_iters < 0 ||
-      p->inner < 0 || p->inner > 3 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
+      p->inner < 0 || p->inner > 4 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
       (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1))))) {
     set_error("params: value out of range");
     return PDHCG_E_INVALID;
@@ -694,6 +694,10 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
   int rc = build_host_qp(in.Q, in.A, in.c, in.lc, in.uc, in.lv, in.uv, h);
   if (rc) return rc;
   int method = prm.inner;
+  if (method == PDHCG_INNER_CG_LIFTED) {
+    lift_box_rows(h);
+    method = PDHCG_INNER_AUTO;  // no finite variable bound is left
+  }
   if (method == PDHCG_INNER_AUTO) method = h->diag_q ? PDHCG_INNER_DIAG : (h->any_box ? PDHCG_INNER_BB : PDHCG_INNER_CG);
   if (method == PDHCG_INNER_DIAG && !h->diag_q) {
     set_error("inner = DIAG needs a diagonal Q");
@@ -710,6 +714,7 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
   P->method = method;
   P->n = h->n;
   P->m = h->m;
+  P->m_user = h->m_user;
   P->nnzQ = int64_t(h->Qc.size());
   P->nnzA = int64_t(h->Ac.size());
   P->has_q = h->has_q;
@@ -1079,14 +1084,18 @@ int pdhcg_solve(pdhcg_t* P, const double* x0, const double* y0, pdhcg_result* re
     return PDHCG_E_INVALID;
   }
   CK(cudaSetDevice(P->device));
-  const size_t n = size_t(P->n), m = size_t(P->m);
+  const size_t n = size_t(P->n), m = size_t(P->m), mu = size_t(P->m_user);
   if (x0) CK(cudaMemcpyAsync(P->x_init_stage, x0, sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
-  if (y0 && m) CK(cudaMemcpyAsync(P->y_init_stage, y0, sizeof(double) * m, cudaMemcpyHostToDevice, P->stream));
+  if (y0 && m) {
+    // lifted bound rows (if any) start with a zero dual
+    if (mu < m) CK(cudaMemsetAsync(P->y_init_stage + mu, 0, sizeof(double) * (m - mu), P->stream));
+    if (mu) CK(cudaMemcpyAsync(P->y_init_stage, y0, sizeof(double) * mu, cudaMemcpyHostToDevice, P->stream));
+  }
   int rc = solve_one(P, x0 ? P->x_init_stage : nullptr, (y0 && m) ? P->y_init_stage : nullptr, res,
                      P->x_stage, P->y_stage);
   if (rc) return rc;
   if (x_out) CK(cudaMemcpyAsync(x_out, P->x_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream));
-  if (y_out && m) CK(cudaMemcpyAsync(y_out, P->y_stage, sizeof(double) * m, cudaMemcpyDeviceToHost, P->stream));
+  if (y_out && mu) CK(cudaMemcpyAsync(y_out, P->y_stage, sizeof(double) * mu, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
   return PDHCG_OK;
 }
@@ -1097,7 +1106,21 @@ int pdhcg_solve_dev(pdhcg_t* P, const double* x0_dev, const double* y0_dev, pdhc
     set_error("NULL handle");
     return PDHCG_E_INVALID;
   }
-  return solve_one(P, x0_dev, y0_dev, res, x_out_dev, y_out_dev);
+  if (P->m_user == P->m) return solve_one(P, x0_dev, y0_dev, res, x_out_dev, y_out_dev);
+  // lifted bound rows: the caller's y buffers hold only the original rows
+  CK(cudaSetDevice(P->device));
+  const size_t m = size_t(P->m), mu = size_t(P->m_user);
+  if (y0_dev) {
+    CK(cudaMemsetAsync(P->y_init_stage + mu, 0, sizeof(double) * (m - mu), P->stream));
+    if (mu) CK(cudaMemcpyAsync(P->y_init_stage, y0_dev, sizeof(double) * mu, cudaMemcpyDeviceToDevice, P->stream));
+  }
+  int rc = solve_one(P, x0_dev, y0_dev ? P->y_init_stage : nullptr, res, x_out_dev, P->y_stage);
+  if (rc) return rc;
+  if (y_out_dev && mu) {
+    CK(cudaMemcpyAsync(y_out_dev, P->y_stage, sizeof(double) * mu, cudaMemcpyDeviceToDevice, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+  }
+  return PDHCG_OK;
 }
 
 int pdhcg_get_eta(const pdhcg_t* P, double* eta, double* norm_A) {
@@ -1111,7 +1134,7 @@ int pdhcg_get_scaling(const pdhcg_t* P, double* D, double* E) {
   if (!P) return PDHCG_E_INVALID;
   CK(cudaSetDevice(P->device));
   if (D) CK(cudaMemcpy(D, P->D, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost));
-  if (E && P->m) CK(cudaMemcpy(E, P->E, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToHost));
+  if (E && P->m_user) CK(cudaMemcpy(E, P->E, sizeof(double) * size_t(P->m_user), cudaMemcpyDeviceToHost));
   return PDHCG_OK;
 }
 
@@ -1124,7 +1147,7 @@ int pdhcg_get_phase_times(const pdhcg_t* P, double* seconds8) {
 int pdhcg_get_info(const pdhcg_t* P, int32_t* n, int32_t* m, size_t* bytes) {
   if (!P) return PDHCG_E_INVALID;
   if (n) *n = P->n;
-  if (m) *m = P->m;
+  if (m) *m = P->m_user;
   if (bytes) *bytes = P->arena_bytes;
   return PDHCG_OK;
 }
@@ -1304,8 +1327,8 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
     if (hs[i].device_error) dev_err = true;
     if (res) fill_result(probs[i], hs[i], res + i);
     if (want_x && x_out[i]) std::memcpy(x_out[i], hx.data() + xoff[i], sizeof(double) * size_t(probs[i]->n));
-    if (want_y && y_out[i] && probs[i]->m)
-      std::memcpy(y_out[i], hy.data() + yoff[i], sizeof(double) * size_t(probs[i]->m));
+    if (want_y && y_out[i] && probs[i]->m_user)
+      std::memcpy(y_out[i], hy.data() + yoff[i], sizeof(double) * size_t(probs[i]->m_user));
   }
   if (dev_err) {
     set_error("solve_batch: a bounded device wait gave up");
@@ -1431,7 +1454,11 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
       new (&hi[i]) Inst<M, V>(make_inst<M, V>(probs[i]));  // placement into the static staging
       hi[i].st = d_st + i;
       hi[i].x_out = x_out_dev ? x_out_dev[i] : nullptr;
-      hi[i].y_out = (y_out_dev && probs[i]->m) ? y_out_dev[i] : nullptr;
+      // lifted bound rows: the kernel writes the handle's own y staging, and
+      // the original rows' duals are copied out after the launch
+      hi[i].y_out = (y_out_dev && probs[i]->m) ? (probs[i]->m_user == probs[i]->m ? y_out_dev[i]
+                                                                                  : probs[i]->y_stage)
+                                               : nullptr;
       const size_t b = smem_need(probs[i]);
       if (b <= kSmemVecBudget) need = std::max(need, b);
     }
@@ -1457,6 +1484,10 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
     return PDHCG_OK;
   });
   if (rc) return rc;
+  for (int i = 0; i < count; ++i)
+    if (y_out_dev && y_out_dev[i] && probs[i]->m_user && probs[i]->m_user != probs[i]->m)
+      CK(cudaMemcpyAsync(y_out_dev[i], probs[i]->y_stage, sizeof(double) * size_t(probs[i]->m_user),
+                         cudaMemcpyDeviceToDevice, s));
   // Returns only after the launch and the state read-back finished, so the next
   // call (which holds the same lock) never overwrites scratch in use.
   CK(cudaStreamSynchronize(s));

@@ -245,7 +245,7 @@ static void worker_loop(pdhcg_server* S) {
       const SolverState& st = S->h_states[S->live[size_t(i)].slot];
       if (st.status != 0 || st.device_error || rc != PDHCG_OK) {
         fin.push_back(i);
-        need += size_t(S->live[size_t(i)].P->n) + size_t(S->live[size_t(i)].P->m);
+        need += size_t(S->live[size_t(i)].P->n) + size_t(S->live[size_t(i)].P->m_user);
       }
     }
     if (need > S->h_sol_len) {
@@ -261,10 +261,10 @@ static void worker_loop(pdhcg_server* S) {
         cudaMemcpyAsync(S->h_sol + off, P->x_stage, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost,
                         S->stream);
         off += size_t(P->n);
-        if (P->m)
-          cudaMemcpyAsync(S->h_sol + off, P->y_stage, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToHost,
+        if (P->m_user)
+          cudaMemcpyAsync(S->h_sol + off, P->y_stage, sizeof(double) * size_t(P->m_user), cudaMemcpyDeviceToHost,
                           S->stream);
-        off += size_t(P->m);
+        off += size_t(P->m_user);
       }
       cudaStreamSynchronize(S->stream);
     }
@@ -285,7 +285,7 @@ static void worker_loop(pdhcg_server* S) {
       Done d;
       fill_result(l.P, st, &d.res);
       if (st.device_error || rc != PDHCG_OK || !S->h_sol) d.res.status = PDHCG_NUMERICAL_ERROR;
-      const size_t n = size_t(l.P->n), m = size_t(l.P->m);
+      const size_t n = size_t(l.P->n), m = size_t(l.P->m_user);
       if (S->h_sol) {
         d.x.assign(S->h_sol + off, S->h_sol + off + n);
         d.y.assign(S->h_sol + off + n, S->h_sol + off + n + m);

@@ -19,7 +19,7 @@ E_INVALID, E_OOM, E_CUDA, E_BUSY, E_NOT_FOUND, E_DEVICE_TIMEOUT = -1, -2, -3, -4
 STATUS_NAMES = {0: "UNSOLVED", 1: "OPTIMAL", 2: "PRIMAL_INFEASIBLE", 3: "DUAL_INFEASIBLE",
                 4: "ITERATION_LIMIT", 5: "TIME_LIMIT", 6: "NUMERICAL_ERROR"}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "dfloat": 3}
-INNER = {"auto": 0, "diag": 1, "cg": 2, "bb": 3}
+INNER = {"auto": 0, "diag": 1, "cg": 2, "bb": 3, "cg_lifted": 4}
 
 
 class PdhcgError(RuntimeError):

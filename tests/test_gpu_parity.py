@@ -246,3 +246,46 @@ def test_lasso_matches_oracle(precision):
     # LASSO in the QP form of Sec. 6.4 (diagonal Q, free variables, one-sided rows)
     qp = W.lasso_qp(rows=4000, cols=400, density=0.01, seed=2)
     check_optimal_parity(qp, precision=precision, max_iter=500000)
+
+
+def lifted(qp):
+    """The same QP with every finite variable bound as a row e_j^T x of A (reading
+    D1's CG_LIFTED variant), built here independently of the library."""
+    import scipy.sparse as sp
+    B = [j for j in range(qp.n) if np.isfinite(qp.lv[j]) or np.isfinite(qp.uv[j])]
+    E = sp.csr_matrix((np.ones(len(B)), (np.arange(len(B)), B)), shape=(len(B), qp.n))
+    A = W._csr(sp.vstack([qp.A, E]))
+    lc = np.concatenate([qp.lc, qp.lv[B]])
+    uc = np.concatenate([qp.uc, qp.uv[B]])
+    free = np.full(qp.n, np.inf)
+    return W.QP(qp.n, qp.m + len(B), qp.Q, A, qp.c, lc, uc, -free, free, name=qp.name + "_lifted")
+
+
+@pytest.mark.parametrize("N", [1, 17, 100])
+def test_cg_lifted_iterates_match_oracle_on_lifted_qp(N):
+    qp = W.random_qp(seed=4)
+    x, y, r, eta = gpu_solve(qp, max_iter=N, inner="cg_lifted")
+    assert r["inner_method"] == 2 and len(y) == qp.m          # CG; only the original rows' duals
+    lq = lifted(qp)
+    xo, yo, ro = oracle.solve(lq, oracle.default_params(max_iter=N, eta_override=eta, inner="cg"))
+    assert r["inner_iterations"] == ro["inner_iterations"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo[: qp.m])) <= 1e-10 * (1 + np.max(np.abs(yo)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cg_lifted_solves_the_original_qp(precision, seed):
+    qp = W.random_qp(seed=seed)
+    x, y, r, _ = gpu_solve(qp, eps_tol=1e-6, precision=precision, inner="cg_lifted", max_iter=500000)
+    assert r["status_name"] == "OPTIMAL", r
+    # the bounds are rows now: satisfied to the relative primal tolerance of Sec. 4.2
+    lq = lifted(qp)
+    scale = 1 + max(np.max(np.abs(lq.lc[np.isfinite(lq.lc)])), np.max(np.abs(lq.uc[np.isfinite(lq.uc)])))
+    assert np.max(np.maximum(qp.lv - x, x - qp.uv)) <= 1e-6 * scale
+    # the original rows' duals plus the implicit bound multipliers satisfy the
+    # original KKT conditions (the bound multipliers are the reduced costs)
+    rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
+    assert max(rp, rd, rg) <= 1e-5, (rp, rd, rg)
+    _, _, ro = oracle.solve(qp, oracle.default_params(eps_tol=1e-6))
+    assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
