@@ -53,6 +53,7 @@ def parse():
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="length of the arrival trace")
+    ap.add_argument("--serve-slots", type=int, default=2 * 148, help="concurrent solves of the serving loop")
     return ap.parse_args()
 
 
@@ -272,7 +273,7 @@ def serving_leg(args, prm, stream):
     trace = W.serving_trace(rate_per_s=args.serve_rate, duration_s=args.serve_seconds, seed=7,
                             mix=(1.0, 0.0, 0.0))
     qps = [W.build_request(k, s, n) for _, k, s, n in trace]
-    srv = pdhcg.Server(hbm_budget_bytes=100 << 30, max_slots=2 * 148, params=prm, stream=stream)
+    srv = pdhcg.Server(hbm_budget_bytes=100 << 30, max_slots=args.serve_slots, params=prm, stream=stream)
     t_sub, out, pending = {}, {}, []
     try:
         t0 = time.perf_counter()
@@ -308,7 +309,7 @@ def serving_leg(args, prm, stream):
             "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if len(out) else None,
             "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if len(out) else None,
             "latency_max_ms": float(lat.max() * 1e3) if len(out) else None,
-            "hbm_budget_gb": 100, "max_slots": 2 * 148, "slice_iterations": 256,
+            "hbm_budget_gb": 100, "max_slots": args.serve_slots, "slice_iterations": 256,
             "launches": st["launches"], "scheduler_seconds": {"admit": st["admit_seconds"],
                                                              "slices": st["slice_seconds"],
                                                              "retire": st["retire_seconds"]}}

@@ -79,7 +79,10 @@ struct pdhcg_server {
   size_t budget = 0;
   int max_slots = 0;
   size_t max_queue = 0;
-  int64_t slice_iters = 256;
+#ifndef PDHCG_SLICE_ITERS
+#define PDHCG_SLICE_ITERS 256
+#endif
+  int64_t slice_iters = PDHCG_SLICE_ITERS;
   pdhcg_params prm{};
   cudaStream_t stream = nullptr;
   int device = 0;
