@@ -156,6 +156,7 @@ struct Group {
   uint64_t timeout_ns;
   bool failed;
   double* lz = nullptr;         // shared Lanczos coefficients (setup kernels only)
+  double* red = nullptr;        // shared BS/32 * 4 doubles for the row engine (setup kernels only)
   double* lz_out = nullptr;     // shared: the warp-computed eigenvalue
 
   // Row range of this CTA in a space whose partition table is `part`

@@ -3,7 +3,4 @@
 
 namespace pdhcg {
 PDHCG_INSTANTIATE(double, double)
-template cudaError_t launch_sell_fill<double>(int, const int32_t*, const int64_t*, const int32_t*,
-                                               const double*, double*, cudaStream_t);
-template cudaError_t launch_sell_fill_batch<double>(const FillDesc*, int, cudaStream_t);
 }  // namespace pdhcg

@@ -100,23 +100,6 @@ cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, in
   return cudaGetLastError();
 }
 
-template <class MatT>
-cudaError_t launch_sell_fill_batch(const FillDesc* d, int count, cudaStream_t s) {
-  if (count <= 0) return cudaSuccess;
-  sell_fill_batch_kernel<MatT><<<std::min(count, 4096), 256, 0, s>>>(d, count);
-  return cudaGetLastError();
-}
-
-template <class MatT>
-cudaError_t launch_sell_fill(int nslices, const int32_t* perm, const int64_t* sptr,
-                             const int32_t* rowptr, const MatT* csr_val, MatT* sell_val, cudaStream_t s) {
-  if (nslices <= 0) return cudaSuccess;
-  const int wpb = 8;
-  const int grid = std::min((nslices + wpb - 1) / wpb, 4096);
-  sell_fill_kernel<MatT><<<grid, wpb * 32, 0, s>>>(nslices, perm, sptr, rowptr, csr_val, sell_val);
-  return cudaGetLastError();
-}
-
 #define PDHCG_INSTANTIATE(MatT, VecT)                                                          \
   template cudaError_t kernel_limits<MatT, VecT>(KernelLimits*);                               \
   template cudaError_t launch_setup<MatT, VecT>(const SetupArgs<MatT, VecT>&, int,             \

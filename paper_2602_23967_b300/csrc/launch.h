@@ -50,13 +50,4 @@ template <class MatT, class VecT>
 cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, int* next, int32_t* err,
                               uint64_t timeout_ns, cudaStream_t s);
 
-struct FillDesc;
-template <class MatT>
-cudaError_t launch_sell_fill_batch(const FillDesc* d, int count, cudaStream_t s);
-
-// Copy scaled CSR values into SELL slice order (one instantiation per value type).
-template <class MatT>
-cudaError_t launch_sell_fill(int nslices, const int32_t* perm, const int64_t* sptr,
-                             const int32_t* rowptr, const MatT* csr_val, MatT* sell_val, cudaStream_t s);
-
 }  // namespace pdhcg

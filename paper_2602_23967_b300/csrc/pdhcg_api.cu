@@ -514,6 +514,35 @@ SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) 
   a.uc = static_cast<V*>(P->uc);
   a.qdiag = static_cast<V*>(P->qdiag);
   a.st = P->st;
+  a.vsp.nslices = P->vsell.nslices;
+  a.vsp.nlong = int32_t(P->vsell.longs.size());
+  a.vsp.nhuge = int32_t(P->vsell.huges.size());
+  a.vsp.perm = P->v_perm;
+  a.vsp.longs = P->v_longs;
+  a.vsp.huges = P->v_huges;
+  a.csp.nslices = P->csell.nslices;
+  a.csp.nlong = int32_t(P->csell.longs.size());
+  a.csp.nhuge = int32_t(P->csell.huges.size());
+  a.csp.perm = P->c_perm;
+  a.csp.longs = P->c_longs;
+  a.csp.huges = P->c_huges;
+  if (ps) {
+    a.vsp.slice_part = ps->v_slice;
+    a.vsp.long_part = ps->v_long;
+    a.vsp.huge_part = ps->v_huge;
+    a.csp.slice_part = ps->c_slice;
+    a.csp.long_part = ps->c_long;
+    a.csp.huge_part = ps->c_huge;
+  }
+  a.sATp = P->sATp;
+  a.sQp = P->sQp;
+  a.sAp = P->sAp;
+  a.sATc = P->sATc;
+  a.sQc = P->sQc;
+  a.sAc = P->sAc;
+  a.sATv = static_cast<M*>(P->sATv);
+  a.sQv = static_cast<M*>(P->sQv);
+  a.sAv = static_cast<M*>(P->sAv);
   return a;
 }
 
@@ -545,23 +574,6 @@ int run_setup(pdhcg_problem* P) {
   });
 }
 
-int fill_sell(pdhcg_problem* P) {
-  auto go = [&](auto* tag) -> int {
-    using M = std::remove_pointer_t<decltype(tag)>;
-    cudaError_t e = launch_sell_fill<M>(P->vsell.nslices, P->v_perm, P->sATp, P->ATp_d,
-                                        static_cast<const M*>(P->ATs), static_cast<M*>(P->sATv), P->stream);
-    if (e == cudaSuccess && P->has_q)
-      e = launch_sell_fill<M>(P->vsell.nslices, P->v_perm, P->sQp, P->Qp_d, static_cast<const M*>(P->Qs),
-                              static_cast<M*>(P->sQv), P->stream);
-    if (e == cudaSuccess)
-      e = launch_sell_fill<M>(P->csell.nslices, P->c_perm, P->sAp, P->Ap_d, static_cast<const M*>(P->As),
-                              static_cast<M*>(P->sAv), P->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
-    return e == cudaSuccess ? PDHCG_OK : cuda_fail(e, "sell fill");
-  };
-  if (P->precision == PDHCG_FP64) return go(static_cast<double*>(nullptr));
-  return go(static_cast<float*>(nullptr));
-}
 
 // One solve of one handle (device pointers for warm start / outputs).
 int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_result* res,
@@ -912,22 +924,13 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
   int rc = PDHCG_OK;
   if (!batch) {
     rc = run_setup(P[0]);
-    if (rc == PDHCG_OK) rc = fill_sell(P[0]);
   } else {
     rc = dispatch_precision(prm.precision, [&](auto tag) -> int {
       using M = typename decltype(tag)::Mat;
       using V = typename decltype(tag)::Vec;
       std::vector<SetupArgs<M, V>> args(static_cast<size_t>(count));
-      std::vector<FillDesc> fills;
-      fills.reserve(size_t(count) * 3);
-      for (int i = 0; i < count; ++i) {
-        const pdhcg_problem* Pi = P[size_t(i)];
-        args[size_t(i)] = make_setup_args<M, V>(Pi, nullptr);
-        fills.push_back(FillDesc{Pi->vsell.nslices, Pi->v_perm, Pi->sATp, Pi->ATp_d, Pi->ATs, Pi->sATv});
-        if (Pi->has_q) fills.push_back(FillDesc{Pi->vsell.nslices, Pi->v_perm, Pi->sQp, Pi->Qp_d, Pi->Qs, Pi->sQv});
-        fills.push_back(FillDesc{Pi->csell.nslices, Pi->c_perm, Pi->sAp, Pi->Ap_d, Pi->As, Pi->sAv});
-      }
-      const size_t abytes = sizeof(SetupArgs<M, V>) * args.size(), fbytes = sizeof(FillDesc) * fills.size();
+      for (int i = 0; i < count; ++i) args[size_t(i)] = make_setup_args<M, V>(P[size_t(i)], nullptr);
+      const size_t abytes = sizeof(SetupArgs<M, V>) * args.size(), fbytes = 0;
       char* dscratch = nullptr;
       struct ScratchGuard {
         char* p;
@@ -943,13 +946,10 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       ScratchGuard guard{dscratch, s, from_pool};
       int32_t* ctl = reinterpret_cast<int32_t*>(dscratch + abytes + fbytes);
       CK(cudaMemcpyAsync(dscratch, args.data(), abytes, cudaMemcpyHostToDevice, s));
-      CK(cudaMemcpyAsync(dscratch + abytes, fills.data(), fbytes, cudaMemcpyHostToDevice, s));
       CK(cudaMemsetAsync(ctl, 0, 2 * sizeof(int32_t), s));
       const uint64_t tmo = uint64_t(std::max(prm.device_timeout_ms, 1)) * 1000000ull;
       cudaError_t e2 = launch_setup_pool<M, V>(reinterpret_cast<SetupArgs<M, V>*>(dscratch), count, ctl,
                                                ctl + 1, tmo, s);
-      if (e2 == cudaSuccess)
-        e2 = launch_sell_fill_batch<M>(reinterpret_cast<FillDesc*>(dscratch + abytes), int(fills.size()), s);
       if (e2 != cudaSuccess) return cuda_fail(e2, "batched setup");
       CK(cudaMemcpyAsync(hstates.data(), states, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
       int32_t err = 0;

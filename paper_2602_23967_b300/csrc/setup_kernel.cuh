@@ -7,6 +7,7 @@
 //  2. Scaled data in the iteration's types: Q, A, A^T values, c = D c,
 //     lv = lv / D, uv = uv / D, lc = E lc, uc = E uc, diag(Q), the Gershgorin
 //     bound of Q (BB step range), ||c||, ||finite(lc, uc)|| (initial primal weight).
+//  2b. The scaled values in SELL slice order (the solve kernel's layout).
 //  3. ||A||_2 of the scaled A (the values the iteration uses) by Lanczos on
 //     A^T A in FP64 (Sec. 3.2 fixes eta = 0.998/||A|| but not how ||A|| is
 //     obtained): t = A v_k, w = A^T t, alpha_k = ||t||^2,
@@ -32,6 +33,12 @@ struct SetupArgs {
   double *D, *E, *Dn, *En;            // scaling work (D, E hold the result)
   double *pv, *pu, *pw, *pt;          // Lanczos work: v_k, v_{k-1}, w (n each), t (m)
   MatT *Qs, *As, *ATs;                // scaled values (outputs)
+  // SELL form of A^T, Q and A (row spaces, slice pointers, columns) and the
+  // scaled values in slice order (outputs, filled from Qs / As / ATs)
+  SpaceLayout vsp, csp;
+  const int64_t *sATp, *sQp, *sAp;
+  const int32_t *sATc, *sQc, *sAc;
+  MatT *sATv, *sQv, *sAv;
   VecT *c, *lv, *uv, *lc, *uc, *qdiag;
   SolverState* st;
 };
@@ -117,6 +124,24 @@ __device__ __forceinline__ double tridiag_max_eig_warp(const double* a, const do
     if (done) break;
   }
   return hi;
+}
+
+// Scaled CSR values into SELL slice order: warp w of CTA r takes slices
+// r * NW + w, stepping over the whole group; padding slots get 0.
+template <int BS, class MatT>
+__device__ __forceinline__ void fill_sell_space(const Group<BS>& g, int nslices, const int32_t* perm,
+                                                const int64_t* sptr, const int32_t* rowptr, const MatT* csr,
+                                                MatT* sell) {
+  constexpr int NW = BS / 32;
+  const int lane = threadIdx.x & 31;
+  for (int s = g.rank * NW + int(threadIdx.x >> 5); s < nslices; s += g.nblk * NW) {
+    const int row = perm[s * 32 + lane];
+    const int64_t b = sptr[s];
+    const int W = int((sptr[s + 1] - b) >> 5);
+    const int rb = row >= 0 ? rowptr[row] : 0;
+    const int len = row >= 0 ? rowptr[row + 1] - rb : 0;
+    for (int j = 0; j < W; ++j) sell[b + 32 * j + lane] = j < len ? csr[rb + j] : MatT(0);
+  }
 }
 
 template <int BS, class MatT, class VecT>
@@ -221,9 +246,19 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
     if (!group_reduce<BS, 5>(g, red, (1u << 2) | (1u << 3) | (1u << 4))) return;
   }
 
+  // ---- SELL values of the scaled matrices (the solve kernel's layout) ----
+  fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sATp, a.ATp, a.ATs, a.sATv);
+  if (a.has_q) fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sQp, a.Qp, a.Qs, a.sQv);
+  fill_sell_space(g, a.csp.nslices, a.csp.perm, a.sAp, a.Ap, a.As, a.sAv);
+  if (!group_sync<BS>(g)) return;
+
   // ---- 3. ||A||_2 by Lanczos on A^T A (FP64 vectors, the scaled values) ----
   double lam = 0.0, lam_prev = -1.0, bprev = 0.0;
   int it = 0;
+  const int prank = g.nblk > 1 ? g.rank : -1;
+  const Csr<MatT> Acsr{a.m, a.Ap[a.m], a.Ap, a.Ac, a.As};
+  const Csr<MatT> ATcsr{a.n, a.ATp[a.n], a.ATp, a.ATc, a.ATs};
+  RowCtx rc{nullptr, g.red, g.err, g.sm_flag, g.timeout_ns};
   if (a.m > 0) {
     const int kmax = a.power_max_iter < kLanczosCap ? a.power_max_iter : kLanczosCap;
     const double v0 = 1.0 / sqrt(double(a.n));
@@ -234,27 +269,26 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
     if (!group_sync<BS>(g)) return;
     int next_check = 8;
     for (it = 1; it <= kmax; ++it) {
+      // t = A v and w = A^T t with the solver's SELL row engine (plain loads:
+      // the SELL values were written by this launch, which rules out the
+      // read-only cache path)
       double tt[1] = {0.0};
-      rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
-        const double t = sub_row_sum(a.Ap, i, valid, sl, Lc,
-                                     [&](int k) { return double(a.As[k]) * a.pv[a.Ac[k]]; });
-        if (valid && sl == 0) {
-          a.pt[i] = t;
-          tt[0] += t * t;
-        }
-      });
+      space_rows<BS, Ld::Generic, double>(
+          a.csp, prank, src(Sell<MatT>{a.sAp, a.sAc, a.sAv}, Acsr, [&](int j) { return a.pv[j]; }),
+          nosrc<MatT>(), rc, [&](int i, const double* sums) {
+            a.pt[i] = sums[0];
+            tt[0] += sums[0] * sums[0];
+          });
       if (!group_reduce<BS, 1>(g, tt, 0u)) return;
       const double alpha = tt[0];
       double ww[1] = {0.0};
-      rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
-        const double w = sub_row_sum(a.ATp, j, valid, sl, Lv,
-                                     [&](int k) { return double(a.ATs[k]) * a.pt[a.ATc[k]]; });
-        if (valid && sl == 0) {
-          const double wj = w - alpha * a.pv[j] - bprev * a.pu[j];
-          a.pw[j] = wj;
-          ww[0] += wj * wj;
-        }
-      });
+      space_rows<BS, Ld::Generic, double>(
+          a.vsp, prank, src(Sell<MatT>{a.sATp, a.sATc, a.sATv}, ATcsr, [&](int i) { return a.pt[i]; }),
+          nosrc<MatT>(), rc, [&](int j, const double* sums) {
+            const double wj = sums[0] - alpha * a.pv[j] - bprev * a.pu[j];
+            a.pw[j] = wj;
+            ww[0] += wj * wj;
+          });
       if (!group_reduce<BS, 1>(g, ww, 0u)) return;
       const double beta = sqrt(ww[0]);
       if (threadIdx.x == 0) {
@@ -306,10 +340,12 @@ __global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsi
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
   __shared__ double sm_lz[2 * kLanczosCap + 1];
+  __shared__ double sm_red[(BS / 32) * 4];
   __shared__ int sm_flag;
   Group<BS> g;
   g.lz = sm_lz;
   g.lz_out = sm_lz + 2 * kLanczosCap;
+  g.red = sm_red;
   g.nblk = gridDim.x;
   g.rank = blockIdx.x;
   g.bar32 = reinterpret_cast<unsigned*>(bar);
@@ -334,11 +370,13 @@ __global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, Ve
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
   __shared__ double sm_lz[2 * kLanczosCap + 1];
+  __shared__ double sm_red[(BS / 32) * 4];
   __shared__ int sm_flag;
   __shared__ int sm_idx;
   Group<BS> g;
   g.lz = sm_lz;
   g.lz_out = sm_lz + 2 * kLanczosCap;
+  g.red = sm_red;
   g.nblk = 1;
   g.rank = 0;
   g.bar32 = nullptr;
@@ -360,33 +398,6 @@ __global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, Ve
     g.epoch = 0;
     setup_instance<BS>(g, args[idx]);
     __syncthreads();
-  }
-}
-
-// SELL values of many matrices: one CTA per descriptor, one warp per slice.
-struct FillDesc {
-  int nslices;
-  const int32_t* perm;
-  const int64_t* sptr;
-  const int32_t* rowptr;
-  const void* csr_val;
-  void* sell_val;
-};
-template <class MatT>
-__global__ void sell_fill_batch_kernel(const FillDesc* d, int count) {
-  const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
-  for (int i = blockIdx.x; i < count; i += gridDim.x) {
-    const FillDesc f = d[i];
-    const MatT* csr = static_cast<const MatT*>(f.csr_val);
-    MatT* out = static_cast<MatT*>(f.sell_val);
-    for (int s = threadIdx.x >> 5; s < f.nslices; s += wpb) {
-      const int row = f.perm[s * 32 + lane];
-      const int64_t b = f.sptr[s];
-      const int W = int((f.sptr[s + 1] - b) >> 5);
-      const int rb = row >= 0 ? f.rowptr[row] : 0;
-      const int len = row >= 0 ? f.rowptr[row + 1] - rb : 0;
-      for (int j = 0; j < W; ++j) out[b + 32 * j + lane] = j < len ? csr[rb + j] : MatT(0);
-    }
   }
 }
 

@@ -962,20 +962,4 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
   }
 }
 
-// SELL values from the scaled CSR values: one warp per slice.
-template <class MatT>
-__global__ void sell_fill_kernel(int nslices, const int32_t* perm, const int64_t* sptr,
-                                 const int32_t* rowptr, const MatT* csr_val, MatT* sell_val) {
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x / 32;
-  for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < nslices; s += gridDim.x * wpb) {
-    const int row = perm[s * 32 + lane];
-    const int64_t b = sptr[s];
-    const int W = int((sptr[s + 1] - b) >> 5);
-    const int rb = row >= 0 ? rowptr[row] : 0;
-    const int len = row >= 0 ? rowptr[row + 1] - rb : 0;
-    for (int j = 0; j < W; ++j) sell_val[b + 32 * j + lane] = j < len ? csr_val[rb + j] : MatT(0);
-  }
-}
-
 }  // namespace pdhcg
