@@ -438,7 +438,9 @@ void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res
   res->precision = P->precision;
 }
 
-int max_group_blocks(int precision) {
+// CTAs of one cooperative group: the solve kernel's co-residency, or (setup)
+// the setup kernel's, which may be lower.
+int max_group_blocks(int precision, bool setup) {
   KernelLimits kl{};
   int rc = dispatch_precision(precision, [&](auto tag) {
     using M = typename decltype(tag)::Mat;
@@ -447,7 +449,20 @@ int max_group_blocks(int precision) {
     return e == cudaSuccess ? PDHCG_OK : cuda_fail(e, "kernel_limits");
   });
   if (rc) return rc;
-  return std::min(kl.max_coresident_group, kl.max_coresident_setup);
+  return setup ? std::min(kl.max_coresident_group, kl.max_coresident_setup) : kl.max_coresident_group;
+}
+
+int cached_max_group_blocks(int precision, bool setup = false) {
+  static std::mutex mu;
+  static int cache[2][4][64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  int* slot = (dev >= 0 && dev < 64) ? &cache[setup ? 1 : 0][precision][dev] : nullptr;
+  if (slot && *slot > 0) return *slot;
+  const int mb = max_group_blocks(precision, setup);
+  if (mb > 0 && slot) *slot = mb;
+  return mb;
 }
 
 // Largest per-instance vector footprint a pool CTA keeps in shared memory.
@@ -547,7 +562,9 @@ SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) 
 }
 
 int run_setup(pdhcg_problem* P) {
-  const int nblk = choose_group_blocks(P, P->max_blk);
+  const int lim = cached_max_group_blocks(P->precision, true);
+  if (lim < 0) return lim;
+  const int nblk = choose_group_blocks(P, std::max(1, std::min(P->max_blk, lim)));
   PartitionSet* ps = nullptr;
   if (nblk > 1) {
     int rc = get_partition(P, nblk, &ps);
@@ -755,17 +772,6 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
   return PDHCG_OK;
 }
 
-int cached_max_group_blocks(int precision) {
-  static std::mutex mu;
-  static int cache[4][64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(mu);
-  if (dev >= 0 && dev < 64 && cache[precision][dev] > 0) return cache[precision][dev];
-  const int mb = max_group_blocks(precision);
-  if (mb > 0 && dev >= 0 && dev < 64) cache[precision][dev] = mb;
-  return mb;
-}
 
 // Create count handles: one device allocation, one staging transfer per handle,
 // and (count > 1) one pooled setup launch.
