@@ -189,8 +189,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 240_771_328, "instances": 512,
-                   "sources_sha256": "2bfd366f55874626e0b9ec3d06d235b09c86f7e5771a8c5bc6780e485d30ac8c",
+TRAFFIC_CAPTURE = {"bytes": 396_636_928, "instances": 512,
+                   "sources_sha256": "0df8c600f3a188f74890a75882700e44f428fae3a49518fc6e608757935dbe9b",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
