@@ -176,6 +176,16 @@ def solve(qp, params: OracleParams | None = None, x0=None, y0=None, eps_trace_le
     x0a = _f64(x0) if x0 is not None else None
     y0a = _f64(y0) if y0 is not None else None
     tr = np.zeros(max(eps_trace_len, 1))
+    R = getattr(qp, "R", None)
+    if R is not None:
+        # structured Q = P + R^T R (qp.Q holds P)
+        Rh = _CsrHold(R, R.shape[0], n)
+        lib.oracle_solve_qr(
+            C.c_int32(n), C.c_int32(m), C.byref(Qh.s) if Qh else None, C.byref(Rh.s), C.byref(Ah.s),
+            _ptr(c), _ptr(lc), _ptr(uc), _ptr(lv), _ptr(uv), C.byref(params),
+            _ptr(x0a) if x0a is not None else None, _ptr(y0a) if y0a is not None else None,
+            _ptr(x), _ptr(y), C.byref(res))
+        return (x, y[:m], res.as_dict())
     lib.oracle_solve(
         C.c_int32(n), C.c_int32(m),
         C.byref(Qh.s) if Qh else None, C.byref(Ah.s),

@@ -11,6 +11,7 @@
  *   support function p(z; l, u), sign cones Y and R .... Sec. 2 (definitions after Eq. dualQP)
  *   PDHG step (primal prox solve, extrapolation, dual) .. Sec. 2.1, Eq. (pdhcg_update)
  *   primal subproblem: diagonal closed form, CG, BB-PG . Sec. 2.2 and Sec. 3.3
+ *   structured Q = P + R^T R, applied matrix-free ...... Sec. 2.2 (oracle_solve_qr)
  *   reflected Halpern scheme ............................ Sec. 3.1
  *   tau = eta/omega, sigma = eta*omega, eta = 0.998/||A|| Sec. 3.2 (||A|| by Lanczos: reading)
  *   PID primal-weight update ............................ Sec. 3.2, Eq. (pid)
@@ -284,15 +285,30 @@ double oracle_norm_estimate(const oracle_csr* A, const double* val, int32_t max_
 typedef struct {
   const oracle_csr* Q;   /* may be NULL (Q = 0) */
   const double* qval;    /* scaled values of Q  */
+  const oracle_csr* R;   /* structured part Q = P + R^T R (Sec. 2.2): may be NULL */
+  const double* rval;    /* scaled values of R  */
   double inv_tau;
   int32_t n;
-  double* tmp;           /* length n */
+  double* tmp;           /* length n (with R) */
+  double* tk;            /* length k (with R) */
 } hop_t;
+
+/* out = Q v with Q = P + R^T R applied as P v + R^T (R v), never forming R^T R
+ * (Sec. 2.2, structured quadratic objective). */
+static void apply_Q(const oracle_csr* P, const double* pval, const oracle_csr* R, const double* rval,
+                    int32_t n, const double* v, double* out, double* tmp, double* tk) {
+  if (P) spmv(P, pval, v, out);
+  else for (int32_t i = 0; i < n; ++i) out[i] = 0.0;
+  if (R) {
+    spmv(R, rval, v, tk);
+    spmv_t(R, rval, tk, tmp);
+    for (int32_t i = 0; i < n; ++i) out[i] += tmp[i];
+  }
+}
 
 /* out = H v = Q v + v / tau */
 static void apply_H(const hop_t* h, const double* v, double* out) {
-  if (h->Q) spmv(h->Q, h->qval, v, out);
-  else for (int32_t i = 0; i < h->n; ++i) out[i] = 0.0;
+  apply_Q(h->Q, h->qval, h->R, h->rval, h->n, v, out, h->tmp, h->tk);
   for (int32_t i = 0; i < h->n; ++i) out[i] += v[i] * h->inv_tau;
 }
 
@@ -383,6 +399,9 @@ int32_t oracle_inner_solve(int32_t n, const oracle_csr* Q, const double* lv, con
                            double tau, const double* b, double eps, int32_t max_it, int32_t method,
                            double* x) {
   hop_t h;
+  h.R = NULL;
+  h.rval = NULL;
+  h.tk = NULL;
   h.Q = Q;
   h.qval = Q ? Q->val : NULL;
   h.inv_tau = 1.0 / tau;
@@ -477,11 +496,37 @@ static int csr_is_diagonal(const oracle_csr* Q) {
   return 1;
 }
 
+static int solve_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* R, const oracle_csr* A,
+                      const double* c, const double* lc, const double* uc, const double* lv,
+                      const double* uv, const oracle_params* prm, const double* x_init,
+                      const double* y_init, double* x_out, double* y_out, oracle_result* res,
+                      double* eps_trace, int32_t eps_trace_len);
+
 int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A, const double* c,
                  const double* lc, const double* uc, const double* lv, const double* uv,
                  const oracle_params* prm, const double* x_init, const double* y_init,
                  double* x_out, double* y_out, oracle_result* res, double* eps_trace,
                  int32_t eps_trace_len) {
+  return solve_impl(n, m, Q, NULL, A, c, lc, uc, lv, uv, prm, x_init, y_init, x_out, y_out, res, eps_trace,
+                    eps_trace_len);
+}
+
+/* Q = P + R^T R with R k x n, applied matrix-free (Sec. 2.2).  Readings: the
+ * Ruiz factors come from P and A (R^T R is never formed); the scaled factor is
+ * R D; the bound on ||Q|| used by the BB step range is the Gershgorin bound of
+ * the scaled P plus ||R D||_1 ||R D||_inf (>= ||R D||_2^2). */
+int oracle_solve_qr(int32_t n, int32_t m, const oracle_csr* P, const oracle_csr* R, const oracle_csr* A,
+                    const double* c, const double* lc, const double* uc, const double* lv,
+                    const double* uv, const oracle_params* prm, const double* x_init,
+                    const double* y_init, double* x_out, double* y_out, oracle_result* res) {
+  return solve_impl(n, m, P, R, A, c, lc, uc, lv, uv, prm, x_init, y_init, x_out, y_out, res, NULL, 0);
+}
+
+static int solve_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* R, const oracle_csr* A,
+                      const double* c, const double* lc, const double* uc, const double* lv,
+                      const double* uv, const oracle_params* prm, const double* x_init,
+                      const double* y_init, double* x_out, double* y_out, oracle_result* res,
+                      double* eps_trace, int32_t eps_trace_len) {
   double t_start = now_seconds();
   memset(res, 0, sizeof(*res));
   const int64_t nz_q = Q ? Q->rowptr[n] : 0;
@@ -520,6 +565,27 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
     for (int64_t k = Q->rowptr[i]; k < Q->rowptr[i + 1]; ++k) s += fabs(qv[k]);
     gersh = fmax(gersh, s);
   }
+  /* structured part: scaled R D, and its contribution to the bound on ||Q|| */
+  const int32_t kr = R ? R->nrows : 0;
+  const int64_t nz_r = R ? R->rowptr[kr] : 0;
+  double* rv = (double*)malloc(sizeof(double) * (size_t)(nz_r > 0 ? nz_r : 1));
+  double* rtmp = (double*)malloc(sizeof(double) * nn);
+  double* rtk = (double*)malloc(sizeof(double) * (size_t)(kr > 0 ? kr : 1));
+  if (R) {
+    double* colsum = (double*)calloc(nn, sizeof(double));
+    double rowmax = 0.0;
+    for (int32_t i = 0; i < kr; ++i) {
+      double s = 0.0;
+      for (int64_t k = R->rowptr[i]; k < R->rowptr[i + 1]; ++k) {
+        rv[k] = R->val[k] * D[R->col[k]];
+        s += fabs(rv[k]);
+        colsum[R->col[k]] += fabs(rv[k]);
+      }
+      rowmax = fmax(rowmax, s);
+    }
+    gersh += rowmax * norminf(colsum, n);
+    free(colsum);
+  }
 
   /* --- step size eta = 0.998 / ||A|| (Sec. 3.2); norm by Lanczos (reading) --- */
   int32_t piters = 0;
@@ -529,7 +595,7 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
 
   /* --- inner solver dispatch (Sec. 2.2; reading: AUTO = closed form for
    *     diagonal Q, BB-PG when any variable bound is finite, else CG) --- */
-  int diagQ = csr_is_diagonal(Q);
+  int diagQ = csr_is_diagonal(Q) && !R;
   int any_box = 0;
   for (int32_t j = 0; j < n; ++j)
     if (isfinite(lv[j]) || isfinite(uv[j])) any_box = 1;
@@ -564,10 +630,13 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
   double tau = eta / omega, sigma = eta * omega;
 
   hop_t h;
+  h.R = R;
+  h.rval = rv;
+  h.tk = rtk;
   h.Q = Q;
   h.qval = qv;
   h.n = n;
-  h.tmp = NULL;
+  h.tmp = rtmp;
 
   double eps_in = INFINITY, mv = 0.0;
   double fpr_anchor = 0.0, fpr_last = 0.0;
@@ -646,8 +715,7 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
       for (int32_t i = 0; i < m; ++i) uAx[i] = uAx[i] / E[i];
       spmv_t(A, av, yp, uATy);
       for (int32_t j = 0; j < n; ++j) uATy[j] = uATy[j] / D[j];
-      if (Q) spmv(Q, qv, xp, uQx);
-      else for (int32_t j = 0; j < n; ++j) uQx[j] = 0.0;
+      apply_Q(Q, qv, R, rv, n, xp, uQx, rtmp, rtk);
       for (int32_t j = 0; j < n; ++j) uQx[j] = uQx[j] / D[j];
       oracle_kkt(n, m, ux, uy, uAx, uATy, uQx, c, lc, uc, lv, uv, kkt);
       double rmax = fmax(kkt[0], fmax(kkt[1], kkt[2]));
@@ -687,8 +755,8 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
           for (int32_t j = 0; j < n; ++j) v1 = fmax(v1, fabs(dd[j] - proj_recc(dd[j], lvs[j], uvs[j])));
           spmv(A, av, dd, t_m);
           for (int32_t i = 0; i < m; ++i) v2 = fmax(v2, fabs(t_m[i] - proj_recc(t_m[i], lcs[i], ucs[i])));
-          if (Q) {
-            spmv(Q, qv, dd, t_n);
+          if (Q || R) {
+            apply_Q(Q, qv, R, rv, n, dd, t_n, rtmp, rtk);
             v3 = norminf(t_n, n);
           }
           if (cd < -prm->eps_tol && fmax(v1, fmax(v2, v3)) <= prm->eps_inf) {
@@ -767,6 +835,6 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
   free(D); free(E); free(qv); free(av); free(cs); free(lvs); free(uvs); free(lcs); free(ucs);
   free(qdiag); free(x); free(y); free(xa); free(ya); free(xp); free(yp); free(xn); free(yn);
   free(g); free(b); free(xbar); free(axb); free(ux); free(uy); free(uAx); free(uATy); free(uQx);
-  free(dd); free(ytil); free(t_n); free(t_m);
+  free(dd); free(ytil); free(t_n); free(t_m); free(rv); free(rtmp); free(rtk);
   return 0;
 }

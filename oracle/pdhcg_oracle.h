@@ -72,6 +72,12 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
                  double* x_out, double* y_out, oracle_result* res, double* eps_trace,
                  int32_t eps_trace_len);
 
+/* The same with Q = P + R^T R (R: k x n), applied as P v + R^T (R v). */
+int oracle_solve_qr(int32_t n, int32_t m, const oracle_csr* P, const oracle_csr* R, const oracle_csr* A,
+                    const double* c, const double* lc, const double* uc, const double* lv,
+                    const double* uv, const oracle_params* prm, const double* x_init,
+                    const double* y_init, double* x_out, double* y_out, oracle_result* res);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,9 @@ class QP:
     uv: np.ndarray
     name: str = "qp"
     meta: dict = field(default_factory=dict)
+    # structured objective (Sec. 2.2): when set, the quadratic term is Q + R^T R
+    # with Q holding the sparse part P and R (k x n) the low-rank factor
+    R: sp.csr_matrix | None = None
 
     def nnz(self) -> int:
         return int(self.A.nnz + (self.Q.nnz if self.Q is not None else 0))
@@ -82,11 +85,13 @@ def _sprandn_rowdeg(rng, rows, cols, per_row, scale=1.0):
 
 
 def random_qp(n=200, m=100, n_eq=50, density=0.05, m_rows=50, seed=0, box=10.0,
-              per_row=None, infeasible=False) -> QP:
+              per_row=None, infeasible=False, factored=False) -> QP:
     """Tiny random convex QP: Q = M^T M + 0.01 I, M m_rows x n, A m x n, both at ``density``
     (or ~``per_row`` nonzeros per row when given), entries N(0,1); c ~ N(0,1); box [-box, box].
     Feasible by construction: x0 ~ U(-5,5), b_eq = A_eq x0, b_ineq = A_ineq x0 + U(0,1).
-    ``infeasible`` duplicates one equality row with right-hand side + 1."""
+    ``infeasible`` duplicates one equality row with right-hand side + 1.
+    ``factored`` returns the same objective as P = 0.01 I plus the factor R = M
+    (Sec. 2.2's structured Q = P + R^T R) instead of the formed M^T M + 0.01 I."""
     rng = np.random.default_rng(seed)
     if per_row is None:
         M = _sprandn(rng, m_rows, n, density)
@@ -114,6 +119,9 @@ def random_qp(n=200, m=100, n_eq=50, density=0.05, m_rows=50, seed=0, box=10.0,
         uc = np.append(uc, uc[0] + 1.0)
         m += 1
         name += "_infeasible"
+    if factored:
+        return QP(n, m, _csr(0.01 * sp.identity(n, format="csr")), A, c, lc, uc, lv, uv,
+                  name=name + "_factored", meta={"x_feasible": x0}, R=_csr(M))
     return QP(n, m, Q, A, c, lc, uc, lv, uv, name=name, meta={"x_feasible": x0})
 
 

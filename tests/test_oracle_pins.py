@@ -373,3 +373,20 @@ def test_lasso_matches_sklearn(seed):
     ref = Lasso(alpha=lam / (2 * rows), fit_intercept=False, tol=1e-14, max_iter=10**6).fit(A, b).coef_
     assert f(x[:cols]) == pytest.approx(f(ref), rel=1e-8)
     assert r["primal_obj"] == pytest.approx(f(ref), rel=1e-8)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_factored_q_reaches_the_formed_q_optimum(seed):
+    # Sec. 2.2's structured objective: Q = P + R^T R applied matrix-free must
+    # reach the optimum of the same QP with Q formed explicitly (scipy product)
+    qf = W.random_qp(seed=seed, factored=True)
+    formed = W.QP(qf.n, qf.m, W._csr(qf.Q + qf.R.T @ qf.R), qf.A, qf.c, qf.lc, qf.uc, qf.lv, qf.uv)
+    xf, yf, rf = oracle.solve(qf, oracle.default_params(eps_tol=1e-9, max_iter=2_000_000))
+    x, y, r = oracle.solve(formed, oracle.default_params(eps_tol=1e-9, max_iter=2_000_000))
+    assert rf["status_name"] == r["status_name"] == "OPTIMAL"
+    assert rf["primal_obj"] == pytest.approx(r["primal_obj"], rel=1e-8)
+    # the factored solution satisfies the formed problem's KKT conditions
+    Qx = formed.Q @ xf
+    rp, rd, rg, _, _ = oracle.kkt(formed.n, formed.m, xf, yf, formed.A @ xf, formed.A.T @ yf, Qx,
+                                  formed.c, formed.lc, formed.uc, formed.lv, formed.uv)
+    assert max(rp, rd, rg) <= 2e-9
