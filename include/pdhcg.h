@@ -142,7 +142,7 @@ int pdhcg_default_params(pdhcg_params* p);
 
 /* Validate the problem, copy it to the device and run the setup of the method
  * on the device: Ruiz equilibration of [Q A^T; A 0] (reading of the paper's
- * "system scaling"), the power-iteration estimate of ||A||_2 for
+ * "system scaling"), the Lanczos estimate of ||A||_2 for
  * eta = 0.998/||A|| (Sec. 3.2), Gershgorin bound of Q for the BB step range,
  * and the initial primal weight.  Q may be NULL (LP).  A must be given even
  * when m = 0 (nrows = 0).  lc, uc: m entries; c, lv, uv: n entries.
@@ -153,6 +153,16 @@ int pdhcg_default_params(pdhcg_params* p);
 int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
                  const double* uc, const double* lv, const double* uv, const pdhcg_params* params,
                  void* cuda_stream, pdhcg_t** out);
+
+/* Structured quadratic term Q = P + R^T R (Sec. 2.2): P n x n symmetric (or NULL
+ * for P = 0), R k x n (k >= 1).  R^T R is never formed: every product with Q is
+ * P v + R^T (R v), the k-vector R v taken by a phase of its own.  Other
+ * arguments and ownership as pdhcg_create.  Scaling reads the Ruiz factors off
+ * P and A only; the step range of the BB inner solver bounds ||R D||_2^2 by
+ * ||R D||_1 ||R D||_inf.  The handle works with every solve entry point. */
+int pdhcg_create_qr(const pdhcg_csr* P, const pdhcg_csr* R, const pdhcg_csr* A, const double* c,
+                    const double* lc, const double* uc, const double* lv, const double* uv,
+                    const pdhcg_params* params, void* cuda_stream, pdhcg_t** out);
 
 /* One problem of a batch creation (same meaning as the pdhcg_create arguments). */
 typedef struct {

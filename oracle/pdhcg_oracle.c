@@ -158,8 +158,22 @@ void oracle_default_params(oracle_params* p) {
  * divides every column j of K by sqrt(max_i |K_ij|) of the currently scaled
  * matrix.  The scaled entries are (Q_ij*D_i)*D_j and (A_ij*E_i)*D_j.
  * Reading: the paper names a "system scaling factor" but no scaling method. */
+static void ruiz_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* R, const oracle_csr* A,
+                      int32_t passes, double* D, double* E);
+
 void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A, int32_t passes,
                  double* D, double* E) {
+  ruiz_impl(n, m, Q, NULL, A, passes, D, E);
+}
+
+/* With a structured Q = P + R^T R (reading): the column maximum of Q is taken
+ * over the entries of P and the diagonal of R^T R (squared column norms of R),
+ * which bounds every entry of R^T R in its row and column. */
+static void ruiz_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* R, const oracle_csr* A,
+                      int32_t passes, double* D, double* E) {
+  double* rd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  for (int32_t l = 0; R && l < R->nrows; ++l)
+    for (int64_t k = R->rowptr[l]; k < R->rowptr[l + 1]; ++k) rd[R->col[k]] += R->val[k] * R->val[k];
   for (int32_t j = 0; j < n; ++j) D[j] = 1.0;
   for (int32_t i = 0; i < m; ++i) E[i] = 1.0;
   double* cn = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -175,6 +189,7 @@ void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
           cn[j] = fmax(cn[j], v);
         }
     }
+    for (int32_t j = 0; R && j < n; ++j) cn[j] = fmax(cn[j], (rd[j] * D[j]) * D[j]);
     for (int32_t i = 0; i < m; ++i)
       for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
         int32_t j = A->col[k];
@@ -187,6 +202,7 @@ void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
   }
   free(cn);
   free(rn);
+  free(rd);
 }
 
 /* Number of eigenvalues below x of the symmetric tridiagonal matrix with
@@ -512,9 +528,10 @@ int oracle_solve(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
 }
 
 /* Q = P + R^T R with R k x n, applied matrix-free (Sec. 2.2).  Readings: the
- * Ruiz factors come from P and A (R^T R is never formed); the scaled factor is
- * R D; the bound on ||Q|| used by the BB step range is the Gershgorin bound of
- * the scaled P plus ||R D||_1 ||R D||_inf (>= ||R D||_2^2). */
+ * Ruiz factors come from P, A and the diagonal of R^T R (R^T R is never
+ * formed); the scaled factor is R D; the bound on ||Q|| used by the BB step
+ * range is the Gershgorin bound of the scaled P plus ||R D||_1 ||R D||_inf
+ * (>= ||R D||_2^2). */
 int oracle_solve_qr(int32_t n, int32_t m, const oracle_csr* P, const oracle_csr* R, const oracle_csr* A,
                     const double* c, const double* lc, const double* uc, const double* lv,
                     const double* uv, const oracle_params* prm, const double* x_init,
@@ -536,7 +553,7 @@ static int solve_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_cs
   /* --- setup: scaling, scaled data (reading: Ruiz) --- */
   double* D = (double*)malloc(sizeof(double) * nn);
   double* E = (double*)malloc(sizeof(double) * mm);
-  oracle_ruiz(n, m, Q, A, prm->ruiz_iters, D, E);
+  ruiz_impl(n, m, Q, R, A, prm->ruiz_iters, D, E);
   double* qv = (double*)malloc(sizeof(double) * (size_t)(nz_q > 0 ? nz_q : 1));
   double* av = (double*)malloc(sizeof(double) * (size_t)(nz_a > 0 ? nz_a : 1));
   for (int32_t i = 0; Q && i < n; ++i)

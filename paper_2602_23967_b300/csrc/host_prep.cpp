@@ -113,7 +113,7 @@ int8_t bound_type(double l, double u) {
 }  // namespace
 
 int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
-                  const double* uc, const double* lv, const double* uv, HostQP* h) {
+                  const double* uc, const double* lv, const double* uv, HostQP* h, const pdhcg_csr* R) {
   if (A == nullptr) return invalid("A must be given (use nrows = 0 for no constraints)");
   const int32_t n = A->ncols, m = A->nrows;
   if (n <= 0) return invalid("n must be positive");
@@ -157,6 +157,36 @@ int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const
     h->Qp.assign(size_t(n) + 1, 0);
     h->Qc.clear();
     h->Qv.clear();
+  }
+  if (R) {
+    // Q v = P v + R^T (R v): keep R, and store [P | R^T] in the Q arrays
+    if (R->ncols != n || R->nrows <= 0) return invalid("R: must be k x n with k >= 1");
+    h->k = R->nrows;
+    rc = canon_csr(R, "R", h->k, n, h->Rp, h->Rc, h->Rv);
+    if (rc) return rc;
+    std::vector<int32_t> tp, tc;
+    std::vector<double> tv;
+    transpose(h->k, n, h->Rp, h->Rc, h->Rv, tp, tc, tv);
+    std::vector<int32_t> qp(size_t(n) + 1, 0), qc;
+    std::vector<double> qv;
+    qc.reserve(h->Qc.size() + tc.size());
+    qv.reserve(h->Qv.size() + tv.size());
+    for (int32_t j = 0; j < n; ++j) {
+      for (int32_t q = h->Qp[j]; q < h->Qp[j + 1]; ++q) {
+        qc.push_back(h->Qc[q]);
+        qv.push_back(h->Qv[q]);
+      }
+      for (int32_t q = tp[j]; q < tp[j + 1]; ++q) {
+        qc.push_back(n + tc[q]);
+        qv.push_back(tv[q]);
+      }
+      qp[size_t(j) + 1] = int32_t(qc.size());
+    }
+    h->Qp.swap(qp);
+    h->Qc.swap(qc);
+    h->Qv.swap(qv);
+    h->has_q = true;
+    h->diag_q = false;
   }
   transpose(m, n, h->Ap, h->Ac, h->Av, h->ATp, h->ATc, h->ATv);
   h->c.assign(c, c + n);

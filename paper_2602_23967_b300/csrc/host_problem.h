@@ -19,6 +19,11 @@ void set_error(const std::string& msg);
 struct HostQP {
   int32_t n = 0, m = 0;
   int32_t m_user = 0;  // rows of the caller's problem (m also counts lifted bound rows)
+  // structured objective Q = P + R^T R (Sec. 2.2): R is k x n; the Q arrays then
+  // hold [P | R^T] (n x (n + k)), i.e. Q v = [P | R^T] [v; R v]
+  int32_t k = 0;
+  std::vector<int32_t> Rp, Rc;
+  std::vector<double> Rv;
   bool has_q = false, diag_q = true, any_box = false;
   std::vector<int32_t> Qp, Qc, Ap, Ac, ATp, ATc;
   std::vector<double> Qv, Av, ATv;
@@ -28,7 +33,8 @@ struct HostQP {
 
 // Validate and canonicalise; returns PDHCG_OK or PDHCG_E_INVALID (with set_error).
 int build_host_qp(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc,
-                  const double* uc, const double* lv, const double* uv, HostQP* out);
+                  const double* uc, const double* lv, const double* uv, HostQP* out,
+                  const pdhcg_csr* R = nullptr);
 // PDHCG_INNER_CG_LIFTED: append a row e_j^T for every variable with a finite
 // bound (row bounds = that variable's bounds) and make every variable free.
 void lift_box_rows(HostQP* h);
@@ -56,10 +62,11 @@ size_t device_footprint(const HostQP& h, int precision);
 
 struct PartitionSet {
   int nblk = 0;
-  int32_t* d_buf = nullptr;  // 8 tables of nblk + 1 entries
+  int32_t* d_buf = nullptr;  // 11 tables of nblk + 1 entries
   int32_t *v_slice = nullptr, *v_long = nullptr, *v_huge = nullptr;
   int32_t *c_slice = nullptr, *c_long = nullptr, *c_huge = nullptr;
   int32_t *v_even = nullptr, *c_even = nullptr;  // even row splits for elementwise work
+  int32_t *r_slice = nullptr, *r_long = nullptr, *r_huge = nullptr;  // rows of R (structured Q)
 };
 
 }  // namespace pdhcg
@@ -71,6 +78,7 @@ namespace pdhcg {
 struct CreateInput {
   const pdhcg_csr *Q, *A;
   const double *c, *lc, *uc, *lv, *uv;
+  const pdhcg_csr* R = nullptr;  // structured objective: Q + R^T R
 };
 
 // Memory sources a long-running caller (the serving loop) hands to creation so
@@ -114,12 +122,24 @@ struct pdhcg_problem {
   int method = PDHCG_INNER_DIAG;
   int32_t n = 0, m = 0;
   int32_t m_user = 0;  // rows the caller sees (m may add lifted bound rows)
-  int64_t nnzQ = 0, nnzA = 0;
+  int32_t k = 0;       // rows of R in a structured objective Q = P + R^T R (0: none)
+  int64_t nnzQ = 0, nnzA = 0, nnzR = 0;
   bool has_q = false;
   int lanes_var = 4, lanes_con = 4;
   // host copies kept for partitioning
   std::vector<int32_t> Qp, Ap, ATp;
+  std::vector<int32_t> Rp;
   pdhcg::SellHost vsell, csell;  // integer SELL layouts (var space: AT [+ Q], con space: A)
+  pdhcg::SellHost rsell;         // rows of R (structured objective)
+  int32_t *r_perm = nullptr, *r_longs = nullptr, *r_huges = nullptr;
+  int64_t* sRp = nullptr;
+  int32_t* sRc = nullptr;
+  void* sRv = nullptr;  // MatT
+  size_t rsell_cols = 0;
+  int32_t *Rp_d = nullptr, *Rc_d = nullptr;
+  double* Rv_o = nullptr;
+  void* Rs = nullptr;               // MatT, scaled R D
+  void *rt1 = nullptr, *rt2 = nullptr;  // VecT, R v products (k each)
   // device SELL arrays
   int32_t *v_perm = nullptr, *v_longs = nullptr, *v_huges = nullptr;
   int32_t *c_perm = nullptr, *c_longs = nullptr, *c_huges = nullptr;

@@ -18,37 +18,45 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
   size_t want = solve_dyn_smem() + extra;
   const size_t static_part = 8192;  // group_reduce / row-engine shared arrays
   if (want + static_part > size_t(optin)) want = size_t(optin) - static_part;
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel<kGroupBS, MatT, VecT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
-  if (e == cudaSuccess && kPoolBS != kGroupBS)
-    e = cudaFuncSetAttribute(solve_kernel<kPoolBS, MatT, VecT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(want));
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {(const void*)solve_kernel<kGroupBS, MatT, VecT, false>,
+                        (const void*)solve_kernel<kGroupBS, MatT, VecT, true>,
+                        (const void*)solve_kernel<kPoolBS, MatT, VecT, false>,
+                        (const void*)solve_kernel<kPoolBS, MatT, VecT, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
   return e;
 }
 
 template <class MatT, class VecT>
 int pool_blocks_per_sm(size_t smem_vec_bytes) {
-  int nb = 0;
+  int nb = 0, nr = 0;
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT>, kPoolBS,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT, false>, kPoolBS,
+                                                    solve_dyn_smem() + smem_vec_bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kPoolBS, MatT, VecT, true>, kPoolBS,
                                                     solve_dyn_smem() + smem_vec_bytes) != cudaSuccess)
     return 0;
+  nb = std::min(nb, nr);
   if (PDHCG_POOL_MAX_PER_SM > 0) nb = std::min(nb, int(PDHCG_POOL_MAX_PER_SM));
   return nb;
 }
 
 template <class MatT, class VecT>
 cudaError_t kernel_limits(KernelLimits* out) {
-  int dev = 0, sms = 0, nb = 0, ns = 0;
+  int dev = 0, sms = 0, nb = 0, nr = 0, ns = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   e = set_solve_attrs<MatT, VecT>();
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT>, kGroupBS,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS,
                                                     solve_dyn_smem());
   if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kGroupBS, MatT, VecT, true>, kGroupBS,
+                                                    solve_dyn_smem());
+  if (e != cudaSuccess) return e;
+  nb = std::min(nb, nr);  // a cooperative launch of either variant must fit
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ns, setup_kernel<kGroupBS, MatT, VecT>, kGroupBS, 0);
   if (e != cudaSuccess) return e;
   out->max_coresident_group = sms * nb;
@@ -78,13 +86,18 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
   if (e != cudaSuccess) return e;
   const size_t smem = solve_dyn_smem() + extra;
+  const bool r = plan.structured != 0;
   if (plan.group_blocks == 0) {
-    solve_kernel<kPoolBS, MatT, VecT><<<grid, kPoolBS, smem, s>>>(di, p);
+    if (r)
+      solve_kernel<kPoolBS, MatT, VecT, true><<<grid, kPoolBS, smem, s>>>(di, p);
+    else
+      solve_kernel<kPoolBS, MatT, VecT, false><<<grid, kPoolBS, smem, s>>>(di, p);
     return cudaGetLastError();
   }
   void* args[] = {&di, &p};
-  return cudaLaunchCooperativeKernel((const void*)solve_kernel<kGroupBS, MatT, VecT>, dim3(grid),
-                                     dim3(kGroupBS), args, smem, s);
+  return cudaLaunchCooperativeKernel(r ? (const void*)solve_kernel<kGroupBS, MatT, VecT, true>
+                                       : (const void*)solve_kernel<kGroupBS, MatT, VecT, false>,
+                                     dim3(grid), dim3(kGroupBS), args, smem, s);
 }
 
 template <class MatT, class VecT>

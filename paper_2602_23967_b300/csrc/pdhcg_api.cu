@@ -105,6 +105,17 @@ void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
   P->sATc = cv.take<int32_t>(P->vsell_cols[0] + 16);
   P->sQc = cv.take<int32_t>(P->vsell_cols[1] + 16);
   P->sAc = cv.take<int32_t>(P->csell_cols + 16);
+  if (P->k > 0) {
+    const size_t k = size_t(P->k), nr = size_t(P->nnzR);
+    P->Rp_d = cv.take<int32_t>(k + 1);
+    P->Rc_d = cv.take<int32_t>(nr);
+    P->Rv_o = cv.take<double>(nr);
+    P->r_perm = cv.take<int32_t>(P->rsell.perm.size());
+    P->r_longs = cv.take<int32_t>(P->rsell.longs.size());
+    P->r_huges = cv.take<int32_t>(P->rsell.huges.size());
+    P->sRp = cv.take<int64_t>(P->rsell.ptr[0].size());
+    P->sRc = cv.take<int32_t>(P->rsell_cols + 16);
+  }
   if (!external_state) P->st = cv.take<SolverState>(1);
   P->input_bytes = (cv.off + 255) & ~size_t(255);
   // ---- computed on the device ----
@@ -114,6 +125,12 @@ void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
   P->sATv = cv.take_bytes(P->vsell_cols[0] + 16, mb);
   P->sQv = cv.take_bytes(P->vsell_cols[1] + 16, mb);
   P->sAv = cv.take_bytes(P->csell_cols + 16, mb);
+  if (P->k > 0) {
+    P->Rs = cv.take_bytes(size_t(P->nnzR), mb);
+    P->sRv = cv.take_bytes(P->rsell_cols + 16, mb);
+    P->rt1 = cv.take_bytes(size_t(P->k), vb);
+    P->rt2 = cv.take_bytes(size_t(P->k), vb);
+  }
   P->D = cv.take<double>(n);
   P->E = cv.take<double>(m);
   P->Dn = cv.take<double>(n);
@@ -179,6 +196,16 @@ void pack_inputs(const pdhcg_problem* P, const HostQP& h, char* stage) {
   put(P->sATc, P->vsell.col[0].data(), sizeof(int32_t) * P->vsell.col[0].size());
   put(P->sQc, P->vsell.col[1].data(), sizeof(int32_t) * P->vsell.col[1].size());
   put(P->sAc, P->csell.col[0].data(), sizeof(int32_t) * P->csell.col[0].size());
+  if (P->k > 0) {
+    put(P->Rp_d, h.Rp.data(), sizeof(int32_t) * h.Rp.size());
+    put(P->Rc_d, h.Rc.data(), sizeof(int32_t) * h.Rc.size());
+    put(P->Rv_o, h.Rv.data(), sizeof(double) * h.Rv.size());
+    put(P->r_perm, P->rsell.perm.data(), sizeof(int32_t) * P->rsell.perm.size());
+    put(P->r_longs, P->rsell.longs.data(), sizeof(int32_t) * P->rsell.longs.size());
+    put(P->r_huges, P->rsell.huges.data(), sizeof(int32_t) * P->rsell.huges.size());
+    put(P->sRp, P->rsell.ptr[0].data(), sizeof(int64_t) * P->rsell.ptr[0].size());
+    put(P->sRc, P->rsell.col[0].data(), sizeof(int32_t) * P->rsell.col[0].size());
+  }
   if (static_cast<const char*>(static_cast<const void*>(P->st)) >= base &&
       static_cast<const char*>(static_cast<const void*>(P->st)) < base + P->input_bytes) {
     SolverState S{};
@@ -269,12 +296,24 @@ int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
     const int32_t nh = b.back();
     for (int k = 0; k <= nblk; ++k) b[size_t(k)] = std::max(0, std::min(nh, k - (nblk - nh)));
   }
+  // rows of R (structured objective): slices, long and huge rows like the other spaces
+  std::vector<int32_t> rt[3];
+  if (P->k > 0) {
+    rt[0] = split_balanced(slice_w(P->rsell, 1), nblk);
+    rt[1] = split_balanced(row_w(P->rsell.longs, &P->Rp, nullptr), nblk);
+    rt[2] = split_balanced(row_w(P->rsell.huges, &P->Rp, nullptr), nblk);
+    const int32_t nh = rt[2].back();
+    for (int k = 0; k <= nblk; ++k) rt[2][size_t(k)] = std::max(0, std::min(nh, k - (nblk - nh)));
+  } else {
+    for (auto& t : rt) t.assign(size_t(nblk) + 1, 0);
+  }
   const size_t per = size_t(nblk) + 1;
-  CK(cudaMalloc(&ps.d_buf, sizeof(int32_t) * per * 8));
+  CK(cudaMalloc(&ps.d_buf, sizeof(int32_t) * per * 11));
   std::vector<int32_t> flat;
   for (auto& t : tabs) flat.insert(flat.end(), t.begin(), t.end());
   flat.insert(flat.end(), ev.begin(), ev.end());
   flat.insert(flat.end(), ec.begin(), ec.end());
+  for (auto& t : rt) flat.insert(flat.end(), t.begin(), t.end());
   CK(cudaMemcpy(ps.d_buf, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
   ps.v_slice = ps.d_buf;
   ps.v_long = ps.d_buf + per;
@@ -284,6 +323,9 @@ int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
   ps.c_huge = ps.d_buf + 5 * per;
   ps.v_even = ps.d_buf + 6 * per;
   ps.c_even = ps.d_buf + 7 * per;
+  ps.r_slice = ps.d_buf + 8 * per;
+  ps.r_long = ps.d_buf + 9 * per;
+  ps.r_huge = ps.d_buf + 10 * per;
   auto res = P->partitions.emplace(nblk, ps);
   *out = &res.first->second;
   return PDHCG_OK;
@@ -373,6 +415,19 @@ Inst<MatT, VecT> make_inst(const pdhcg_problem* P) {
   I.xbar = static_cast<VecT*>(P->xbar);
   I.st = P->st;
   I.prm = dev_params(P->prm);
+  if (P->k > 0) {
+    I.k = P->k;
+    I.R = Csr<MatT>{P->k, int32_t(P->nnzR), P->Rp_d, P->Rc_d, static_cast<const MatT*>(P->Rs)};
+    I.Rsl = Sell<MatT>{P->sRp, P->sRc, static_cast<const MatT*>(P->sRv)};
+    I.rsp.nslices = P->rsell.nslices;
+    I.rsp.nlong = int32_t(P->rsell.longs.size());
+    I.rsp.nhuge = int32_t(P->rsell.huges.size());
+    I.rsp.perm = P->r_perm;
+    I.rsp.longs = P->r_longs;
+    I.rsp.huges = P->r_huges;
+    I.rt1 = static_cast<VecT*>(P->rt1);
+    I.rt2 = static_cast<VecT*>(P->rt2);
+  }
   return I;
 }
 
@@ -386,6 +441,9 @@ void set_partition(Inst<MatT, VecT>& I, const PartitionSet& ps, const pdhcg_prob
   I.csp.huge_part = ps.c_huge;
   I.var_part = ps.v_even;
   I.con_part = ps.c_even;
+  I.rsp.slice_part = ps.r_slice;
+  I.rsp.long_part = ps.r_long;
+  I.rsp.huge_part = ps.r_huge;
   I.part_blocks = ps.nblk;
   (void)P;
 }
@@ -477,7 +535,7 @@ size_t smem_need(const pdhcg_problem* P) {
 
 int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
   if (P->prm.group_blocks > 0) return std::min(P->prm.group_blocks, maxblk);
-  const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ : 0) + 2 * P->nnzA + P->n + P->m;
+  const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ + P->nnzR : 0) + 2 * P->nnzA + P->n + P->m;
   if (work < 150000) return 1;
   return int(std::max<int64_t>(2, std::min<int64_t>(maxblk, work / 8192)));
 }
@@ -558,6 +616,17 @@ SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) 
   a.sATv = static_cast<M*>(P->sATv);
   a.sQv = static_cast<M*>(P->sQv);
   a.sAv = static_cast<M*>(P->sAv);
+  if (P->k > 0) {
+    a.k = P->k;
+    a.Rp = P->Rp_d;
+    a.Rc = P->Rc_d;
+    a.Rv_o = P->Rv_o;
+    a.Rs = static_cast<M*>(P->Rs);
+    a.rsp.nslices = P->rsell.nslices;
+    a.rsp.perm = P->r_perm;
+    a.sRp = P->sRp;
+    a.sRv = static_cast<M*>(P->sRv);
+  }
   return a;
 }
 
@@ -621,6 +690,7 @@ int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_re
     int64_t zero = 0;
     CK(cudaMemcpyAsync(P->part_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, P->stream));
     LaunchPlan plan;
+    plan.structured = P->k > 0;
     plan.err = P->plan_i32 + 5;
     plan.timeout_ns = uint64_t(std::max(P->prm.device_timeout_ms, 1)) * 1000000ull;
     int grid = 1;
@@ -720,7 +790,7 @@ namespace pdhcg {
 // the SELL layouts.  No device work.
 int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream, pdhcg_problem** out,
                     HostQP* h) {
-  int rc = build_host_qp(in.Q, in.A, in.c, in.lc, in.uc, in.lv, in.uv, h);
+  int rc = build_host_qp(in.Q, in.A, in.c, in.lc, in.uc, in.lv, in.uv, h, in.R);
   if (rc) return rc;
   int method = prm.inner;
   if (method == PDHCG_INNER_CG_LIFTED) {
@@ -768,6 +838,15 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
   P->vsell_cols[0] = P->vsell.col[0].size();
   P->vsell_cols[1] = P->vsell.col[1].size();
   P->csell_cols = P->csell.col[0].size();
+  if (h->k > 0) {
+    P->k = h->k;
+    P->nnzR = int64_t(h->Rc.size());
+    P->Rp = h->Rp;
+    const std::vector<int32_t>* rrp[2] = {&h->Rp, nullptr};
+    const std::vector<int32_t>* rci[2] = {&h->Rc, nullptr};
+    build_sell(h->k, 1, rrp, rci, &P->rsell);
+    P->rsell_cols = P->rsell.col[0].size();
+  }
   *out = P;
   return PDHCG_OK;
 }
@@ -1031,6 +1110,7 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
     CK(cudaMemcpyAsync(d + ib, order.data(), ob, cudaMemcpyHostToDevice, s));
     int32_t* d_i32 = reinterpret_cast<int32_t*>(d + ib);
     LaunchPlan plan;
+    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
     plan.npool = count;
     plan.pool_inst = d_i32;
     plan.pool_next = d_i32 + count;
@@ -1065,6 +1145,18 @@ int pdhcg_create(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const 
   }
   *out = nullptr;
   CreateInput in{Q, A, c, lc, uc, lv, uv};
+  return create_impl(1, &in, params, cuda_stream, out, false);
+}
+
+int pdhcg_create_qr(const pdhcg_csr* P, const pdhcg_csr* R, const pdhcg_csr* A, const double* c,
+                    const double* lc, const double* uc, const double* lv, const double* uv,
+                    const pdhcg_params* params, void* cuda_stream, pdhcg_t** out) {
+  if (!out || !R) {
+    set_error("create_qr: out and R must be given");
+    return PDHCG_E_INVALID;
+  }
+  *out = nullptr;
+  CreateInput in{P, A, c, lc, uc, lv, uv, R};
   return create_impl(1, &in, params, cuda_stream, out, false);
 }
 
@@ -1294,6 +1386,7 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
     cudaError_t e = kernel_limits<M, V>(&kl);
     if (e != cudaSuccess) return cuda_fail(e, "kernel_limits");
     LaunchPlan plan;
+    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
     plan.npool = count;
     plan.pool_inst = d_i32;
     plan.pool_next = d_i32 + count;
@@ -1473,6 +1566,7 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
     CK(cudaMemcpyAsync(d_i32, g_noalloc_horder, sizeof(int32_t) * kNoAllocQueueWords, cudaMemcpyHostToDevice,
                        s));
     LaunchPlan plan;
+    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
     plan.npool = count;
     plan.pool_inst = d_i32;
     plan.pool_next = d_i32 + count;

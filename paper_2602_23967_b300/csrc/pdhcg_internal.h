@@ -99,6 +99,15 @@ struct Inst {
   const int32_t* con_part = nullptr;
   int32_t part_blocks = 0;
   int32_t long_row = 1 << 30;            // rows at least this long use the whole CTA
+  // Structured objective Q = P + R^T R (Sec. 2.2): Q / Qs hold [P | R^T] with
+  // columns n.. n+k-1 addressing R v, which a phase over the k rows of R puts in
+  // rt1 (rt2: a second product in the checks).  k = 0: plain Q.
+  int32_t k = 0;
+  Csr<MatT> R;
+  Sell<MatT> Rsl;
+  SpaceLayout rsp;
+  VecT* rt1 = nullptr;
+  VecT* rt2 = nullptr;
   // scaled problem data
   const VecT *c = nullptr, *lv = nullptr, *uv = nullptr, *lc = nullptr, *uc = nullptr,
              *qdiag = nullptr;
@@ -153,6 +162,9 @@ struct LaunchPlan {
   int64_t smem_vec_bytes = 0;
   uint64_t timeout_ns = 8000000000ull;  // bound on any device wait
   int32_t* err = nullptr;               // set to 1 when a bounded wait gave up
+  // Some instance has a structured Q = P + R^T R: launch the kernel variant
+  // with the R phases (the plain variant has none of their cost).
+  int32_t structured = 0;
 };
 
 }  // namespace pdhcg

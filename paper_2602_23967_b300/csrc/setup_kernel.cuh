@@ -39,6 +39,15 @@ struct SetupArgs {
   const int64_t *sATp, *sQp, *sAp;
   const int32_t *sATc, *sQc, *sAc;
   MatT *sATv, *sQv, *sAv;
+  // structured objective Q = P + R^T R: the Q arrays hold [P | R^T] (columns
+  // >= n address R v); R (k x n) with its scaled copy R D and SELL form
+  int32_t k;
+  const int32_t *Rp, *Rc;
+  const double* Rv_o;
+  MatT* Rs;
+  SpaceLayout rsp;
+  const int64_t* sRp;
+  MatT* sRv;
   VecT *c, *lv, *uv, *lc, *uc, *qdiag;
   SolverState* st;
 };
@@ -160,18 +169,31 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
   double* En = a.En;
   for_elems<BS>(vlo, vhi, [&](int j) { D[j] = 1.0; });
   for_elems<BS>(clo, chi, [&](int i) { E[i] = 1.0; });
+  // structured Q = P + R^T R: diag(R^T R) (squared column norms of R, the R^T
+  // entries of row j of the stored [P | R^T]) joins the column maxima of Ruiz
+  double* rdiag = a.pu;  // free until the Lanczos estimate
+  if (a.k > 0)
+    for_elems<BS>(vlo, vhi, [&](int j) {
+      double t = 0.0;
+      for (int q = a.Qp[j]; q < a.Qp[j + 1]; ++q)
+        if (a.Qc[q] >= a.n) t += a.Qv_o[q] * a.Qv_o[q];
+      rdiag[j] = t;
+    });
   if (!group_sync<BS>(g)) return;
 
   // ---- 1. Ruiz passes ----
   for (int pass = 0; pass < a.ruiz_iters; ++pass) {
     rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
       double cq = 0.0;
-      if (a.has_q)
-        cq = sub_row_max(a.Qp, j, valid, sl, Lv, [&](int k) { return fabs((a.Qv_o[k] * D[a.Qc[k]]) * D[j]); });
+      if (a.has_q)  // the P part only (columns < n) in a structured objective
+        cq = sub_row_max(a.Qp, j, valid, sl, Lv, [&](int k) {
+          return a.Qc[k] < a.n ? fabs((a.Qv_o[k] * D[a.Qc[k]]) * D[j]) : 0.0;
+        });
       double ca = sub_row_max(a.ATp, j, valid, sl, Lv,
                               [&](int k) { return fabs((a.ATv_o[k] * E[a.ATc[k]]) * D[j]); });
       if (valid && sl == 0) {
-        const double cn = fmax(cq, ca);
+        double cn = fmax(cq, ca);
+        if (a.k > 0) cn = fmax(cn, (rdiag[j] * D[j]) * D[j]);
         Dn[j] = D[j] * (cn > 0.0 ? 1.0 / sqrt(cn) : 1.0);
       }
     });
@@ -195,20 +217,28 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
   // ---- 2. scaled data ----
   double red[5];  // ||c~||^2, ||b~||^2, gersh (max), bscale (max), cinf (max)
   {
-    double cn2 = 0.0, bn2 = 0.0, gmax = 0.0, bsc = 0.0, cinf = 0.0;
+    double cn2 = 0.0, bn2 = 0.0, gmax = 0.0, bsc = 0.0, cinf = 0.0, rcol = 0.0;
     rows_loop<BS>(vlo, vhi, Lv, [&](int j, bool valid, int sl) {
-      double qd = 0.0, gs = 0.0;
+      double qd = 0.0, gs = 0.0, rs = 0.0;
       if (a.has_q) {
         if (valid)
           for (int k = a.Qp[j] + sl; k < a.Qp[j + 1]; k += Lv) {
-            const double v = (a.Qv_o[k] * D[j]) * D[a.Qc[k]];
-            a.Qs[k] = MatT(v);
-            if (a.Qc[k] == j) qd += v;
-            gs += fabs(v);
+            const int col = a.Qc[k];
+            if (col < a.n) {
+              const double v = (a.Qv_o[k] * D[j]) * D[col];
+              a.Qs[k] = MatT(v);
+              if (col == j) qd += v;
+              gs += fabs(v);
+            } else {  // (R^T)_j,(col-n) scaled: R D
+              const double v = a.Qv_o[k] * D[j];
+              a.Qs[k] = MatT(v);
+              rs += fabs(v);
+            }
           }
         for (int off = Lv >> 1; off > 0; off >>= 1) {
           qd += __shfl_xor_sync(kFull, qd, off);
           gs += __shfl_xor_sync(kFull, gs, off);
+          rs += __shfl_xor_sync(kFull, rs, off);
         }
       }
       if (valid)
@@ -222,6 +252,7 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
         a.qdiag[j] = VecT(qd);
         cn2 += cs * cs;
         gmax = fmax(gmax, gs);
+        rcol = fmax(rcol, rs);  // ||R D||_1 (largest column sum)
         cinf = fmax(cinf, fabs(a.c_o[j]));
       }
     });
@@ -238,18 +269,35 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
         if (isfinite(a.uc_o[i])) bsc = fmax(bsc, fabs(a.uc_o[i]));
       }
     });
-    red[0] = cn2;
-    red[1] = bn2;
-    red[2] = gmax;
-    red[3] = bsc;
-    red[4] = cinf;
-    if (!group_reduce<BS, 5>(g, red, (1u << 2) | (1u << 3) | (1u << 4))) return;
+    // rows of R: scaled copy R D and ||R D||_inf (largest row sum)
+    double rrow = 0.0;
+    if (a.k > 0) {
+      const int r0 = int(int64_t(a.k) * g.rank / g.nblk), r1 = int(int64_t(a.k) * (g.rank + 1) / g.nblk);
+      for (int l = r0 + int(threadIdx.x); l < r1; l += BS) {
+        double t = 0.0;
+        for (int q = a.Rp[l]; q < a.Rp[l + 1]; ++q) {
+          const double v = a.Rv_o[q] * D[a.Rc[q]];
+          a.Rs[q] = MatT(v);
+          t += fabs(v);
+        }
+        rrow = fmax(rrow, t);
+      }
+    }
+    double red7[7] = {cn2, bn2, gmax, bsc, cinf, rcol, rrow};
+    if (!group_reduce<BS, 7>(g, red7, (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6))) return;
+    red[0] = red7[0];
+    red[1] = red7[1];
+    // bound on ||Q||: Gershgorin of the scaled P plus ||R D||_2^2 <= ||R D||_1 ||R D||_inf
+    red[2] = red7[2] + red7[5] * red7[6];
+    red[3] = red7[3];
+    red[4] = red7[4];
   }
 
   // ---- SELL values of the scaled matrices (the solve kernel's layout) ----
   fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sATp, a.ATp, a.ATs, a.sATv);
   if (a.has_q) fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sQp, a.Qp, a.Qs, a.sQv);
   fill_sell_space(g, a.csp.nslices, a.csp.perm, a.sAp, a.Ap, a.As, a.sAv);
+  if (a.k > 0) fill_sell_space(g, a.rsp.nslices, a.rsp.perm, a.sRp, a.Rp, a.Rs, a.sRv);
   if (!group_sync<BS>(g)) return;
 
   // ---- 3. ||A||_2 by Lanczos on A^T A (FP64 vectors, the scaled values) ----

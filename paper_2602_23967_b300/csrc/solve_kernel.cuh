@@ -165,9 +165,46 @@ struct StepScalars {
   CT itau, isig, sig, wk, ak, th, th1;
 };
 
+// ---- structured objective Q = P + R^T R (Sec. 2.2): out = R v over the k rows
+// of R, the k-vector that the Q products of the next phase gather from ----
+template <int BS, Ld LM, class MatT, class VecT, class G>
+__device__ __forceinline__ void r_rows(const Inst<MatT, VecT>& I, int prank, G gat, VecT* __restrict__ out,
+                                       const RowCtx& rc) {
+  space_rows<BS, LM, VecT>(I.rsp, prank, src(I.Rsl, I.R, gat), nosrc<MatT>(), rc,
+                           [&](int l, const VecT* sums) { out[l] = sums[0]; });
+}
+// R x (Phase I and BB steps: Q x, x the given vector)
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ PDHCG_PHASE_ATTR void r_phase_x(const Inst<MatT, VecT>& I, int prank, const VecT* __restrict__ x,
+                                           const RowCtx& rc) {
+  r_rows<BS, LM>(I, prank, [&](int j) { return x[j]; }, I.rt1, rc);
+}
+// R p with p = r + beta p_old formed on the fly as in CG Phase A
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ PDHCG_PHASE_ATTR void r_phase_p(const Inst<MatT, VecT>& I, int prank, bool first, VecT be,
+                                           const VecT* __restrict__ pold, const RowCtx& rc) {
+  const VecT* __restrict__ rv = I.r;
+  r_rows<BS, LM>(I, prank, [&](int j) { return first ? rv[j] : VecT(fma(be, pold[j], rv[j])); }, I.rt1, rc);
+}
+// R x+ and R (x+ - x) in FP64 for the checks
+template <int BS, Ld LM, class MatT, class VecT>
+__device__ PDHCG_PHASE_ATTR void r_phase_check(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
+  const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
+  const VecT* __restrict__ xT = I.xT;
+  VecT* __restrict__ o1 = I.rt1;
+  VecT* __restrict__ o2 = I.rt2;
+  space_rows<BS, LM, double>(
+      I.rsp, prank,
+      src2(I.Rsl, I.R, [&](int j) { return double(xT[j]); }, [&](int j) { return double(xT[j]) - double(x[j]); }),
+      nosrc<MatT>(), rc, [&](int l, const double* sums) {
+        o1[l] = VecT(sums[0]);
+        o2[l] = VecT(sums[1]);
+      });
+}
+
 // ---- Phase I: g = A^T y, b = x/tau - c - g, inner-solver start (Eq. primal_update) ----
 // returns {inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2}
-template <int BS, Ld LM, class MatT, class VecT>
+template <int BS, Ld LM, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
                                       StepScalars<VecT> sc, const RowCtx& rc) {
   using CT = VecT;
@@ -186,10 +223,13 @@ __device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, 
   VecT* __restrict__ grad = I.grad;
   VecT* __restrict__ bvv = I.bv;
   const CT itau = sc.itau, wkc = sc.wk, akc = sc.ak, th = sc.th, th1 = sc.th1;
+  const int nv = I.n;                    // Q columns >= n address R x (structured Q)
+  const VecT* __restrict__ rt = I.rt1;
   DotAcc<CT> a0, a1, a2, a3;
   space_rows<BS, LM, Acc>(
       I.vsp, prank, src(I.ATs, I.AT, [&](int i) { return y[i]; }),
-      src(I.Qs, I.Q, [&](int k) { return x[k]; }, method != PDHCG_INNER_DIAG && I.has_q != 0), rc,
+      src(I.Qs, I.Q, [&](int k) { return kR && k >= nv ? rt[k - nv] : x[k]; }, method != PDHCG_INNER_DIAG && I.has_q != 0),
+      rc,
       [&](int j, const Acc* sums) {
         const CT xj = x[j];
         const CT bj = xj * itau - c[j] - CT(sums[0]);
@@ -224,7 +264,7 @@ __device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, 
 
 // ---- CG Phase A: p = r + beta p_old (gathered on the fly, bit-identical to the
 // owner's write), q = H p; returns p^T q ----
-template <int BS, Ld LM, class MatT, class VecT>
+template <int BS, Ld LM, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR double cg_phase_a(const Inst<MatT, VecT>& I, int prank, bool first, VecT be,
                                           const VecT* __restrict__ pold, VecT* __restrict__ pnew, VecT itau,
                                           const RowCtx& rc) {
@@ -232,10 +272,14 @@ __device__ PDHCG_PHASE_ATTR double cg_phase_a(const Inst<MatT, VecT>& I, int pra
   using Acc = VecT;
   const VecT* __restrict__ rv = I.r;
   VecT* __restrict__ qv = I.q;
+  const int nv = I.n;
+  const VecT* __restrict__ rt = I.rt1;
   DotAcc<CT> apq;
   space_rows<BS, LM, Acc>(
       I.vsp, prank,
-      src(I.Qs, I.Q, [&](int k) { return first ? rv[k] : CT(fma(be, pold[k], rv[k])); }, I.has_q != 0),
+      src(I.Qs, I.Q,
+          [&](int k) { return kR && k >= nv ? rt[k - nv] : (first ? rv[k] : CT(fma(be, pold[k], rv[k]))); },
+          I.has_q != 0),
       nosrc<MatT>(), rc, [&](int i, const Acc* sums) {
         const CT pi = first ? rv[i] : CT(fma(be, pold[i], rv[i]));
         pnew[i] = pi;
@@ -291,7 +335,7 @@ __device__ PDHCG_PHASE_ATTR void bb_phase_b(const Inst<MatT, VecT>& I, int lo, i
 
 // ---- BB Phase A': gradient, BB quantities and natural residual at xc ----
 // returns {s^T s, s^T (g - g_prev), ||x - proj(x - g)||^2}
-template <int BS, Ld LM, class MatT, class VecT>
+template <int BS, Ld LM, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int prank, const VecT* __restrict__ xc,
                                           const VecT* __restrict__ xo, const VecT* __restrict__ gc,
                                           VecT* __restrict__ gn, VecT itau, const RowCtx& rc) {
@@ -301,7 +345,10 @@ __device__ PDHCG_PHASE_ATTR Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int pra
   const VecT* __restrict__ lv = I.lv;
   const VecT* __restrict__ uv = I.uv;
   DotAcc<CT> ass, asy, anr;
-  space_rows<BS, LM, Acc>(I.vsp, prank, src(I.Qs, I.Q, [&](int k) { return xc[k]; }, I.has_q != 0),
+  const int nv = I.n;
+  const VecT* __restrict__ rt = I.rt1;
+  space_rows<BS, LM, Acc>(I.vsp, prank,
+                          src(I.Qs, I.Q, [&](int k) { return kR && k >= nv ? rt[k - nv] : xc[k]; }, I.has_q != 0),
                           nosrc<MatT>(), rc, [&](int i, const Acc* sums) {
                             const CT xi = xc[i];
                             const CT gi = (CT(sums[0]) + xi * itau) - bvv[i];
@@ -361,7 +408,7 @@ __device__ PDHCG_PHASE_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, 
 
 // ---- check phase: KKT residual pieces on the original data (Sec. 4.2) and the
 // infeasibility tests' pieces (Sec. 5.1, 5.2), with Delta = T(z) - z ----
-template <int BS, Ld LM, class MatT, class VecT>
+template <int BS, Ld LM, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
   const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
@@ -376,6 +423,7 @@ __device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int p
   const VecT* __restrict__ c_s = I.c;
   const int8_t* __restrict__ ctype = I.ctype;
   const int8_t* __restrict__ vtype = I.vtype;
+  const int nv = I.n;
   Red<18> cv;
 #pragma unroll
   for (int q = 0; q < 18; ++q) cv.v[q] = 0.0;
@@ -398,7 +446,8 @@ __device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int p
       I.vsp, prank,
       src2(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
            [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
-      src2(I.Qs, I.Q, [&](int k) { return double(xT[k]); }, [&](int k) { return double(xT[k]) - double(x[k]); },
+      src2(I.Qs, I.Q, [&](int k) { return kR && k >= nv ? double(I.rt1[k - nv]) : double(xT[k]); },
+           [&](int k) { return kR && k >= nv ? double(I.rt2[k - nv]) : double(xT[k]) - double(x[k]); },
            I.has_q != 0),
       rc, [&](int j, const double* sums) {
         const double aty = sums[0], atyt = sums[1], qx = sums[2], qdd = sums[3];
@@ -509,7 +558,9 @@ __device__ PDHCG_PHASE_ATTR void init_point(const Inst<MatT, VecT>& I, int vlo, 
 
 // The control loop: scalar state, decisions and group reductions; the row and
 // elementwise work is in the phase functions above.
-template <int BS, Ld LM, class MatT, class VecT>
+// kR: the structured-Q variant (instances with a factor R); the plain variant
+// compiles without the R phases and the split gathers.
+template <int BS, Ld LM, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
                                             const RowCtx& rc) {
   using CT = VecT;
@@ -568,10 +619,14 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       sc.th1 = shfl_idx(qc, 6);
     }
 
-    // Phase I
+    // Phase I (structured Q: R x first)
+    if (kR && I.k > 0 && method != PDHCG_INNER_DIAG) {
+      r_phase_x<BS, LM>(I, prank, cur ? I.xb1 : I.xb0, rc);
+      if (!group_sync<BS>(g)) { ok = false; break; }
+    }
     double red1[4];
     {
-      const Red<4> r = phase1<BS, LM>(I, prank, method, cur, sc, rc);
+      const Red<4> r = phase1<BS, LM, kR>(I, prank, method, cur, sc, rc);
 #pragma unroll
       for (int q = 0; q < 4; ++q) red1[q] = r.v[q];
     }
@@ -603,7 +658,11 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
         if (sqrt(rr) <= eps || j >= P.max_inner_iter) break;
         const VecT* pold = pc ? I.p1 : I.p0;
         VecT* pnew = pc ? I.p0 : I.p1;
-        double pq[1] = {cg_phase_a<BS, LM>(I, prank, j == 0, CT(beta), pold, pnew, sc.itau, rc)};
+        if (kR && I.k > 0) {
+          r_phase_p<BS, LM>(I, prank, j == 0, CT(beta), pold, rc);
+          if (!group_sync<BS>(g)) { ok = false; break; }
+        }
+        double pq[1] = {cg_phase_a<BS, LM, kR>(I, prank, j == 0, CT(beta), pold, pnew, sc.itau, rc)};
         PDHCG_CLK(1);
         if (!group_reduce<BS, 1, kWT>(g, pq, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
@@ -642,10 +701,14 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
         { VecT* t = xo; xo = xc; xc = t; }
         PDHCG_CLK(2);
         if (!group_sync<BS>(g)) { ok = false; break; }
+        if (kR && I.k > 0) {
+          r_phase_x<BS, LM>(I, prank, xc, rc);
+          if (!group_sync<BS>(g)) { ok = false; break; }
+        }
         PDHCG_CLK(5);
         double v3[3];
         {
-          const Red<3> r = bb_phase_a<BS, LM>(I, prank, xc, xo, gc, go, sc.itau, rc);
+          const Red<3> r = bb_phase_a<BS, LM, kR>(I, prank, xc, xo, gc, go, sc.itau, rc);
           v3[0] = r.v[0];
           v3[1] = r.v[1];
           v3[2] = r.v[2];
@@ -690,8 +753,12 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     const bool check = ((S.K + 1) % P.k_eval == 0) || (S.K + 1 >= P.max_iter);
     if (check) {
       double cv[18];
+      if (kR && I.k > 0) {
+        r_phase_check<BS, LM>(I, prank, cur, rc);
+        if (!group_sync<BS>(g)) { ok = false; break; }
+      }
       {
-        const Red<18> r = check_phase<BS, LM>(I, prank, cur, rc);
+        const Red<18> r = check_phase<BS, LM, kR>(I, prank, cur, rc);
 #pragma unroll
         for (int q = 0; q < 18; ++q) cv[q] = r.v[q];
       }
@@ -804,7 +871,7 @@ __device__ __forceinline__ void copy_inst(Inst<MatT, VecT>& dst, const Inst<MatT
   __syncthreads();
 }
 
-template <int BS, class MatT, class VecT>
+template <int BS, bool kR, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig, Inst<MatT, VecT>& I,
                                            const LaunchPlan& plan, const RowCtx& rc, char* base,
                                            int method) {
@@ -877,7 +944,7 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
     I.yb0 = yb0; I.yb1 = yb1; I.yT = yT; I.ya = ya; I.lc = lc; I.uc = uc; I.ctype = ct;
   }
   __syncthreads();
-  solve_instance<BS, Ld::Cached>(g, I, plan, rc);
+  solve_instance<BS, Ld::Cached, kR>(g, I, plan, rc);
   __syncthreads();
   const int cur2 = Ig.st->cur;
   for (int i = threadIdx.x; i < n; i += BS) {
@@ -900,7 +967,7 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
 #ifndef PDHCG_POOL_MIN_BLOCKS
 #define PDHCG_POOL_MIN_BLOCKS PDHCG_MIN_BLOCKS
 #endif
-template <int BS, class MatT, class VecT>
+template <int BS, class MatT, class VecT, bool kR>
 __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_POOL_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
@@ -935,7 +1002,7 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     g.bar32 = reinterpret_cast<unsigned*>(plan.g_bar) + size_t(gi) * kBarWords;
     g.part = plan.g_part + plan.g_part_off[gi];
     copy_inst<BS>(sh_inst, insts[plan.g_inst[gi]]);
-    solve_instance<BS, Ld::Stream>(g, sh_inst, plan, rc);
+    solve_instance<BS, Ld::Stream, kR>(g, sh_inst, plan, rc);
     return;
   }
   g.nblk = 1;
@@ -954,9 +1021,9 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
     copy_inst<BS>(sh_inst, Ig);
     if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
-      solve_in_smem<BS>(g, Ig, sh_inst, plan, rc, dsm + vec_smem_offset<BS>(), method);
+      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm + vec_smem_offset<BS>(), method);
     } else {
-      solve_instance<BS, Ld::Cached>(g, sh_inst, plan, rc);
+      solve_instance<BS, Ld::Cached, kR>(g, sh_inst, plan, rc);
     }
     __syncthreads();
   }

@@ -100,6 +100,8 @@ def lib():
                                    C.POINTER(Params), _P, C.POINTER(_P)]
         L.pdhcg_create_batch.argtypes = [C.c_int, C.POINTER(ProblemData), C.POINTER(Params), _P,
                                          C.POINTER(_P)]
+        L.pdhcg_create_qr.argtypes = [C.POINTER(Csr), C.POINTER(Csr), C.POINTER(Csr), _D, _D, _D, _D, _D,
+                                      C.POINTER(Params), _P, C.POINTER(_P)]
         L.pdhcg_solve.argtypes = [_P, _D, _D, C.POINTER(Result), _D, _D]
         L.pdhcg_solve_dev.argtypes = [_P, _P, _P, C.POINTER(Result), _P, _P]
         L.pdhcg_solve_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(Result), C.POINTER(_D),
@@ -191,10 +193,19 @@ class Problem:
             return
         h = _qp_args(qp)
         handle = _P()
-        rc = L.pdhcg_create(C.byref(h["Q"].s) if "Q" in h else None, C.byref(h["A"].s),
-                            _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]),
-                            C.byref(self.params), _P(stream) if stream else None, C.byref(handle))
-        check(rc, "pdhcg_create")
+        R = getattr(qp, "R", None)
+        if R is not None:
+            # structured objective Q + R^T R (pdhcg_create_qr)
+            Rh = _CsrHold(R, int(R.shape[0]), self.n)
+            rc = L.pdhcg_create_qr(C.byref(h["Q"].s) if "Q" in h else None, C.byref(Rh.s), C.byref(h["A"].s),
+                                   _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]),
+                                   C.byref(self.params), _P(stream) if stream else None, C.byref(handle))
+            check(rc, "pdhcg_create_qr")
+        else:
+            rc = L.pdhcg_create(C.byref(h["Q"].s) if "Q" in h else None, C.byref(h["A"].s),
+                                _dp(h["c"]), _dp(h["lc"]), _dp(h["uc"]), _dp(h["lv"]), _dp(h["uv"]),
+                                C.byref(self.params), _P(stream) if stream else None, C.byref(handle))
+            check(rc, "pdhcg_create")
         self.handle = handle
 
     def solve(self, x0=None, y0=None):
@@ -251,6 +262,8 @@ class Problem:
 
 def create_batch(qps, params: Params | None = None, stream=None):
     """Create many Problems at once (pdhcg_create_batch: shared allocation, one setup launch)."""
+    if any(getattr(q, "R", None) is not None for q in qps):
+        raise ValueError("create_batch takes plain Q; create structured (Q + R^T R) problems one by one")
     params = params if params is not None else default_params()
     holds = [_qp_args(q) for q in qps]
     # the pdhcg_problem_data array: seven pointers per problem, filled as integers

@@ -289,3 +289,43 @@ def test_cg_lifted_solves_the_original_qp(precision, seed):
     assert max(rp, rd, rg) <= 1e-5, (rp, rd, rg)
     _, _, ro = oracle.solve(qp, oracle.default_params(eps_tol=1e-6))
     assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
+
+
+@pytest.mark.parametrize("group_blocks", [1, 7])
+@pytest.mark.parametrize("N", [1, 17, 100])
+def test_structured_q_iterates_match_oracle(N, group_blocks):
+    # Q = P + R^T R applied as P v + R^T (R v) on both sides (Sec. 2.2)
+    qp = W.random_qp(seed=4, factored=True)
+    x, y, r, eta = gpu_solve(qp, max_iter=N, group_blocks=group_blocks)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
+    assert r["iterations"] == ro["iterations"] == N
+    assert r["inner_iterations"] == ro["inner_iterations"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
+
+
+@pytest.mark.parametrize("inner", ["auto", "cg_lifted"])
+@pytest.mark.parametrize("precision", ["fp64", "dfloat"])
+def test_structured_q_solves_to_the_formed_optimum(precision, inner):
+    qf = W.random_qp(seed=1, factored=True)
+    formed = W.QP(qf.n, qf.m, W._csr(qf.Q + qf.R.T @ qf.R), qf.A, qf.c, qf.lc, qf.uc, qf.lv, qf.uv)
+    x, y, r, _ = gpu_solve(qf, eps_tol=1e-6, precision=precision, inner=inner, max_iter=500000)
+    assert r["status_name"] == "OPTIMAL", r
+    rp, rd, rg, pobj, _ = kkt_of(formed, x, y)
+    assert max(rp, rd, rg) <= (3e-6 if inner == "auto" else 1e-5), (rp, rd, rg)
+    _, _, ro = oracle.solve(formed, oracle.default_params(eps_tol=1e-6))
+    assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
+
+
+def test_structured_q_large_factor_multi_cta():
+    # a large factor (k = 2000 rows of ~50 entries) on several CTAs: iterates vs oracle
+    import scipy.sparse as sp
+    rng = np.random.default_rng(8)
+    base = W.large_sparse_qp(n=20000, m=10000, seed=2)
+    R = W._csr(sp.random(2000, base.n, density=50 / base.n, random_state=rng, format="csr"))
+    qp = W.QP(base.n, base.m, base.Q, base.A, base.c, base.lc, base.uc, base.lv, base.uv, R=R)
+    x, y, r, eta = gpu_solve(qp, max_iter=64, group_blocks=0)
+    xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=64, eta_override=eta))
+    assert r["inner_iterations"] == ro["inner_iterations"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
+    assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo)))
