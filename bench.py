@@ -189,8 +189,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 374_601_728, "instances": 512,
-                   "sources_sha256": "209d5c7acafc18a94ed83ddc3a6aa0afda669e707fe2520c407ce431dee17e88",
+TRAFFIC_CAPTURE = {"bytes": 417_948_160, "instances": 512,
+                   "sources_sha256": "19928cd0ae9dd640047158c94e3d1237c9d8ed39a13fdd655d1ccfbbff81c330",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")

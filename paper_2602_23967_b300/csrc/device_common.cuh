@@ -53,6 +53,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for).
+// src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // Bounded wait for phase `parity` of `bar`; false after timeout_ns.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns);
 
@@ -415,6 +420,11 @@ __device__ __forceinline__ int64_t ldm64(const int64_t* p) {
   else return __ldg(reinterpret_cast<const long long*>(p));
 }
 
+// Stage SELL slices of streamed matrices into shared memory with TMA bulk
+// copies (1) instead of loading them directly (0).
+#ifndef PDHCG_TMA_STAGING
+#define PDHCG_TMA_STAGING 0
+#endif
 // Columns per TMA chunk of a slice (chunk = 32 rows x kChunkCols columns).
 constexpr int kChunkCols = 8;
 constexpr int kChunkElems = kChunkCols * 32;
@@ -488,89 +498,6 @@ __device__ __forceinline__ RowSrc<MatT, 0, NoGather, NoGather> nosrc() {
   return RowSrc<MatT, 0, NoGather, NoGather>{Sell<MatT>{}, Csr<MatT>{}, NoGather{}, NoGather{}, false};
 }
 
-// First CH column/value pairs of slot `lane` of slice s of source X, loaded
-// ahead of use (software pipelining across the slices of a warp).
-template <class MatT, int CH>
-struct SlicePre {
-  int64_t b;
-  int W;
-  int c[CH];
-  MatT v[CH];
-};
-
-template <Ld LM, int CH, class X, class MatT>
-__device__ __forceinline__ void slice_prefetch(const X& x, int s, int lane, SlicePre<MatT, CH>& p) {
-  p.W = 0;
-  if constexpr (X::NG > 0) {
-    if (!x.on) return;
-    p.b = ldm64<LM>(x.S.ptr + s);
-    p.W = int((ldm64<LM>(x.S.ptr + s + 1) - p.b) >> 5);
-    const int* cp = x.S.col + p.b + lane;
-    const MatT* vp = x.S.val + p.b + lane;
-#pragma unroll
-    for (int u = 0; u < CH; ++u)
-      if (u < p.W) {
-        p.c[u] = ldm<LM>(cp + 32 * u);
-        p.v[u] = ldm<LM>(vp + 32 * u);
-      }
-  }
-}
-
-// Finish slot `lane` of a prefetched slice: gathers and multiply-adds of the
-// prefetched chunk, then the rest of the row in chunks, all in column order.
-template <Ld LM, int CH, class Acc, class X, class MatT>
-__device__ __forceinline__ void slice_finish(const X& x, int lane, const SlicePre<MatT, CH>& p, Acc* sums) {
-  if constexpr (X::NG > 0) {
-    if (p.W == 0) return;
-    {
-      Acc g1v[CH];
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (u < p.W) g1v[u] = Acc(x.g1(p.c[u]));
-      if constexpr (X::NG == 2) {
-        Acc g2v[CH];
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-          if (u < p.W) g2v[u] = Acc(x.g2(p.c[u]));
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-          if (u < p.W) madd(sums[1], p.v[u], g2v[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (u < p.W) madd(sums[0], p.v[u], g1v[u]);
-    }
-    const int* cp = x.S.col + p.b + lane;
-    const MatT* vp = x.S.val + p.b + lane;
-    for (int j0 = CH; j0 < p.W; j0 += CH) {
-      int c[CH];
-      MatT v[CH];
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (j0 + u < p.W) {
-          c[u] = ldm<LM>(cp + 32 * (j0 + u));
-          v[u] = ldm<LM>(vp + 32 * (j0 + u));
-        }
-      Acc g1v[CH];
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (j0 + u < p.W) g1v[u] = Acc(x.g1(c[u]));
-      if constexpr (X::NG == 2) {
-        Acc g2v[CH];
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-          if (j0 + u < p.W) g2v[u] = Acc(x.g2(c[u]));
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-          if (j0 + u < p.W) madd(sums[1], v[u], g2v[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (j0 + u < p.W) madd(sums[0], v[u], g1v[u]);
-    }
-  }
-}
-
 // Columns of a slice whose loads are issued together (memory-level parallelism).
 #ifndef PDHCG_SLICE_UNROLL
 #define PDHCG_SLICE_UNROLL 4
@@ -605,6 +532,38 @@ template <class X>
 struct SrcMat {
   using type = typename X::mat_type;
 };
+
+// Prefetch distance, in slices of the same warp, of the bulk L2 prefetch of
+// streamed SELL slices (0 = off).
+#ifndef PDHCG_L2_PREFETCH
+#define PDHCG_L2_PREFETCH 1
+#endif
+// Element span [b, e) of slice s of source X (empty when s >= s_end or X is off).
+template <Ld LM, class X>
+__device__ __forceinline__ void slice_span(const X& x, int s, int s_end, int64_t& b, int64_t& e) {
+  b = 0;
+  e = 0;
+  if constexpr (X::NG > 0)
+    if (x.on && s < s_end) {
+      b = ldm64<LM>(x.S.ptr + s);
+      e = ldm64<LM>(x.S.ptr + s + 1);
+    }
+}
+// Bulk L2 prefetch of the column indices and values of span [b, e).  Slices
+// start on multiples of 32 elements of 16-byte-aligned arrays, so both copies
+// are 16-byte aligned with sizes that are multiples of 16 (checked anyway).
+template <class X>
+__device__ __forceinline__ void slice_prefetch_l2(const X& x, int64_t b, int64_t e) {
+  if constexpr (X::NG > 0) {
+    using MatT = typename SrcMat<X>::type;
+    if (e <= b) return;
+    const int* c = x.S.col + b;
+    const MatT* v = x.S.val + b;
+    const unsigned cb = unsigned(e - b) * 4u, vb = unsigned(e - b) * unsigned(sizeof(MatT));
+    if (((reinterpret_cast<uintptr_t>(c) | cb) & 15u) == 0) bulk_prefetch_l2(c, cb);
+    if (((reinterpret_cast<uintptr_t>(v) | vb) & 15u) == 0) bulk_prefetch_l2(v, vb);
+  }
+}
 
 // Lane-strided partial of CSR row `row` of source X, start offset `first`,
 // stride `step`; 8 elements per lane in flight.
@@ -667,182 +626,209 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
     h0 = sp.huge_part[part_rank];
     h1 = sp.huge_part[part_rank + 1];
   }
-#ifndef PDHCG_TMA_STAGING
-#define PDHCG_TMA_STAGING 0
-#endif
-#if PDHCG_TMA_STAGING
-  // regular rows: the warp streams its slices in chunks of kChunkCols columns.
-  // Lane 0 bulk-copies (TMA) the next chunk's column indices and values of both
-  // sources into the warp's other shared-memory stage while the lanes gather and
-  // multiply-add the current chunk; the row epilogue runs after a slice's last chunk.
-  if (sp.nslices > 0 && s0 + warp < s1) {
-    using MA = typename SrcMat<SA>::type;
-    using MB = typename SrcMat<SB>::type;
-    constexpr int CC = kChunkCols;
-    constexpr int CE = CC * 32;
-    WarpStages& ws = stages[warp];
-    const bool onA = NA > 0 && A.on, onB = NB > 0 && B.on;
-    // slice geometry
-    auto geom = [&](int s, int64_t& ba, int& wa, int64_t& bb, int& wb) {
-      ba = 0; wa = 0; bb = 0; wb = 0;
-      if constexpr (NA > 0) if (onA) { ba = ldm64<LM>(A.S.ptr + s); wa = int((ldm64<LM>(A.S.ptr + s + 1) - ba) >> 5); }
-      if constexpr (NB > 0) if (onB) { bb = ldm64<LM>(B.S.ptr + s); wb = int((ldm64<LM>(B.S.ptr + s + 1) - bb) >> 5); }
-    };
-    // issue chunk ch of slice (ba, wa, bb, wb) into stage st
-    auto issue = [&](int st, int ch, int64_t ba, int wa, int64_t bb, int wb) {
+  // TMA staging applies to streamed matrices (multi-CTA groups), whose launch
+  // provides the per-warp stages; other callers pass no stages.
+  constexpr bool kTma = PDHCG_TMA_STAGING && LM == Ld::Stream;
+  if (kTma && stages != nullptr) {
+    // regular rows: the warp streams its slices in chunks of kChunkCols columns.
+    // Lane 0 bulk-copies (TMA) the next chunk's column indices and values of both
+    // sources into the warp's other shared-memory stage while the lanes gather and
+    // multiply-add the current chunk; the row epilogue runs after a slice's last chunk.
+    if (sp.nslices > 0 && s0 + warp < s1) {
+      using MA = typename SrcMat<SA>::type;
+      using MB = typename SrcMat<SB>::type;
+      constexpr int CC = kChunkCols;
+      constexpr int CE = CC * 32;
+      WarpStages& ws = stages[warp];
+      const bool onA = NA > 0 && A.on, onB = NB > 0 && B.on;
+      // slice geometry
+      auto geom = [&](int s, int64_t& ba, int& wa, int64_t& bb, int& wb) {
+        ba = 0; wa = 0; bb = 0; wb = 0;
+        if constexpr (NA > 0) if (onA) { ba = ldm64<LM>(A.S.ptr + s); wa = int((ldm64<LM>(A.S.ptr + s + 1) - ba) >> 5); }
+        if constexpr (NB > 0) if (onB) { bb = ldm64<LM>(B.S.ptr + s); wb = int((ldm64<LM>(B.S.ptr + s + 1) - bb) >> 5); }
+      };
+      // issue chunk ch of slice (ba, wa, bb, wb) into stage st
+      auto issue = [&](int st, int ch, int64_t ba, int wa, int64_t bb, int wb) {
+        if (lane == 0) {
+          const int na = max(0, min(CC, wa - ch * CC)), nb = max(0, min(CC, wb - ch * CC));
+          const unsigned bytes = unsigned(na) * 32u * (4u + sizeof(MA)) + unsigned(nb) * 32u * (4u + sizeof(MB));
+          fence_proxy_async();
+          mbar_arrive_expect_tx(&ws.bar[st], bytes);
+          if constexpr (NA > 0)
+            if (na > 0) {
+              const int64_t off = ba + int64_t(ch) * CE;
+              bulk_g2s(ws.colA(st), A.S.col + off, unsigned(na) * 128u, &ws.bar[st]);
+              bulk_g2s(ws.valA(st), A.S.val + off, unsigned(na) * 32u * sizeof(MA), &ws.bar[st]);
+            }
+          if constexpr (NB > 0)
+            if (nb > 0) {
+              const int64_t off = bb + int64_t(ch) * CE;
+              bulk_g2s(ws.colB(st), B.S.col + off, unsigned(nb) * 128u, &ws.bar[st]);
+              bulk_g2s(ws.valB(st), B.S.val + off, unsigned(nb) * 32u * sizeof(MB), &ws.bar[st]);
+            }
+        }
+      };
+      // stage index and barrier parities live in registers (identical in all
+      // lanes) and are written back to shared memory once at the end
+      int st = ws.next;
+      unsigned par[2] = {ws.parity[0], ws.parity[1]};
+      __syncwarp();
+      int s = s0 + warp;
+      int64_t ba, bb;
+      int wa, wb;
+      geom(s, ba, wa, bb, wb);
+      int nch = (max(wa, wb) + CC - 1) / CC;
+      int ch = 0;
+      bool have = false;  // chunk (s, ch) already issued into stage st
+      int row = ldm<LM>(sp.perm + s * 32 + lane);
+      Acc sums[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+      int sn = s + NW;
+      int64_t nba = 0, nbb = 0;
+      int nwa = 0, nwb = 0;
+      if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
+      bool failed = false;
+      while (true) {
+        if (ch < nch) {
+          if (!have) issue(st, ch, ba, wa, bb, wb);
+          // prefetch the following chunk (this slice or the next one)
+          bool have2 = false;
+          if (ch + 1 < nch) {
+            issue(st ^ 1, ch + 1, ba, wa, bb, wb);
+            have2 = true;
+          } else if (sn < s1 && max(nwa, nwb) > 0) {
+            issue(st ^ 1, 0, nba, nwa, nbb, nwb);
+            have2 = true;
+          }
+          if (!mbar_wait(&ws.bar[st], par[st], tmo)) {
+            // give the prefetched copy (if any) a bounded chance to land before leaving
+            if (have2) mbar_wait(&ws.bar[st ^ 1], par[st ^ 1], tmo);
+            failed = true;
+            break;
+          }
+          par[st] ^= 1u;
+          if constexpr (NA > 0)
+            if (onA && ch * CC < wa) {
+              const int na = min(CC, wa - ch * CC);
+              const int* cs = ws.colA(st) + lane;
+              const MA* vs = reinterpret_cast<const MA*>(ws.valA(st)) + lane;
+              Acc g1v[CC];
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < na) g1v[u] = Acc(A.g1(cs[32 * u]));
+              if constexpr (NA == 2) {
+                Acc g2v[CC];
+#pragma unroll
+                for (int u = 0; u < CC; ++u)
+                  if (u < na) g2v[u] = Acc(A.g2(cs[32 * u]));
+#pragma unroll
+                for (int u = 0; u < CC; ++u)
+                  if (u < na) madd(sums[1], vs[32 * u], g2v[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < na) madd(sums[0], vs[32 * u], g1v[u]);
+            }
+          if constexpr (NB > 0)
+            if (onB && ch * CC < wb) {
+              const int nb = min(CC, wb - ch * CC);
+              const int* cs = ws.colB(st) + lane;
+              const MB* vs = reinterpret_cast<const MB*>(ws.valB(st)) + lane;
+              Acc g1v[CC];
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < nb) g1v[u] = Acc(B.g1(cs[32 * u]));
+              if constexpr (NB == 2) {
+                Acc g2v[CC];
+#pragma unroll
+                for (int u = 0; u < CC; ++u)
+                  if (u < nb) g2v[u] = Acc(B.g2(cs[32 * u]));
+#pragma unroll
+                for (int u = 0; u < CC; ++u)
+                  if (u < nb) madd(sums[NA + 1], vs[32 * u], g2v[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < CC; ++u)
+                if (u < nb) madd(sums[NA], vs[32 * u], g1v[u]);
+            }
+          __syncwarp();  // every lane is done with stage st before it is refilled
+          st ^= 1;
+          ++ch;
+          have = have2;
+          continue;
+        }
+        // slice done
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
+        if (row >= 0) epi(row, sums);
+        if (sn >= s1) break;
+        s = sn;
+        ba = nba;
+        wa = nwa;
+        bb = nbb;
+        wb = nwb;
+        nch = (max(wa, wb) + CC - 1) / CC;
+        ch = 0;
+        row = ldm<LM>(sp.perm + s * 32 + lane);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+        sn = s + NW;
+        if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
+      }
+      __syncwarp();
       if (lane == 0) {
-        const int na = max(0, min(CC, wa - ch * CC)), nb = max(0, min(CC, wb - ch * CC));
-        const unsigned bytes = unsigned(na) * 32u * (4u + sizeof(MA)) + unsigned(nb) * 32u * (4u + sizeof(MB));
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&ws.bar[st], bytes);
-        if constexpr (NA > 0)
-          if (na > 0) {
-            const int64_t off = ba + int64_t(ch) * CE;
-            bulk_g2s(ws.colA(st), A.S.col + off, unsigned(na) * 128u, &ws.bar[st]);
-            bulk_g2s(ws.valA(st), A.S.val + off, unsigned(na) * 32u * sizeof(MA), &ws.bar[st]);
-          }
-        if constexpr (NB > 0)
-          if (nb > 0) {
-            const int64_t off = bb + int64_t(ch) * CE;
-            bulk_g2s(ws.colB(st), B.S.col + off, unsigned(nb) * 128u, &ws.bar[st]);
-            bulk_g2s(ws.valB(st), B.S.val + off, unsigned(nb) * 32u * sizeof(MB), &ws.bar[st]);
-          }
-      }
-    };
-    // stage index and barrier parities live in registers (identical in all
-    // lanes) and are written back to shared memory once at the end
-    int st = ws.next;
-    unsigned par[2] = {ws.parity[0], ws.parity[1]};
-    __syncwarp();
-    int s = s0 + warp;
-    int64_t ba, bb;
-    int wa, wb;
-    geom(s, ba, wa, bb, wb);
-    int nch = (max(wa, wb) + CC - 1) / CC;
-    int ch = 0;
-    bool have = false;  // chunk (s, ch) already issued into stage st
-    int row = ldm<LM>(sp.perm + s * 32 + lane);
-    Acc sums[NS];
-#pragma unroll
-    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-    int sn = s + NW;
-    int64_t nba = 0, nbb = 0;
-    int nwa = 0, nwb = 0;
-    if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
-    bool failed = false;
-    while (true) {
-      if (ch < nch) {
-        if (!have) issue(st, ch, ba, wa, bb, wb);
-        // prefetch the following chunk (this slice or the next one)
-        bool have2 = false;
-        if (ch + 1 < nch) {
-          issue(st ^ 1, ch + 1, ba, wa, bb, wb);
-          have2 = true;
-        } else if (sn < s1 && max(nwa, nwb) > 0) {
-          issue(st ^ 1, 0, nba, nwa, nbb, nwb);
-          have2 = true;
+        ws.next = st;
+        ws.parity[0] = par[0];
+        ws.parity[1] = par[1];
+        if (failed) {
+          atomicExch(err, 1);
+          *rc.fail_flag = 1;
         }
-        if (!mbar_wait(&ws.bar[st], par[st], tmo)) {
-          // give the prefetched copy (if any) a bounded chance to land before leaving
-          if (have2) mbar_wait(&ws.bar[st ^ 1], par[st ^ 1], tmo);
-          failed = true;
-          break;
-        }
-        par[st] ^= 1u;
-        if constexpr (NA > 0)
-          if (onA && ch * CC < wa) {
-            const int na = min(CC, wa - ch * CC);
-            const int* cs = ws.colA(st) + lane;
-            const MA* vs = reinterpret_cast<const MA*>(ws.valA(st)) + lane;
-            Acc g1v[CC];
-#pragma unroll
-            for (int u = 0; u < CC; ++u)
-              if (u < na) g1v[u] = Acc(A.g1(cs[32 * u]));
-            if constexpr (NA == 2) {
-              Acc g2v[CC];
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < na) g2v[u] = Acc(A.g2(cs[32 * u]));
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < na) madd(sums[1], vs[32 * u], g2v[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < CC; ++u)
-              if (u < na) madd(sums[0], vs[32 * u], g1v[u]);
-          }
-        if constexpr (NB > 0)
-          if (onB && ch * CC < wb) {
-            const int nb = min(CC, wb - ch * CC);
-            const int* cs = ws.colB(st) + lane;
-            const MB* vs = reinterpret_cast<const MB*>(ws.valB(st)) + lane;
-            Acc g1v[CC];
-#pragma unroll
-            for (int u = 0; u < CC; ++u)
-              if (u < nb) g1v[u] = Acc(B.g1(cs[32 * u]));
-            if constexpr (NB == 2) {
-              Acc g2v[CC];
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < nb) g2v[u] = Acc(B.g2(cs[32 * u]));
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < nb) madd(sums[NA + 1], vs[32 * u], g2v[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < CC; ++u)
-              if (u < nb) madd(sums[NA], vs[32 * u], g1v[u]);
-          }
-        __syncwarp();  // every lane is done with stage st before it is refilled
-        st ^= 1;
-        ++ch;
-        have = have2;
-        continue;
       }
-      // slice done
+      __syncwarp();
+    }
+  } else {
+    // regular rows: one slice per warp at a time, lane l summing the row in slot l.
+    // Streamed matrices: lane 0 also prefetches into L2 the slice this warp takes
+    // PDHCG_L2_PREFETCH turns later (issued after the current slice, whose work
+    // covers the latency of the two pointer loads).
+    constexpr bool kPf = LM == Ld::Stream && PDHCG_L2_PREFETCH > 0;
+    if constexpr (kPf) {
+      if (lane == 0)
+        for (int d = 0; d < PDHCG_L2_PREFETCH; ++d) {
+          int64_t b, e;
+          slice_span<LM>(A, s0 + warp + d * NW, s1, b, e);
+          slice_prefetch_l2(A, b, e);
+          slice_span<LM>(B, s0 + warp + d * NW, s1, b, e);
+          slice_prefetch_l2(B, b, e);
+        }
+    }
+    for (int s = s0 + warp; s < s1; s += NW) {
+      const int row = ldm<LM>(sp.perm + s * 32 + lane);
+      int64_t pab = 0, pae = 0, pbb = 0, pbe = 0;
+      if constexpr (kPf) {
+        if (lane == 0) {
+          slice_span<LM>(A, s + PDHCG_L2_PREFETCH * NW, s1, pab, pae);
+          slice_span<LM>(B, s + PDHCG_L2_PREFETCH * NW, s1, pbb, pbe);
+        }
+      }
+      Acc sums[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+      slice_dot<LM, Acc>(A, s, lane, sums);
+      slice_dot<LM, Acc>(B, s, lane, sums + NA);
+      if constexpr (kPf) {
+        if (lane == 0) {
+          slice_prefetch_l2(A, pab, pae);
+          slice_prefetch_l2(B, pbb, pbe);
+        }
+      }
 #pragma unroll
       for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
       if (row >= 0) epi(row, sums);
-      if (sn >= s1) break;
-      s = sn;
-      ba = nba;
-      wa = nwa;
-      bb = nbb;
-      wb = nwb;
-      nch = (max(wa, wb) + CC - 1) / CC;
-      ch = 0;
-      row = ldm<LM>(sp.perm + s * 32 + lane);
-#pragma unroll
-      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-      sn = s + NW;
-      if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
     }
-    __syncwarp();
-    if (lane == 0) {
-      ws.next = st;
-      ws.parity[0] = par[0];
-      ws.parity[1] = par[1];
-      if (failed) {
-        atomicExch(err, 1);
-        *rc.fail_flag = 1;
-      }
-    }
-    __syncwarp();
   }
-#else
-  // regular rows: one slice per warp at a time, lane l summing the row in slot l
-  for (int s = s0 + warp; s < s1; s += NW) {
-    const int row = ldm<LM>(sp.perm + s * 32 + lane);
-    Acc sums[NS];
-#pragma unroll
-    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-    slice_dot<LM, Acc>(A, s, lane, sums);
-    slice_dot<LM, Acc>(B, s, lane, sums + NA);
-#pragma unroll
-    for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
-    if (row >= 0) epi(row, sums);
-  }
-#endif
   // long rows: one warp per row
   for (int li = l0 + warp; li < l1; li += NW) {
     const int row = __ldg(sp.longs + li);

@@ -8,6 +8,8 @@
 
 namespace pdhcg {
 
+// Dynamic shared memory of a group launch (TMA stages); pool launches use theirs
+// for instance vectors instead.
 inline size_t solve_dyn_smem() { return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (kGroupBS / 32) : 0; }
 
 template <class MatT, class VecT>
@@ -32,9 +34,9 @@ int pool_blocks_per_sm(size_t smem_vec_bytes) {
   int nb = 0, nr = 0;
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT, false>, kPoolBS,
-                                                    solve_dyn_smem() + smem_vec_bytes) != cudaSuccess ||
+                                                    smem_vec_bytes) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kPoolBS, MatT, VecT, true>, kPoolBS,
-                                                    solve_dyn_smem() + smem_vec_bytes) != cudaSuccess)
+                                                    smem_vec_bytes) != cudaSuccess)
     return 0;
   nb = std::min(nb, nr);
   if (PDHCG_POOL_MAX_PER_SM > 0) nb = std::min(nb, int(PDHCG_POOL_MAX_PER_SM));
@@ -85,7 +87,7 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   const size_t extra = plan.group_blocks == 0 ? size_t(plan.smem_vec_bytes) : 0;
   cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
   if (e != cudaSuccess) return e;
-  const size_t smem = solve_dyn_smem() + extra;
+  const size_t smem = plan.group_blocks > 0 ? solve_dyn_smem() : extra;
   const bool r = plan.structured != 0;
   if (plan.group_blocks == 0) {
     if (r)

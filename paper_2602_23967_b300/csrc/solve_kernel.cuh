@@ -850,11 +850,6 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   if (g.rank == 0 && threadIdx.x == 0) *I.st = S;
 }
 
-// Offset of the vector area in dynamic shared memory (after the TMA stages, if any).
-template <int BS>
-__host__ __device__ constexpr size_t vec_smem_offset() {
-  return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (BS / 32) : 0;
-}
 
 // Solve one instance with every iteration vector held in shared memory.  The
 // iterate state (current x, y and the Halpern anchors) is copied in when the
@@ -984,12 +979,14 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
   g.failed = false;
   g.epoch = 0;
   if (threadIdx.x == 0) sm_flag = 0;
-  WarpStages* stages = reinterpret_cast<WarpStages*>(dsm);
-#if PDHCG_TMA_STAGING
-  init_stages<BS>(stages);
-#else
-  __syncthreads();
-#endif
+  // dynamic shared memory: the TMA stages of a group launch, else the vectors
+  // of pool solves
+  WarpStages* stages = (PDHCG_TMA_STAGING && plan.group_blocks > 0) ? reinterpret_cast<WarpStages*>(dsm) : nullptr;
+  const size_t vec_off = stages ? sizeof(WarpStages) * (BS / 32) : 0;
+  if (stages)
+    init_stages<BS>(stages);
+  else
+    __syncthreads();
   const RowCtx rc{stages, sm_red, plan.err, &sm_flag, plan.timeout_ns};
   // the instance descriptor lives in shared memory (one copy per CTA)
   __shared__ __align__(16) char sh_inst_raw[sizeof(Inst<MatT, VecT>)];
@@ -1021,7 +1018,7 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
     copy_inst<BS>(sh_inst, Ig);
     if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
-      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm + vec_smem_offset<BS>(), method);
+      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm + vec_off, method);
     } else {
       solve_instance<BS, Ld::Cached, kR>(g, sh_inst, plan, rc);
     }
