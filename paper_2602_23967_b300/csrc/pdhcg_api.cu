@@ -1017,18 +1017,19 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       for (int i = 0; i < count; ++i) args[size_t(i)] = make_setup_args<M, V>(P[size_t(i)], nullptr);
       const size_t abytes = sizeof(SetupArgs<M, V>) * args.size(), fbytes = 0;
       char* dscratch = nullptr;
+      // stream-ordered scratch: a plain cudaFree would wait for every kernel on
+      // the device, including a solve running on another stream
       struct ScratchGuard {
         char* p;
         cudaStream_t s;
-        bool async;
         ~ScratchGuard() {
-          if (p) async ? (void)cudaFreeAsync(p, s) : (void)cudaFree(p);
+          if (p) (void)cudaFreeAsync(p, s);
         }
       };
       if (from_pool) CK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dscratch), abytes + fbytes + 256,
                                                 alloc->pool, s));
-      else CK(cudaMalloc(&dscratch, abytes + fbytes + 256));
-      ScratchGuard guard{dscratch, s, from_pool};
+      else CK(cudaMallocAsync(reinterpret_cast<void**>(&dscratch), abytes + fbytes + 256, s));
+      ScratchGuard guard{dscratch, s};
       int32_t* ctl = reinterpret_cast<int32_t*>(dscratch + abytes + fbytes);
       CK(cudaMemcpyAsync(dscratch, args.data(), abytes, cudaMemcpyHostToDevice, s));
       CK(cudaMemsetAsync(ctl, 0, 2 * sizeof(int32_t), s));

@@ -29,9 +29,11 @@ class PdhcgError(RuntimeError):
 
 
 class Csr(C.Structure):
+    # pdhcg_csr: the three pointers (const int64_t*, const int32_t*, const
+    # double*) are filled with the arrays' integer addresses, which is much
+    # cheaper than building typed ctypes pointers for thousands of problems
     _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
-                ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
-                ("val", C.POINTER(C.c_double))]
+                ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -166,9 +168,7 @@ class _CsrHold:
         self.indices = np.ascontiguousarray(M.indices, dtype=np.int32)
         self.data = _f64(M.data)
         self.s = Csr(nrows, ncols, int(self.indptr[-1]) if len(self.indptr) else 0,
-                     self.indptr.ctypes.data_as(C.POINTER(C.c_int64)),
-                     self.indices.ctypes.data_as(C.POINTER(C.c_int32)),
-                     self.data.ctypes.data_as(_D))
+                     self.indptr.ctypes.data, self.indices.ctypes.data, self.data.ctypes.data)
 
 
 def _qp_args(qp):
@@ -286,8 +286,11 @@ def solve_batch(problems, want_solutions=True):
     res = (Result * count)()
     xs = [np.zeros(p.n) for p in problems] if want_solutions else None
     ys = [np.zeros(max(p.m, 1)) for p in problems] if want_solutions else None
-    xp = (_D * count)(*[_dp(x) for x in xs]) if want_solutions else None
-    yp = (_D * count)(*[_dp(y) for y in ys]) if want_solutions else None
+    # the double* tables as integer address arrays (one cast each, not one per problem)
+    xa = np.array([x.ctypes.data for x in xs], dtype=np.uint64) if want_solutions else None
+    ya = np.array([y.ctypes.data for y in ys], dtype=np.uint64) if want_solutions else None
+    xp = xa.ctypes.data_as(C.POINTER(_D)) if want_solutions else None
+    yp = ya.ctypes.data_as(C.POINTER(_D)) if want_solutions else None
     check(lib().pdhcg_solve_batch(handles, count, res, xp, yp), "pdhcg_solve_batch")
     out = [r.as_dict() for r in res]
     if want_solutions:
