@@ -189,8 +189,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 417_948_160, "instances": 512,
-                   "sources_sha256": "19928cd0ae9dd640047158c94e3d1237c9d8ed39a13fdd655d1ccfbbff81c330",
+TRAFFIC_CAPTURE = {"bytes": 545_607_936, "instances": 512,
+                   "sources_sha256": "d7929febae7ec4865d018b310e9c850c4603e512cff306e8089f2d09d60b3173",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")

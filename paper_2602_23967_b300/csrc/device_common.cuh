@@ -27,40 +27,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// ---- mbarrier + bulk-copy (TMA) helpers ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-// Bulk copy global -> shared, completing `bytes` of transaction on `bar`.
-// src, dst 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 // Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for).
 // src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-// Bounded wait for phase `parity` of `bar`; false after timeout_ns.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns);
-
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -177,24 +148,6 @@ struct Group {
     }
   }
 };
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
-  uint32_t done = 0;
-  uint64_t t0 = 0;
-  for (unsigned it = 0;; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63u) == 63u) {
-      const uint64_t t = globaltimer_ns();
-      if (t0 == 0) t0 = t;
-      else if (t - t0 > timeout_ns) return false;
-    }
-  }
-}
 
 // Bounded spin until *addr >= target.  Returns false after timeout_ns or when
 // another CTA reported an error.
@@ -420,53 +373,10 @@ __device__ __forceinline__ int64_t ldm64(const int64_t* p) {
   else return __ldg(reinterpret_cast<const long long*>(p));
 }
 
-// Stage SELL slices of streamed matrices into shared memory with TMA bulk
-// copies (1) instead of loading them directly (0).
-#ifndef PDHCG_TMA_STAGING
-#define PDHCG_TMA_STAGING 0
-#endif
-// Columns per TMA chunk of a slice (chunk = 32 rows x kChunkCols columns).
-constexpr int kChunkCols = 8;
-constexpr int kChunkElems = kChunkCols * 32;
-
-// Per-warp double-buffered shared-memory staging of slice chunks for two sources.
-// Values are stored in 8-byte slots so one layout serves FP32 and FP64 matrices.
-struct WarpStages {
-  int colA_[2][kChunkElems];
-  int colB_[2][kChunkElems];
-  double valA_[2][kChunkElems];
-  double valB_[2][kChunkElems];
-  uint64_t bar[2];
-  unsigned parity[2];
-  int next;
-  __device__ __forceinline__ int* colA(int st) { return colA_[st]; }
-  __device__ __forceinline__ int* colB(int st) { return colB_[st]; }
-  __device__ __forceinline__ void* valA(int st) { return valA_[st]; }
-  __device__ __forceinline__ void* valB(int st) { return valB_[st]; }
-};
-
 // Shared context of the row engine for one CTA.
 struct RowCtx {
-  WarpStages* stages;  // one per warp (TMA staging only)
-  double* red;         // BS/32 * 4 doubles
-  int* err;
-  int* fail_flag;      // shared: set when a bounded wait of this CTA gave up
-  uint64_t timeout_ns;
+  double* red;  // BS/32 * 4 doubles of shared scratch (huge-row reductions)
 };
-
-// Initialise the warps' stage barriers (once per kernel, before any phase).
-template <int BS>
-__device__ __forceinline__ void init_stages(WarpStages* st) {
-  if (threadIdx.x < BS / 32) {
-    mbar_init(&st[threadIdx.x].bar[0], 1);
-    mbar_init(&st[threadIdx.x].bar[1], 1);
-    st[threadIdx.x].parity[0] = 0;
-    st[threadIdx.x].parity[1] = 0;
-    st[threadIdx.x].next = 0;
-  }
-  fence_mbar_init();
-  __syncthreads();
-}
 
 // A product source: matrix in SELL form (regular rows) and CSR form (long and
 // huge rows), with NG gathers (0, 1 or 2) of the column index.
@@ -609,10 +519,7 @@ __device__ __forceinline__ void csr_part(const X& x, int row, int first, int ste
 template <int BS, Ld LM, class Acc, class SA, class SB, class Epi>
 __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank, const SA& A,
                                         const SB& B, const RowCtx& rc, Epi epi) {
-  WarpStages* stages = rc.stages;
   double* red = rc.red;
-  int* err = rc.err;
-  const uint64_t tmo = rc.timeout_ns;
   constexpr int NA = SA::NG, NB = SB::NG, NS = NA + NB;
   static_assert(NS >= 1 && NS <= 4, "1..4 sums per row");
   constexpr int NW = BS / 32;
@@ -626,208 +533,44 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
     h0 = sp.huge_part[part_rank];
     h1 = sp.huge_part[part_rank + 1];
   }
-  // TMA staging applies to streamed matrices (multi-CTA groups), whose launch
-  // provides the per-warp stages; other callers pass no stages.
-  constexpr bool kTma = PDHCG_TMA_STAGING && LM == Ld::Stream;
-  if (kTma && stages != nullptr) {
-    // regular rows: the warp streams its slices in chunks of kChunkCols columns.
-    // Lane 0 bulk-copies (TMA) the next chunk's column indices and values of both
-    // sources into the warp's other shared-memory stage while the lanes gather and
-    // multiply-add the current chunk; the row epilogue runs after a slice's last chunk.
-    if (sp.nslices > 0 && s0 + warp < s1) {
-      using MA = typename SrcMat<SA>::type;
-      using MB = typename SrcMat<SB>::type;
-      constexpr int CC = kChunkCols;
-      constexpr int CE = CC * 32;
-      WarpStages& ws = stages[warp];
-      const bool onA = NA > 0 && A.on, onB = NB > 0 && B.on;
-      // slice geometry
-      auto geom = [&](int s, int64_t& ba, int& wa, int64_t& bb, int& wb) {
-        ba = 0; wa = 0; bb = 0; wb = 0;
-        if constexpr (NA > 0) if (onA) { ba = ldm64<LM>(A.S.ptr + s); wa = int((ldm64<LM>(A.S.ptr + s + 1) - ba) >> 5); }
-        if constexpr (NB > 0) if (onB) { bb = ldm64<LM>(B.S.ptr + s); wb = int((ldm64<LM>(B.S.ptr + s + 1) - bb) >> 5); }
-      };
-      // issue chunk ch of slice (ba, wa, bb, wb) into stage st
-      auto issue = [&](int st, int ch, int64_t ba, int wa, int64_t bb, int wb) {
-        if (lane == 0) {
-          const int na = max(0, min(CC, wa - ch * CC)), nb = max(0, min(CC, wb - ch * CC));
-          const unsigned bytes = unsigned(na) * 32u * (4u + sizeof(MA)) + unsigned(nb) * 32u * (4u + sizeof(MB));
-          fence_proxy_async();
-          mbar_arrive_expect_tx(&ws.bar[st], bytes);
-          if constexpr (NA > 0)
-            if (na > 0) {
-              const int64_t off = ba + int64_t(ch) * CE;
-              bulk_g2s(ws.colA(st), A.S.col + off, unsigned(na) * 128u, &ws.bar[st]);
-              bulk_g2s(ws.valA(st), A.S.val + off, unsigned(na) * 32u * sizeof(MA), &ws.bar[st]);
-            }
-          if constexpr (NB > 0)
-            if (nb > 0) {
-              const int64_t off = bb + int64_t(ch) * CE;
-              bulk_g2s(ws.colB(st), B.S.col + off, unsigned(nb) * 128u, &ws.bar[st]);
-              bulk_g2s(ws.valB(st), B.S.val + off, unsigned(nb) * 32u * sizeof(MB), &ws.bar[st]);
-            }
-        }
-      };
-      // stage index and barrier parities live in registers (identical in all
-      // lanes) and are written back to shared memory once at the end
-      int st = ws.next;
-      unsigned par[2] = {ws.parity[0], ws.parity[1]};
-      __syncwarp();
-      int s = s0 + warp;
-      int64_t ba, bb;
-      int wa, wb;
-      geom(s, ba, wa, bb, wb);
-      int nch = (max(wa, wb) + CC - 1) / CC;
-      int ch = 0;
-      bool have = false;  // chunk (s, ch) already issued into stage st
-      int row = ldm<LM>(sp.perm + s * 32 + lane);
-      Acc sums[NS];
-#pragma unroll
-      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-      int sn = s + NW;
-      int64_t nba = 0, nbb = 0;
-      int nwa = 0, nwb = 0;
-      if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
-      bool failed = false;
-      while (true) {
-        if (ch < nch) {
-          if (!have) issue(st, ch, ba, wa, bb, wb);
-          // prefetch the following chunk (this slice or the next one)
-          bool have2 = false;
-          if (ch + 1 < nch) {
-            issue(st ^ 1, ch + 1, ba, wa, bb, wb);
-            have2 = true;
-          } else if (sn < s1 && max(nwa, nwb) > 0) {
-            issue(st ^ 1, 0, nba, nwa, nbb, nwb);
-            have2 = true;
-          }
-          if (!mbar_wait(&ws.bar[st], par[st], tmo)) {
-            // give the prefetched copy (if any) a bounded chance to land before leaving
-            if (have2) mbar_wait(&ws.bar[st ^ 1], par[st ^ 1], tmo);
-            failed = true;
-            break;
-          }
-          par[st] ^= 1u;
-          if constexpr (NA > 0)
-            if (onA && ch * CC < wa) {
-              const int na = min(CC, wa - ch * CC);
-              const int* cs = ws.colA(st) + lane;
-              const MA* vs = reinterpret_cast<const MA*>(ws.valA(st)) + lane;
-              Acc g1v[CC];
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < na) g1v[u] = Acc(A.g1(cs[32 * u]));
-              if constexpr (NA == 2) {
-                Acc g2v[CC];
-#pragma unroll
-                for (int u = 0; u < CC; ++u)
-                  if (u < na) g2v[u] = Acc(A.g2(cs[32 * u]));
-#pragma unroll
-                for (int u = 0; u < CC; ++u)
-                  if (u < na) madd(sums[1], vs[32 * u], g2v[u]);
-              }
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < na) madd(sums[0], vs[32 * u], g1v[u]);
-            }
-          if constexpr (NB > 0)
-            if (onB && ch * CC < wb) {
-              const int nb = min(CC, wb - ch * CC);
-              const int* cs = ws.colB(st) + lane;
-              const MB* vs = reinterpret_cast<const MB*>(ws.valB(st)) + lane;
-              Acc g1v[CC];
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < nb) g1v[u] = Acc(B.g1(cs[32 * u]));
-              if constexpr (NB == 2) {
-                Acc g2v[CC];
-#pragma unroll
-                for (int u = 0; u < CC; ++u)
-                  if (u < nb) g2v[u] = Acc(B.g2(cs[32 * u]));
-#pragma unroll
-                for (int u = 0; u < CC; ++u)
-                  if (u < nb) madd(sums[NA + 1], vs[32 * u], g2v[u]);
-              }
-#pragma unroll
-              for (int u = 0; u < CC; ++u)
-                if (u < nb) madd(sums[NA], vs[32 * u], g1v[u]);
-            }
-          __syncwarp();  // every lane is done with stage st before it is refilled
-          st ^= 1;
-          ++ch;
-          have = have2;
-          continue;
-        }
-        // slice done
-#pragma unroll
-        for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
-        if (row >= 0) epi(row, sums);
-        if (sn >= s1) break;
-        s = sn;
-        ba = nba;
-        wa = nwa;
-        bb = nbb;
-        wb = nwb;
-        nch = (max(wa, wb) + CC - 1) / CC;
-        ch = 0;
-        row = ldm<LM>(sp.perm + s * 32 + lane);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-        sn = s + NW;
-        if (sn < s1) geom(sn, nba, nwa, nbb, nwb);
+  // regular rows: one slice per warp at a time, lane l summing the row in slot l.
+  // Streamed matrices: lane 0 also prefetches into L2 the slice this warp takes
+  // PDHCG_L2_PREFETCH turns later (issued after the current slice, whose work
+  // covers the latency of the two pointer loads).
+  constexpr bool kPf = LM == Ld::Stream && PDHCG_L2_PREFETCH > 0;
+  if constexpr (kPf) {
+    if (lane == 0)
+      for (int d = 0; d < PDHCG_L2_PREFETCH; ++d) {
+        int64_t b, e;
+        slice_span<LM>(A, s0 + warp + d * NW, s1, b, e);
+        slice_prefetch_l2(A, b, e);
+        slice_span<LM>(B, s0 + warp + d * NW, s1, b, e);
+        slice_prefetch_l2(B, b, e);
       }
-      __syncwarp();
-      if (lane == 0) {
-        ws.next = st;
-        ws.parity[0] = par[0];
-        ws.parity[1] = par[1];
-        if (failed) {
-          atomicExch(err, 1);
-          *rc.fail_flag = 1;
-        }
-      }
-      __syncwarp();
-    }
-  } else {
-    // regular rows: one slice per warp at a time, lane l summing the row in slot l.
-    // Streamed matrices: lane 0 also prefetches into L2 the slice this warp takes
-    // PDHCG_L2_PREFETCH turns later (issued after the current slice, whose work
-    // covers the latency of the two pointer loads).
-    constexpr bool kPf = LM == Ld::Stream && PDHCG_L2_PREFETCH > 0;
+  }
+  for (int s = s0 + warp; s < s1; s += NW) {
+    const int row = ldm<LM>(sp.perm + s * 32 + lane);
+    int64_t pab = 0, pae = 0, pbb = 0, pbe = 0;
     if constexpr (kPf) {
-      if (lane == 0)
-        for (int d = 0; d < PDHCG_L2_PREFETCH; ++d) {
-          int64_t b, e;
-          slice_span<LM>(A, s0 + warp + d * NW, s1, b, e);
-          slice_prefetch_l2(A, b, e);
-          slice_span<LM>(B, s0 + warp + d * NW, s1, b, e);
-          slice_prefetch_l2(B, b, e);
-        }
-    }
-    for (int s = s0 + warp; s < s1; s += NW) {
-      const int row = ldm<LM>(sp.perm + s * 32 + lane);
-      int64_t pab = 0, pae = 0, pbb = 0, pbe = 0;
-      if constexpr (kPf) {
-        if (lane == 0) {
-          slice_span<LM>(A, s + PDHCG_L2_PREFETCH * NW, s1, pab, pae);
-          slice_span<LM>(B, s + PDHCG_L2_PREFETCH * NW, s1, pbb, pbe);
-        }
+      if (lane == 0) {
+        slice_span<LM>(A, s + PDHCG_L2_PREFETCH * NW, s1, pab, pae);
+        slice_span<LM>(B, s + PDHCG_L2_PREFETCH * NW, s1, pbb, pbe);
       }
-      Acc sums[NS];
-#pragma unroll
-      for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
-      slice_dot<LM, Acc>(A, s, lane, sums);
-      slice_dot<LM, Acc>(B, s, lane, sums + NA);
-      if constexpr (kPf) {
-        if (lane == 0) {
-          slice_prefetch_l2(A, pab, pae);
-          slice_prefetch_l2(B, pbb, pbe);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
-      if (row >= 0) epi(row, sums);
     }
+    Acc sums[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sums[q] = Acc(0);
+    slice_dot<LM, Acc>(A, s, lane, sums);
+    slice_dot<LM, Acc>(B, s, lane, sums + NA);
+    if constexpr (kPf) {
+      if (lane == 0) {
+        slice_prefetch_l2(A, pab, pae);
+        slice_prefetch_l2(B, pbb, pbe);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc_finish(sums[q]);
+    if (row >= 0) epi(row, sums);
   }
   // long rows: one warp per row
   for (int li = l0 + warp; li < l1; li += NW) {

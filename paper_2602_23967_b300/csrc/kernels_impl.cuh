@@ -8,16 +8,13 @@
 
 namespace pdhcg {
 
-// Dynamic shared memory of a group launch (TMA stages); pool launches use theirs
-// for instance vectors instead.
-inline size_t solve_dyn_smem() { return PDHCG_TMA_STAGING ? sizeof(WarpStages) * (kGroupBS / 32) : 0; }
-
 template <class MatT, class VecT>
 cudaError_t set_solve_attrs(size_t extra = 0) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  size_t want = solve_dyn_smem() + extra;
+  // dynamic shared memory: the instance vectors of pool solves (group launches use none)
+  size_t want = extra;
   const size_t static_part = 8192;  // group_reduce / row-engine shared arrays
   if (want + static_part > size_t(optin)) want = size_t(optin) - static_part;
   cudaError_t e = cudaSuccess;
@@ -52,11 +49,9 @@ cudaError_t kernel_limits(KernelLimits* out) {
   if (e != cudaSuccess) return e;
   e = set_solve_attrs<MatT, VecT>();
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS,
-                                                    solve_dyn_smem());
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS, 0);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kGroupBS, MatT, VecT, true>, kGroupBS,
-                                                    solve_dyn_smem());
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kGroupBS, MatT, VecT, true>, kGroupBS, 0);
   if (e != cudaSuccess) return e;
   nb = std::min(nb, nr);  // a cooperative launch of either variant must fit
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ns, setup_kernel<kGroupBS, MatT, VecT>, kGroupBS, 0);
@@ -87,7 +82,7 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   const size_t extra = plan.group_blocks == 0 ? size_t(plan.smem_vec_bytes) : 0;
   cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
   if (e != cudaSuccess) return e;
-  const size_t smem = plan.group_blocks > 0 ? solve_dyn_smem() : extra;
+  const size_t smem = plan.group_blocks > 0 ? 0 : extra;
   const bool r = plan.structured != 0;
   if (plan.group_blocks == 0) {
     if (r)

@@ -306,7 +306,7 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
   const int prank = g.nblk > 1 ? g.rank : -1;
   const Csr<MatT> Acsr{a.m, a.Ap[a.m], a.Ap, a.Ac, a.As};
   const Csr<MatT> ATcsr{a.n, a.ATp[a.n], a.ATp, a.ATc, a.ATs};
-  RowCtx rc{nullptr, g.red, g.err, g.sm_flag, g.timeout_ns};
+  RowCtx rc{g.red};
   if (a.m > 0) {
     const int kmax = a.power_max_iter < kLanczosCap ? a.power_max_iter : kLanczosCap;
     const double v0 = 1.0 / sqrt(double(a.n));

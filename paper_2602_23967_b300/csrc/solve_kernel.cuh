@@ -979,15 +979,8 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
   g.failed = false;
   g.epoch = 0;
   if (threadIdx.x == 0) sm_flag = 0;
-  // dynamic shared memory: the TMA stages of a group launch, else the vectors
-  // of pool solves
-  WarpStages* stages = (PDHCG_TMA_STAGING && plan.group_blocks > 0) ? reinterpret_cast<WarpStages*>(dsm) : nullptr;
-  const size_t vec_off = stages ? sizeof(WarpStages) * (BS / 32) : 0;
-  if (stages)
-    init_stages<BS>(stages);
-  else
-    __syncthreads();
-  const RowCtx rc{stages, sm_red, plan.err, &sm_flag, plan.timeout_ns};
+  __syncthreads();
+  const RowCtx rc{sm_red};
   // the instance descriptor lives in shared memory (one copy per CTA)
   __shared__ __align__(16) char sh_inst_raw[sizeof(Inst<MatT, VecT>)];
   Inst<MatT, VecT>& sh_inst = *reinterpret_cast<Inst<MatT, VecT>*>(sh_inst_raw);
@@ -1018,7 +1011,7 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
     copy_inst<BS>(sh_inst, Ig);
     if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
-      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm + vec_off, method);
+      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm, method);
     } else {
       solve_instance<BS, Ld::Cached, kR>(g, sh_inst, plan, rc);
     }
