@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--large-iters", type=int, default=128,
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second")
-    ap.add_argument("--serve-seconds", type=float, default=1.5, help="length of the arrival trace")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the arrival trace")
     ap.add_argument("--serve-slots", type=int, default=2 * 148, help="concurrent solves of the serving loop")
     return ap.parse_args()
 
@@ -189,8 +189,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 545_607_936, "instances": 512,
-                   "sources_sha256": "d7929febae7ec4865d018b310e9c850c4603e512cff306e8089f2d09d60b3173",
+TRAFFIC_CAPTURE = {"bytes": 425_223_424, "instances": 512,
+                   "sources_sha256": "51f8744ed4a8d2d4c9dc7a9a5ab2fa385c849571e82c5796fc73a8196ffbc8c9",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
@@ -309,7 +309,8 @@ def serving_leg(args, prm, stream):
             "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if len(out) else None,
             "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if len(out) else None,
             "latency_max_ms": float(lat.max() * 1e3) if len(out) else None,
-            "hbm_budget_gb": 100, "max_slots": args.serve_slots, "slice_iterations": 256,
+            "hbm_budget_gb": 100, "max_slots": args.serve_slots,
+            "slice": "10 ms of device time per launch (each solve pauses at the first 16-step boundary past it)",
             "launches": st["launches"], "scheduler_seconds": {"admit": st["admit_seconds"],
                                                              "slices": st["slice_seconds"],
                                                              "retire": st["retire_seconds"]}}

@@ -101,14 +101,16 @@ int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes);
 SolverState initial_state(const pdhcg_problem* P);
 void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res);
 // One pooled launch advancing every handle by at most iter_budget PDHG steps
-// (0 = to completion), with handle i's state at d_states[slots ? slots[i] : i]
+// (0 = no step limit) and, when slice_ns > 0, until about slice_ns of device
+// time has passed (checked every 16 steps), with handle i's state at d_states[slots ? slots[i] : i]
 // on the device and its solution written to x_out[i] / y_out[i] (device, may
 // be null).  scratch (device, scratch_bytes) holds the launch descriptors when
 // large enough; the caller then synchronises the stream before reusing it.
 // Without it the call allocates a temporary buffer and blocks until done.
 int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states,
                       double* const* x_out, double* const* y_out, int64_t iter_budget,
-                      const int* slots = nullptr, void* scratch = nullptr, size_t scratch_bytes = 0);
+                      const int* slots = nullptr, void* scratch = nullptr, size_t scratch_bytes = 0,
+                      uint64_t slice_ns = 0);
 int check_params_c(const pdhcg_params* p);
 
 }  // namespace pdhcg

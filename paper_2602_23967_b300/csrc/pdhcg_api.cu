@@ -1080,7 +1080,7 @@ int check_params_c(const pdhcg_params* p) { return check_params(p); }
 
 int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states, double* const* x_out,
                       double* const* y_out, int64_t iter_budget, const int* slots, void* scratch,
-                      size_t scratch_bytes) {
+                      size_t scratch_bytes, uint64_t slice_ns) {
   if (count <= 0) return PDHCG_OK;
   const pdhcg_problem* P0 = probs[0];
   CK(cudaSetDevice(P0->device));
@@ -1117,6 +1117,7 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
     plan.pool_next = d_i32 + count;
     plan.err = d_i32 + count + 1;
     plan.iter_budget = iter_budget;
+    plan.slice_ns = slice_ns;
     plan.smem_vec_bytes = int64_t(need);
     plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
     int sms = 0, dev = 0;

@@ -157,6 +157,10 @@ struct LaunchPlan {
   // Slice limits for the serving loop: a solve pauses at the first check
   // boundary after it has done iter_budget steps in this launch (0 = none).
   int64_t iter_budget = 0;
+  // Serving slices: a single-CTA solve also pauses, at a step boundary, once
+  // this many nanoseconds of device time have passed since it resumed (0 = none),
+  // so that every slot of a launch stops at about the same time.
+  uint64_t slice_ns = 0;
   // Pool CTAs copy an instance's vectors into dynamic shared memory when they
   // fit in this many bytes (0 = never); see smem_vector_bytes().
   int64_t smem_vec_bytes = 0;

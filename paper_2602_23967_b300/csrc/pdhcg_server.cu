@@ -7,8 +7,8 @@
 //     launch) on its own stream, so creation and device setup of new requests
 //     overlap the slices of the running ones.  Finished handles go to a ready list.
 //   Slice thread: at each slice boundary moves ready handles into free slots,
-//     advances every live solve by one slice of at most `slice_iters` PDHG steps
-//     in a single pooled launch (iterates, anchors, PID and restart state stay
+//     advances every live solve by one slice of 10 ms of device time
+//     (PDHCG_SLICE_US) in a single pooled launch (iterates, anchors, PID and restart state stay
 //     on the device between slices), then retires the solves that stopped:
 //     copies their results and solutions to host memory in one batch and frees
 //     their device memory and slot.
@@ -79,10 +79,18 @@ struct pdhcg_server {
   size_t budget = 0;
   int max_slots = 0;
   size_t max_queue = 0;
+// A slice advances every live solve for PDHCG_SLICE_US microseconds of device
+// time (instances differ in cost per step, so a fixed step count would leave the
+// CTAs of small instances idle while the largest finish); with
+// PDHCG_SLICE_US = 0, for PDHCG_SLICE_ITERS steps instead.
+#ifndef PDHCG_SLICE_US
+#define PDHCG_SLICE_US 10000
+#endif
 #ifndef PDHCG_SLICE_ITERS
 #define PDHCG_SLICE_ITERS 256
 #endif
-  int64_t slice_iters = PDHCG_SLICE_ITERS;
+  int64_t slice_iters = PDHCG_SLICE_US > 0 ? 0 : PDHCG_SLICE_ITERS;
+  uint64_t slice_ns = uint64_t(PDHCG_SLICE_US) * 1000u;
   pdhcg_params prm{};
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -236,7 +244,7 @@ static void worker_loop(pdhcg_server* S) {
       slots[size_t(i)] = l.slot;
     }
     int rc = launch_pool_slice(probs.data(), count, S->d_states, xo.data(), yo.data(), S->slice_iters,
-                               slots.data(), S->d_launch, S->launch_bytes);
+                               slots.data(), S->d_launch, S->launch_bytes, S->slice_ns);
     cudaMemcpyAsync(S->h_states, S->d_states, sizeof(SolverState) * size_t(S->max_slots),
                     cudaMemcpyDeviceToHost, S->stream);
     cudaStreamSynchronize(S->stream);

@@ -590,6 +590,10 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     S.cur = 0;
   }
   const int64_t K_first = S.K;
+  // device-time slice budget (single-CTA solves): thread 0 reads the clock every
+  // 16 steps and shares the decision, so the whole CTA pauses together
+  __shared__ int sm_pause;
+  const uint64_t t_resume = globaltimer_ns();
 
   while (ok) {
     const int cur = S.cur;
@@ -845,6 +849,13 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     }
     S.K += 1;
     if (plan.iter_budget > 0 && S.K - K_first >= plan.iter_budget) break;  // paused
+    if (plan.slice_ns > 0 && g.nblk == 1 && ((S.K - K_first) & 15) == 0) {
+      if (threadIdx.x == 0) sm_pause = globaltimer_ns() - t_resume >= plan.slice_ns;
+      __syncthreads();
+      const bool pause = sm_pause != 0;
+      __syncthreads();  // thread 0 rewrites sm_pause only after every thread has read it
+      if (pause) break;  // paused
+    }
   }
   if (!ok) S.device_error = 1;
   if (g.rank == 0 && threadIdx.x == 0) *I.st = S;
