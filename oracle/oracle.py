@@ -203,14 +203,22 @@ def solve(qp, params: OracleParams | None = None, x0=None, y0=None, eps_trace_le
 
 
 def ruiz(qp, passes: int = 10):
+    """Ruiz factors (D, E) of the problem; with a factor qp.R the objective is
+    Q + R^T R and the diagonal of R^T R enters the column maxima."""
     lib = _load()
     n, m = int(qp.n), int(qp.m)
     Qh = _CsrHold(qp.Q, n, n) if qp.Q is not None else None
     Ah = _CsrHold(qp.A, m, n)
     D = np.zeros(n)
     E = np.zeros(max(m, 1))
-    lib.oracle_ruiz(C.c_int32(n), C.c_int32(m), C.byref(Qh.s) if Qh else None, C.byref(Ah.s),
-                    C.c_int32(passes), _ptr(D), _ptr(E))
+    R = getattr(qp, "R", None)
+    if R is not None:
+        Rh = _CsrHold(R, R.shape[0], n)
+        lib.oracle_ruiz_qr(C.c_int32(n), C.c_int32(m), C.byref(Qh.s) if Qh else None, C.byref(Rh.s),
+                           C.byref(Ah.s), C.c_int32(passes), _ptr(D), _ptr(E))
+    else:
+        lib.oracle_ruiz(C.c_int32(n), C.c_int32(m), C.byref(Qh.s) if Qh else None, C.byref(Ah.s),
+                        C.c_int32(passes), _ptr(D), _ptr(E))
     return D, E[:m]
 
 

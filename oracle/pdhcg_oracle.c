@@ -166,9 +166,16 @@ void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A,
   ruiz_impl(n, m, Q, NULL, A, passes, D, E);
 }
 
+void oracle_ruiz_qr(int32_t n, int32_t m, const oracle_csr* P, const oracle_csr* R, const oracle_csr* A,
+                    int32_t passes, double* D, double* E) {
+  ruiz_impl(n, m, P, R, A, passes, D, E);
+}
+
 /* With a structured Q = P + R^T R (reading): the column maximum of Q is taken
- * over the entries of P and the diagonal of R^T R (squared column norms of R),
- * which bounds every entry of R^T R in its row and column. */
+ * over the entries of P and the diagonal of R^T R (squared column norms of R).
+ * By Cauchy-Schwarz each entry of R^T R is at most the geometric mean of the
+ * two diagonal entries in its row and column, so the diagonal carries the size
+ * of R^T R without forming it. */
 static void ruiz_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* R, const oracle_csr* A,
                       int32_t passes, double* D, double* E) {
   double* rd = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));

@@ -56,6 +56,10 @@ typedef struct {
 void oracle_default_params(oracle_params* p);
 void oracle_ruiz(int32_t n, int32_t m, const oracle_csr* Q, const oracle_csr* A, int32_t passes,
                  double* D, double* E);
+/* The same for a structured Q = P + R^T R given by P (n x n, may be NULL) and
+ * R (k x n): the column maxima include the scaled diagonal of R^T R. */
+void oracle_ruiz_qr(int32_t n, int32_t m, const oracle_csr* P, const oracle_csr* R, const oracle_csr* A,
+                    int32_t passes, double* D, double* E);
 double oracle_norm_estimate(const oracle_csr* A, const double* val, int32_t max_iter, double tol,
                             int32_t* iters_out);
 int32_t oracle_inner_solve(int32_t n, const oracle_csr* Q, const double* lv, const double* uv,

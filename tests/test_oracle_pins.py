@@ -390,3 +390,30 @@ def test_factored_q_reaches_the_formed_q_optimum(seed):
     rp, rd, rg, _, _ = oracle.kkt(formed.n, formed.m, xf, yf, formed.A @ xf, formed.A.T @ yf, Qx,
                                   formed.c, formed.lc, formed.uc, formed.lv, formed.uv)
     assert max(rp, rd, rg) <= 2e-9
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_factored_ruiz_equals_formed_when_RtR_is_diagonal(seed):
+    # Scaling of a structured Q = P + R^T R (Sec. 2.2; the scaling itself is a
+    # reading): the column maxima take the scaled diagonal of R^T R.  With one
+    # nonzero per row of R, R^T R is exactly diagonal, so with P = 0 the factored
+    # scaling must equal Ruiz on the explicitly formed Q = R^T R (scipy product).
+    rng = np.random.default_rng(seed)
+    n, m, k = 30, 12, 45
+    cols = rng.integers(0, n, k)
+    vals = rng.normal(size=k) * rng.uniform(0.1, 10.0, k)
+    R = sp.csr_matrix((vals, (np.arange(k), cols)), shape=(k, n))
+    A = sp.random(m, n, density=0.3, random_state=rng, format="csr")
+    A.data = rng.normal(size=A.nnz) * 5.0
+    c = rng.normal(size=n)
+    lv, uv = -np.ones(n), np.ones(n)
+    lc, uc = -np.ones(m), np.ones(m)
+    formed = W.QP(n, m, W._csr(R.T @ R), A, c, lc, uc, lv, uv)
+    factored = W.QP(n, m, None, A, c, lc, uc, lv, uv, R=R)
+    Df, Ef = oracle.ruiz(factored, 10)
+    D, E = oracle.ruiz(formed, 10)
+    np.testing.assert_allclose(Df, D, rtol=1e-14)
+    np.testing.assert_allclose(Ef, E, rtol=1e-14)
+    # and the reading is not vacuous: without R the scaling differs
+    Dn, _ = oracle.ruiz(W.QP(n, m, None, A, c, lc, uc, lv, uv), 10)
+    assert np.max(np.abs(Dn - D) / D) > 1e-3
