@@ -84,3 +84,27 @@ def test_rejects_bad_params():
         pdhcg.Problem(qp, p)
     with pytest.raises(pdhcg.PdhcgError):
         pdhcg.Problem(qp, pdhcg.default_params(k_eval=0))
+
+
+def test_rejects_malformed_structured_objective():
+    # pdhcg_create_qr (Q = P + R^T R, Sec. 2.2) validates R before any device work
+    def factored():
+        return W.random_qp(n=20, m=8, n_eq=4, m_rows=5, density=0.3, seed=2, factored=True)
+    qp = factored()
+    R = qp.R.tocsr().copy()
+    R.indices = R.indices.copy(); R.indices[0] = qp.n + 3   # column beyond n
+    qp.R = R
+    assert "range" in _bad(qp)
+    qp = factored()
+    R = qp.R.tocsr().copy()
+    R.data = R.data.copy(); R.data[0] = np.inf
+    qp.R = R
+    assert "finite" in _bad(qp)
+    qp = factored()
+    qp.R = sp.csr_matrix((0, qp.n))
+    assert "k >= 1" in _bad(qp)
+    # R^T R makes Q non-diagonal: the closed-form inner solve does not apply
+    assert "DIAG" in _bad(factored(), inner="diag")
+    # the batched creation takes plain Q only
+    with pytest.raises(ValueError):
+        pdhcg.create_batch([factored()], pdhcg.default_params())
