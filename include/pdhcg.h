@@ -255,8 +255,11 @@ void pdhcg_destroy(pdhcg_t* prob);
  * footprint fits hbm_budget_bytes and a slot (max_slots) is free, keeps every
  * live solve's iterates and restart state resident on the device, and packs
  * all live solves into shared persistent launches that each advance every live
- * solve by a bounded slice of iterations; finished solves free their slot and
- * memory at the next slice boundary, where waiting requests are admitted. */
+ * solve for a slice of about 10 ms of device time (each solve pauses at the
+ * first 16-step boundary past it, so slots of unequal cost stop together);
+ * finished solves free their slot and memory at the next slice boundary, where
+ * waiting requests are admitted.  The paper solves one problem at a time and
+ * has no counterpart of this loop. */
 typedef struct {
   uint64_t submitted, admitted, completed, rejected;
   uint64_t launches;
