@@ -3,7 +3,7 @@
 Workload (default ``--workload mpc_batch``): 4,096 linear-MPC QPs, horizon
 T ~ U{10..50}, 12 states / 4 inputs (n = 16T, m = 12T), solved to relative KKT
 1e-6 by one persistent launch of the PDHCG-II kernel (pdhcg_solve_batch), FP32
-matrix values with FP64 vectors and reductions.  Also timed: the plain
+matrix values, double-float vectors and FP64 reductions.  Also timed: the plain
 one-at-a-time solver on a sample of the same instances, the end-to-end path
 through the public API (problem upload + device setup + solve + result
 download), and the FP64 CPU oracle on a sample (cpu_baseline).
@@ -190,18 +190,33 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
 TRAFFIC_CAPTURE = {"bytes": 425_223_424, "instances": 512,
-                   "sources_sha256": "51f8744ed4a8d2d4c9dc7a9a5ab2fa385c849571e82c5796fc73a8196ffbc8c9",
+                   "sources_sha256": "58fb6ef4585b9c53d30c1cf4b63e92eda6623f5b9a45535fe4dfe8e31537c652",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
 
 
-def kernel_sources_sha256():
+def code_of(text):
+    """C/C++/CUDA source with comments and blank lines removed, so that the hash
+    below follows the code only (string literals in kernel sources hold no
+    comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
+def kernel_sources_sha256(read=None):
+    """SHA-256 over the code (comments stripped) of the solve kernel's sources."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2602_23967_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2602_23967_b300", "csrc", name)) as f:
+                text = f.read()
+        else:
+            text = read(name)
+        h.update(code_of(text).encode())
     return h.hexdigest()
 
 

@@ -2,7 +2,7 @@
 //
 // One call of solve_instance() runs the iteration of one instance on a group of
 // CTAs (see device_common.cuh) until it stops (KKT tolerance, infeasibility,
-// limits) or its iteration slice is used up.  Per PDHG step:
+// limits) or its slice (a step count or, for serving, device time) is used up.  Per PDHG step:
 //
 //   Phase I   (n-space rows)  g = A^T y, b = x/tau - c - g            (Eq. primal_update)
 //                             DIAG: x+ = clamp(b / (diag Q + 1/tau))   (Sec. 2.2, closed form)
@@ -15,6 +15,11 @@
 //   every k_eval steps        KKT residuals on the original data (Sec. 4.2), primal and dual
 //                             infeasibility tests (Sec. 5.1, 5.2), restart test and PID
 //                             update of the primal weight (Sec. 3.2, Eq. pid)
+//
+// Structured objective Q = P + R^T R (Sec. 2.2): before each Q product an
+// R-space phase computes t = R v over the k rows of R, and the Q rows gather
+// P v and R^T t as one matrix [P | R^T] whose columns >= n address t.  These
+// phases exist only in the kernel variant with kR = true.
 //
 // Vector updates run in VecT; inner products use DotAcc (FP64, or compensated
 // FP32 that is exact to about 2^-48 relative) and are combined across the
