@@ -28,3 +28,30 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def golden_closed_form_qps():
+    """The hand-derived QPs of tests/golden/closed_form_qps.json as (QP, x*, f*)."""
+    import json
+
+    import numpy as np
+    import scipy.sparse as sp
+
+    from paper_2602_23967_b300 import workloads as W
+
+    def vec(v, absent):
+        return np.array([absent if a is None else a for a in v], dtype=np.float64)
+
+    with open(os.path.join(ROOT, "tests", "golden", "closed_form_qps.json")) as f:
+        data = json.load(f)
+    out = []
+    for p in data["problems"]:
+        n = len(p["c"])
+        m = len(p["A"])
+        Q = sp.csr_matrix(np.array(p["Q"], dtype=np.float64))
+        A = sp.csr_matrix(np.array(p["A"], dtype=np.float64).reshape(m, n))
+        lc, uc = vec(p["lc"], -np.inf), vec(p["uc"], np.inf)  # null = absent bound
+        lv, uv = vec(p["lv"], -np.inf), vec(p["uv"], np.inf)
+        qp = W.QP(n, m, Q, A, np.array(p["c"], dtype=np.float64), lc, uc, lv, uv, name=p["name"])
+        out.append((qp, np.array(p["x"], dtype=np.float64), float(p["objective"])))
+    return out

@@ -369,3 +369,14 @@ def test_mixed_batch_of_plain_and_structured_problems():
         assert max(rp, rd, rg) <= 3e-6, (rp, rd, rg)
         _, _, ro = oracle.solve(formed, oracle.default_params(eps_tol=1e-6))
         assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat"])
+def test_golden_closed_forms_on_gpu(precision):
+    # the hand-derived QPs of tests/golden/closed_form_qps.json on the CUDA path
+    from conftest import golden_closed_form_qps
+    for qp, xs, fs in golden_closed_form_qps():
+        x, y, r, _ = gpu_solve(qp, eps_tol=1e-9, precision=precision, max_iter=1_000_000)
+        assert r["status_name"] == "OPTIMAL", (qp.name, r)
+        np.testing.assert_allclose(x, xs, atol=1e-7, err_msg=qp.name)
+        assert rel(r["primal_obj"], fs) <= 1e-8, (qp.name, r["primal_obj"], fs)

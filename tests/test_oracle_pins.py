@@ -437,3 +437,14 @@ def test_iterate_test_instances_amplify_rounding_little():
                W.random_qp(seed=4, factored=True)):
         assert _ulp_sensitivity(qp) < 1e-11
     assert _ulp_sensitivity(W.random_qp(seed=6, factored=True)) > 1e-10
+
+
+def test_golden_closed_forms():
+    # tests/golden/closed_form_qps.json: QPs solved by hand from the optimality
+    # conditions (equality-constrained, separable box, one active row)
+    from conftest import golden_closed_form_qps
+    for qp, xs, fs in golden_closed_form_qps():
+        x, y, r = oracle.solve(qp, oracle.default_params(eps_tol=1e-10, max_iter=1_000_000))
+        assert r["status_name"] == "OPTIMAL", (qp.name, r)
+        np.testing.assert_allclose(x, xs, atol=1e-8, err_msg=qp.name)
+        assert r["primal_obj"] == pytest.approx(fs, rel=1e-9, abs=1e-9), qp.name
