@@ -26,8 +26,11 @@
  *
  * Parity pins: see tests/test_oracle_pins.py (dense KKT LU, active-set brute
  * force, constructed infeasible and unbounded instances, SVD norm, subproblem
- * optimality).  Parity unpinned: iteration counts relative to the paper's own
- * release (no instance or trace is published).
+ * optimality, LASSO against coordinate descent, the factored objective against
+ * the explicitly formed one, factored scaling against scaling of a diagonal
+ * R^T R, hand-derived closed forms in tests/golden).  Parity unpinned:
+ * iteration counts relative to the paper's own release (no instance or trace
+ * is published).
  */
 #include <math.h>
 #include <stdint.h>
