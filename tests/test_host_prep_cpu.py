@@ -1,0 +1,143 @@
+"""The library's host-side SELL-C-sigma packing (csrc/host_prep.cpp), checked on
+the CPU against the CSR it packs.  The kernels rely on this layout:
+
+* rows whose longest matrix row exceeds 64 entries are "long" (warp per row),
+  those with 2048 or more are "huge" (CTA per row); the rest are "regular";
+* the permutation lists every regular row once, then -1 padding to whole slices
+  of 32, and inside each window of 1024 positions orders rows by their summed
+  length over both matrices, longest first, ties in row order;
+* slice s of matrix k is 32 x w_k(s) column-major, w_k(s) the longest row of
+  the slice in that matrix, ptr_k[s] its first element; lane l holds the row in
+  slot l, its column indices first, then zeros.
+"""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2602_23967_b300", "csrc")
+OUT = os.path.join(ROOT, "tests", "_build")
+SIGMA, LONG, HUGE = 1024, 64, 2048
+
+
+@pytest.fixture(scope="module")
+def shim():
+    os.makedirs(OUT, exist_ok=True)
+    lib = os.path.join(OUT, "libhostprep_shim.so")
+    srcs = [os.path.join(ROOT, "tests", "host_prep_shim.cpp"), os.path.join(CSRC, "host_prep.cpp")]
+    cmd = ["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+           "-I", "/usr/local/cuda/include", *srcs, "-o", lib]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    L = C.CDLL(lib)
+    L.shim_build_sell.restype = C.c_int
+    return L
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def pack(L, mats):
+    """Run build_sell on one or two CSR matrices with the same row count."""
+    rps = [np.ascontiguousarray(M.indptr, dtype=np.int32) for M in mats]
+    cis = [np.ascontiguousarray(M.indices, dtype=np.int32) for M in mats]
+    nrows = mats[0].shape[0]
+    two = len(mats) == 2
+    L.shim_build_sell(C.c_int32(nrows), _p(rps[0], C.c_int32), _p(cis[0], C.c_int32),
+                      _p(rps[1], C.c_int32) if two else None, _p(cis[1], C.c_int32) if two else None)
+    sz = np.zeros(6, dtype=np.int64)
+    L.shim_sizes(_p(sz, C.c_int64))
+    ns, nl, nh, c0, c1, p1 = (int(v) for v in sz)
+    perm = np.zeros(ns * 32, np.int32)
+    longs, huges = np.zeros(max(nl, 1), np.int32), np.zeros(max(nh, 1), np.int32)
+    ptr0, ptr1 = np.zeros(ns + 1, np.int64), np.zeros(max(p1, 1), np.int64)
+    col0, col1 = np.zeros(max(c0, 1), np.int32), np.zeros(max(c1, 1), np.int32)
+    L.shim_copy(_p(perm, C.c_int32), _p(longs, C.c_int32), _p(huges, C.c_int32), _p(ptr0, C.c_int64),
+                _p(ptr1, C.c_int64), _p(col0, C.c_int32), _p(col1, C.c_int32))
+    return dict(nslices=ns, perm=perm, longs=longs[:nl], huges=huges[:nh], ptr=[ptr0, ptr1[: ns + 1]],
+                col=[col0[:c0], col1[:c1]])
+
+
+def random_rows(rng, nrows, ncols, lengths):
+    rows = []
+    for r, ln in enumerate(lengths):
+        cols = np.sort(rng.choice(ncols, size=ln, replace=False))
+        rows.append(cols)
+    indptr = np.concatenate([[0], np.cumsum([len(c) for c in rows])])
+    indices = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    return sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(nrows, ncols))
+
+
+def check_layout(mats, out):
+    nrows = mats[0].shape[0]
+    lens = np.array([np.diff(M.indptr) for M in mats])        # nmat x nrows
+    mx, tot = lens.max(axis=0), lens.sum(axis=0)
+    huge = np.flatnonzero(mx >= HUGE)
+    long = np.flatnonzero((mx > LONG) & (mx < HUGE))
+    regular = np.flatnonzero(mx <= LONG)
+    assert sorted(out["huges"].tolist()) == huge.tolist()
+    assert sorted(out["longs"].tolist()) == long.tolist()
+    perm = out["perm"]
+    assert out["nslices"] == (len(regular) + 31) // 32
+    live = perm[: len(regular)]
+    assert np.all(perm[len(regular):] == -1)
+    assert sorted(live.tolist()) == regular.tolist()
+    # windows of sigma positions: non-increasing total length, ties in row order
+    for w0 in range(0, len(regular), SIGMA):
+        win = live[w0: w0 + SIGMA]
+        keys = list(zip(-tot[win], win))
+        assert keys == sorted(keys)
+    for k, M in enumerate(mats):
+        ptr, col = out["ptr"][k], out["col"][k]
+        assert ptr[0] == 0 and len(col) == ptr[-1]
+        for s in range(out["nslices"]):
+            slot = perm[32 * s: 32 * s + 32]
+            w = max((lens[k][r] for r in slot if r >= 0), default=0)
+            assert ptr[s + 1] - ptr[s] == 32 * w
+            block = col[ptr[s]: ptr[s + 1]].reshape(w, 32)    # column-major: entry j of lane l at 32 j + l
+            for l, r in enumerate(slot):
+                got = block[:, l]
+                if r < 0:
+                    assert np.all(got == 0)
+                    continue
+                ln = lens[k][r]
+                want = M.indices[M.indptr[r]: M.indptr[r + 1]]
+                assert np.array_equal(got[:ln], want)
+                assert np.all(got[ln:] == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sell_packing_one_matrix(shim, seed):
+    rng = np.random.default_rng(seed)
+    nrows, ncols = 2500, 4000
+    lengths = rng.integers(0, 20, nrows)
+    lengths[rng.integers(0, nrows)] = 100      # one long row
+    lengths[rng.integers(0, nrows)] = 3000     # one huge row
+    M = random_rows(rng, nrows, ncols, lengths)
+    check_layout([M], pack(shim, [M]))
+
+
+def test_sell_packing_two_matrices(shim):
+    # the variable space packs A^T and Q together: classification by the longer
+    # row, ordering by the summed length, one slice geometry per matrix
+    rng = np.random.default_rng(7)
+    nrows, ncols = 1500, 1500
+    l1 = rng.integers(0, 12, nrows)
+    l2 = rng.integers(0, 12, nrows)
+    l2[5] = 70                                  # long through the second matrix only
+    A = random_rows(rng, nrows, ncols, l1)
+    Q = random_rows(rng, nrows, ncols, l2)
+    check_layout([A, Q], pack(shim, [A, Q]))
+
+
+def test_sell_packing_tiny_and_empty_rows(shim):
+    rng = np.random.default_rng(3)
+    for nrows in (1, 31, 32, 33):
+        lengths = rng.integers(0, 3, nrows)
+        M = random_rows(rng, nrows, 10, lengths)
+        check_layout([M], pack(shim, [M]))
