@@ -1,6 +1,7 @@
 // host_prep_shim.cpp — test-only C entry points over the library's host-side
-// SELL-C-sigma packing (build_sell in paper_2602_23967_b300/csrc/host_prep.cpp),
-// so that a CPU test can check the layout the kernels read.  Built by
+// preparation (paper_2602_23967_b300/csrc/host_prep.cpp): the SELL-C-sigma
+// packing, the balanced split of rows over a group's CTAs and the lifting of
+// variable bounds into rows, so that a CPU test can check them.  Built by
 // tests/test_host_prep_cpu.py with g++; not part of the library.
 #include <cstring>
 #include <vector>
@@ -53,6 +54,51 @@ void shim_copy(int32_t* perm, int32_t* longs, int32_t* huges, int64_t* ptr0, int
   std::memcpy(ptr1, g_sell.ptr[1].data(), sizeof(int64_t) * g_sell.ptr[1].size());
   std::memcpy(col0, g_sell.col[0].data(), sizeof(int32_t) * g_sell.col[0].size());
   std::memcpy(col1, g_sell.col[1].data(), sizeof(int32_t) * g_sell.col[1].size());
+}
+
+// Balanced contiguous split of n weights into nblk ranges; bounds: nblk + 1.
+void shim_split_balanced(const int64_t* w, int32_t n, int32_t nblk, int32_t* bounds) {
+  const std::vector<int64_t> wv(w, w + n);
+  const std::vector<int32_t> b = pdhcg::split_balanced(wv, nblk);
+  std::memcpy(bounds, b.data(), sizeof(int32_t) * b.size());
+}
+
+namespace {
+pdhcg::HostQP g_qp;
+}
+
+// Validate a problem (Q may be NULL) and lift its finite variable bounds into
+// rows (the CG_LIFTED reading).  Returns the library's status code.
+int shim_lift(const pdhcg_csr* Q, const pdhcg_csr* A, const double* c, const double* lc, const double* uc,
+              const double* lv, const double* uv) {
+  g_qp = pdhcg::HostQP{};
+  const int rc = pdhcg::build_host_qp(Q, A, c, lc, uc, lv, uv, &g_qp);
+  if (rc) return rc;
+  pdhcg::lift_box_rows(&g_qp);
+  return 0;
+}
+
+// sizes[0..2]: m after lifting, nnz(A), m_user
+void shim_lift_sizes(int64_t* sizes) {
+  sizes[0] = g_qp.m;
+  sizes[1] = int64_t(g_qp.Ac.size());
+  sizes[2] = g_qp.m_user;
+}
+
+// Lifted A (CSR) and A^T (CSR), row bounds, variable bounds and types.
+void shim_lift_copy(int32_t* Ap, int32_t* Ac, double* Av, int32_t* ATp, int32_t* ATc, double* ATv, double* lc,
+                    double* uc, double* lv, double* uv, int8_t* vtype) {
+  std::memcpy(Ap, g_qp.Ap.data(), sizeof(int32_t) * g_qp.Ap.size());
+  std::memcpy(Ac, g_qp.Ac.data(), sizeof(int32_t) * g_qp.Ac.size());
+  std::memcpy(Av, g_qp.Av.data(), sizeof(double) * g_qp.Av.size());
+  std::memcpy(ATp, g_qp.ATp.data(), sizeof(int32_t) * g_qp.ATp.size());
+  std::memcpy(ATc, g_qp.ATc.data(), sizeof(int32_t) * g_qp.ATc.size());
+  std::memcpy(ATv, g_qp.ATv.data(), sizeof(double) * g_qp.ATv.size());
+  std::memcpy(lc, g_qp.lc.data(), sizeof(double) * g_qp.lc.size());
+  std::memcpy(uc, g_qp.uc.data(), sizeof(double) * g_qp.uc.size());
+  std::memcpy(lv, g_qp.lv.data(), sizeof(double) * g_qp.lv.size());
+  std::memcpy(uv, g_qp.uv.data(), sizeof(double) * g_qp.uv.size());
+  std::memcpy(vtype, g_qp.vtype.data(), g_qp.vtype.size());
 }
 
 }  // extern "C"

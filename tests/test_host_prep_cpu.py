@@ -1,5 +1,7 @@
-"""The library's host-side SELL-C-sigma packing (csrc/host_prep.cpp), checked on
-the CPU against the CSR it packs.  The kernels rely on this layout:
+"""The library's host-side preparation (csrc/host_prep.cpp), checked on the CPU
+through a test-only shim: the balanced split of rows over a group's CTAs, the
+lifting of variable bounds into rows (reading D1's CG_LIFTED), and the
+SELL-C-sigma packing, against the CSR it packs.  The kernels rely on this layout:
 
 * rows whose longest matrix row exceeds 64 entries are "long" (warp per row),
   those with 2048 or more are "huge" (CTA per row); the rest are "regular";
@@ -141,3 +143,56 @@ def test_sell_packing_tiny_and_empty_rows(shim):
         lengths = rng.integers(0, 3, nrows)
         M = random_rows(rng, nrows, 10, lengths)
         check_layout([M], pack(shim, [M]))
+
+
+@pytest.mark.parametrize("nblk", [1, 3, 7, 64])
+def test_split_balanced_ranges(shim, nblk):
+    # contiguous ranges, each within one largest item of total / nblk (an item
+    # goes to the range that holds the midpoint of its prefix-sum interval)
+    rng = np.random.default_rng(nblk)
+    w = np.ascontiguousarray((rng.pareto(1.5, 5000) * 10 + 1).astype(np.int64))
+    b = np.zeros(nblk + 1, np.int32)
+    shim.shim_split_balanced(_p(w, C.c_int64), C.c_int32(len(w)), C.c_int32(nblk), _p(b, C.c_int32))
+    assert b[0] == 0 and b[-1] == len(w) and np.all(np.diff(b) >= 0)
+    share, wmax = w.sum() / nblk, w.max()
+    for k in range(nblk):
+        assert abs(w[b[k]: b[k + 1]].sum() - share) <= wmax
+
+
+def test_lift_box_rows(shim):
+    # the CG_LIFTED reading: one row e_j^T per variable with a finite bound, in
+    # variable order, carrying that variable's bounds; every variable then free
+    from paper_2602_23967_b300 import pdhcg
+    rng = np.random.default_rng(4)
+    n, m = 12, 5
+    A = sp.random(m, n, density=0.4, random_state=rng, format="csr")
+    lv = np.where(rng.random(n) < 0.5, -rng.random(n), -np.inf)
+    uv = np.where(rng.random(n) < 0.5, rng.random(n) + 1, np.inf)
+    lc, uc = -np.ones(m), np.ones(m)
+    c = rng.normal(size=n)
+    indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(A.indices, dtype=np.int32)
+    data = np.ascontiguousarray(A.data, dtype=np.float64)
+    As = pdhcg.Csr(m, n, A.nnz, indptr.ctypes.data, indices.ctypes.data, data.ctypes.data)
+    rc = shim.shim_lift(None, C.byref(As), _p(c, C.c_double), _p(lc, C.c_double), _p(uc, C.c_double),
+                        _p(lv, C.c_double), _p(uv, C.c_double))
+    assert rc == 0
+    sz = np.zeros(3, np.int64)
+    shim.shim_lift_sizes(_p(sz, C.c_int64))
+    m2, nnz2, m_user = (int(v) for v in sz)
+    boxed = np.flatnonzero(np.isfinite(lv) | np.isfinite(uv))
+    assert m2 == m + len(boxed) and m_user == m and nnz2 == A.nnz + len(boxed)
+    Ap, Ac, Av = np.zeros(m2 + 1, np.int32), np.zeros(nnz2, np.int32), np.zeros(nnz2)
+    ATp, ATc, ATv = np.zeros(n + 1, np.int32), np.zeros(nnz2, np.int32), np.zeros(nnz2)
+    lc2, uc2, lv2, uv2 = np.zeros(m2), np.zeros(m2), np.zeros(n), np.zeros(n)
+    vt = np.zeros(n, np.int8)
+    shim.shim_lift_copy(_p(Ap, C.c_int32), _p(Ac, C.c_int32), _p(Av, C.c_double), _p(ATp, C.c_int32),
+                        _p(ATc, C.c_int32), _p(ATv, C.c_double), _p(lc2, C.c_double), _p(uc2, C.c_double),
+                        _p(lv2, C.c_double), _p(uv2, C.c_double), _p(vt, C.c_int8))
+    lifted = sp.csr_matrix((Av, Ac, Ap), shape=(m2, n)).toarray()
+    expect = np.vstack([A.toarray(), np.eye(n)[boxed]])
+    np.testing.assert_array_equal(lifted, expect)
+    np.testing.assert_array_equal(sp.csr_matrix((ATv, ATc, ATp), shape=(n, m2)).toarray(), expect.T)
+    np.testing.assert_array_equal(lc2, np.concatenate([lc, lv[boxed]]))
+    np.testing.assert_array_equal(uc2, np.concatenate([uc, uv[boxed]]))
+    assert np.all(np.isneginf(lv2)) and np.all(np.isposinf(uv2)) and np.all(vt == 0)
