@@ -109,9 +109,9 @@ typedef struct {
   double restart_sufficient;  /* restart if FPR <= this * FPR(anchor) (0.2)                  */
   double restart_necessary;   /* ... or FPR <= this * FPR(anchor) and FPR grew (0.8)         */
   double restart_artificial;  /* ... or round length >= this * total steps (0.36)            */
-  int32_t power_max_iter;     /* power iteration for ||A||_2 (1000)                          */
+  int32_t power_max_iter;     /* cap on Lanczos steps of the ||A||_2 estimate (1000)         */
   int32_t lanes_override;     /* force lanes per CSR row (1..32, power of 2); 0 = tuned      */
-  double power_tol;           /* relative change stopping the power iteration (1e-8)         */
+  double power_tol;           /* relative change of the ||A||_2 estimate that stops it (1e-8)*/
   double eta_override;        /* > 0: use this eta instead of 0.998/||A||                    */
   double omega0_override;     /* > 0: use this initial primal weight                         */
   double omega_clamp;         /* omega kept within [omega0/c, omega0*c] (1e5)                */
@@ -129,7 +129,7 @@ typedef struct {
   double primal_obj, dual_obj;
   double eta, omega, norm_A;  /* step size, final primal weight, ||A||_2 estimate (scaled) */
   double solve_seconds;       /* device-timer duration of the solve                          */
-  int32_t power_iters;
+  int32_t power_iters;        /* Lanczos steps taken by the ||A||_2 estimate                 */
   int32_t precision;
   double latency_seconds;     /* serving loop: pdhcg_submit to result ready (wall clock); 0 otherwise */
 } pdhcg_result;
