@@ -108,3 +108,17 @@ def test_rejects_malformed_structured_objective():
     # the batched creation takes plain Q only
     with pytest.raises(ValueError):
         pdhcg.create_batch([factored()], pdhcg.default_params())
+
+
+def test_empty_batches_and_negative_counts():
+    # a batch of zero problems is a no-op for every batched entry point, and a
+    # negative count is rejected; neither touches the device
+    assert pdhcg.create_batch([], pdhcg.default_params()) == []
+    assert pdhcg.solve_batch([]) == []
+    assert pdhcg.solve_batch([], want_solutions=False) == []
+    assert pdhcg.solve_batch_noalloc([]) == []
+    L = pdhcg.lib()
+    res = (pdhcg.Result * 1)()
+    handles = (C.c_void_p * 1)()
+    assert L.pdhcg_solve_batch(handles, -1, res, None, None) == pdhcg.E_INVALID
+    assert L.pdhcg_solve_batch_noalloc(handles, -1, res, None, None) == pdhcg.E_INVALID
