@@ -519,7 +519,7 @@ def run_ours(args):
 
 
 def run_ablation_inner_tolerance(args):
-    """Sec. 6.3's question on this build: outer steps, inner steps and device time
+    """Sec. 6.3's question on these synthetic inputs: outer steps, inner steps and device time
     to relative KKT 1e-6 with the adaptive inner tolerance of Sec. 3.3 against
     fixed inner tolerances (gamma = 0: eps_k = eps_min from the second step)."""
     import torch
