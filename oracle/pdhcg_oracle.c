@@ -28,7 +28,10 @@
  * force, constructed infeasible and unbounded instances, SVD norm, subproblem
  * optimality, LASSO against coordinate descent, the factored objective against
  * the explicitly formed one, factored scaling against scaling of a diagonal
- * R^T R, hand-derived closed forms in tests/golden).  Parity unpinned:
+ * R^T R, hand-derived closed forms in tests/golden, and a hand-derived trace of
+ * the first four steps on a one-variable QP that fixes the adaptive inner
+ * tolerance, the reflected Halpern weights and the step sizes, plus a point
+ * where only the gap term of Sec. 4.2 is nonzero).  Parity unpinned:
  * iteration counts relative to the paper's own release (no instance or trace
  * is published).
  */
@@ -772,7 +775,10 @@ static int solve_impl(int32_t n, int32_t m, const oracle_csr* Q, const oracle_cs
         }
       }
       if (!status) {
-        /* dual: d = Delta x / ||Delta x||_inf (Sec. 5.2) */
+        /* dual: d = Delta x / ||Delta x||_inf (Sec. 5.2).  Reading: the printed
+         * formula normalises Delta x itself; "projected" in the text refers to
+         * x+ being the projection onto X, since projecting Delta x onto
+         * Recc(X) would make the first term of the test vanish identically. */
         for (int32_t j = 0; j < n; ++j) dd[j] = xp[j] - x[j];
         double dn = norminf(dd, n);
         if (dn > 0.0) {

@@ -380,3 +380,25 @@ def test_golden_closed_forms_on_gpu(precision):
         assert r["status_name"] == "OPTIMAL", (qp.name, r)
         np.testing.assert_allclose(x, xs, atol=1e-7, err_msg=qp.name)
         assert rel(r["primal_obj"], fs) <= 1e-8, (qp.name, r["primal_obj"], fs)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat"])
+def test_golden_step_trace_on_gpu(precision):
+    # tests/golden/step_trace_1d.json on the CUDA path: T(z) after K = 1..4
+    # steps, derived by hand, depends on the reflected Halpern weights and theta
+    # (Sec. 3.1), the step sizes tau = eta/omega and sigma = eta*omega (Sec. 3.2)
+    # and the dual update; FP64 to 1e-14, double-float vectors to 1e-12
+    from conftest import golden_step_trace
+    g = golden_step_trace()
+    tol = 1e-14 if precision == "fp64" else 1e-12
+    for case in g["cases"]:
+        for K, (xs, ys) in case["outputs"].items():
+            prob = pdhcg.Problem(g["qp"], pdhcg.default_params(precision=precision, max_iter=K,
+                                                               theta=case["theta"], **g["settings"]))
+            try:
+                x, y, r = prob.solve(x0=g["x0"], y0=g["y0"])
+            finally:
+                prob.close()
+            assert r["status_name"] == "ITERATION_LIMIT" and r["iterations"] == K, r
+            np.testing.assert_allclose(x, xs, rtol=tol, err_msg=f"theta={case['theta']} K={K}")
+            np.testing.assert_allclose(y, ys, rtol=tol, err_msg=f"theta={case['theta']} K={K}")

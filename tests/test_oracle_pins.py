@@ -448,3 +448,40 @@ def test_golden_closed_forms():
         assert r["status_name"] == "OPTIMAL", (qp.name, r)
         np.testing.assert_allclose(x, xs, atol=1e-8, err_msg=qp.name)
         assert r["primal_obj"] == pytest.approx(fs, rel=1e-9, abs=1e-9), qp.name
+
+
+def test_golden_step_trace_inner_tolerance_and_halpern():
+    # tests/golden/step_trace_1d.json: the first four steps on a one-variable QP,
+    # derived by hand in exact fractions.  eps_k pins the adaptive inner
+    # tolerance of Sec. 3.3 (the gamma * omega * movement / tau term, the
+    # running min and the first tolerance); T(z_k) after K = 2..4 steps depends
+    # on the reflected Halpern weights (k+1)/(k+2), 1/(k+2) and theta of
+    # Sec. 3.1 through the iterate z_k it is taken at.
+    from conftest import golden_step_trace
+    g = golden_step_trace()
+    for case in g["cases"]:
+        prm = dict(g["settings"], theta=case["theta"])
+        _, _, r, tr = oracle.solve(g["qp"], oracle.default_params(max_iter=len(case["eps_trace"]), **prm),
+                                   x0=g["x0"], y0=g["y0"], eps_trace_len=len(case["eps_trace"]))
+        np.testing.assert_allclose(tr, case["eps_trace"], rtol=1e-14, atol=0)
+        for K, (xs, ys) in case["outputs"].items():
+            x, y, r = oracle.solve(g["qp"], oracle.default_params(max_iter=K, **prm), x0=g["x0"], y0=g["y0"])
+            assert r["status_name"] == "ITERATION_LIMIT" and r["iterations"] == K
+            np.testing.assert_allclose(x, xs, rtol=1e-14, err_msg=f"theta={case['theta']} K={K}")
+            np.testing.assert_allclose(y, ys, rtol=1e-14, err_msg=f"theta={case['theta']} K={K}")
+
+
+def test_golden_gap_term():
+    # Sec. 4.2 at a primal- and dual-feasible point that is not optimal: only
+    # the gap term is nonzero, so its numerator (x^T Q x + c^T x + p(-r) + p(y))
+    # and denominator are pinned separately from the other residuals
+    from conftest import golden_step_trace
+    gp = golden_step_trace()["gap"]
+    qp, x, y, e = gp["qp"], gp["x"], gp["y"], gp["expect"]
+    Q, A = dense(qp.Q), dense(qp.A)
+    rp, rd, rg, pobj, dobj = oracle.kkt(qp.n, qp.m, x, y, A @ x, A.T @ y, Q @ x, qp.c, qp.lc, qp.uc,
+                                        qp.lv, qp.uv)
+    assert rp == e["r_primal"] and rd == e["r_dual"]
+    assert rg == pytest.approx(e["r_gap"], rel=1e-15)
+    assert pobj == pytest.approx(e["primal_obj"], abs=1e-15)
+    assert dobj == pytest.approx(e["dual_obj"], rel=1e-15)
