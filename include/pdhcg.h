@@ -223,7 +223,9 @@ int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result* res, doubl
  *   states and descriptors) before its launch.
  * Set-up: the first call on each device looks up the scratch's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
- *   any stream capture on that device.
+ *   any stream capture on that device.  The call copies from host memory and
+ *   synchronises its stream, so it must not be called while that stream is
+ *   being captured into a CUDA graph.
  * Concurrency: the scratch is one per device per process, so overlapping calls
  *   would race on it; the library serialises calls on a process-wide lock.
  * Results equal pdhcg_solve_batch's for the same handles. */
@@ -239,6 +241,9 @@ int pdhcg_get_scaling(const pdhcg_t* prob, double* D, double* E);
 
 /* Sizes of a handle: n, m, device bytes held. */
 int pdhcg_get_info(const pdhcg_t* prob, int32_t* n, int32_t* m, size_t* device_bytes);
+
+/* CUDA device ordinal the handle's data lives on (the device current at create). */
+int pdhcg_get_device(const pdhcg_t* prob, int32_t* device);
 
 /* Profiling aid: device-timer seconds of the last pdhcg_solve / pdhcg_solve_dev
  * on this handle, as seen by one thread of the first CTA, split into 8

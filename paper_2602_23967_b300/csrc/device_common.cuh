@@ -374,18 +374,24 @@ __device__ __forceinline__ int64_t ldm64(const int64_t* p) {
 }
 
 // Shared context of the row engine for one CTA.
+constexpr int kRowSums = 8;  // most row sums one space_rows call produces
 struct RowCtx {
-  double* red;  // BS/32 * 4 doubles of shared scratch (huge-row reductions)
+  double* red;  // BS/32 * kRowSums doubles of shared scratch (huge-row reductions)
 };
 
 // A product source: matrix in SELL form (regular rows) and CSR form (long and
-// huge rows), with NG gathers (0, 1 or 2) of the column index.
+// huge rows), with NG gathers (0, 1 or 2) of the column index.  With LO the
+// source also sums the products of the values' rounding remainders (Sell::lo,
+// Csr::lo) with the same gathers: it then yields 2 NG sums, the NG products
+// with the values first, then the NG products with the remainders.
 struct NoGather {
   __device__ __forceinline__ float operator()(int) const { return 0.f; }
 };
-template <class MatT, int NGv, class G1, class G2>
+template <class MatT, int NGv, class G1, class G2, bool LOv = false>
 struct RowSrc {
   static constexpr int NG = NGv;
+  static constexpr bool LO = LOv;
+  static constexpr int NSUM = NGv * (LOv ? 2 : 1);
   using mat_type = MatT;
   Sell<MatT> S;
   Csr<MatT> M;
@@ -403,6 +409,17 @@ __device__ __forceinline__ RowSrc<MatT, 2, G1, G2> src2(const Sell<MatT>& S, con
                                                         G2 g2, bool on = true) {
   return RowSrc<MatT, 2, G1, G2>{S, M, g1, g2, on};
 }
+// The same with the remainder products (LO); the caller ensures S.lo and M.lo are set.
+template <bool LO, class MatT, class G1>
+__device__ __forceinline__ RowSrc<MatT, 1, G1, NoGather, LO> src_lo(const Sell<MatT>& S, const Csr<MatT>& M,
+                                                                   G1 g1, bool on = true) {
+  return RowSrc<MatT, 1, G1, NoGather, LO>{S, M, g1, NoGather{}, on};
+}
+template <bool LO, class MatT, class G1, class G2>
+__device__ __forceinline__ RowSrc<MatT, 2, G1, G2, LO> src2_lo(const Sell<MatT>& S, const Csr<MatT>& M, G1 g1,
+                                                              G2 g2, bool on = true) {
+  return RowSrc<MatT, 2, G1, G2, LO>{S, M, g1, g2, on};
+}
 template <class MatT>
 __device__ __forceinline__ RowSrc<MatT, 0, NoGather, NoGather> nosrc() {
   return RowSrc<MatT, 0, NoGather, NoGather>{Sell<MatT>{}, Csr<MatT>{}, NoGather{}, NoGather{}, false};
@@ -419,7 +436,7 @@ __device__ __forceinline__ RowSrc<MatT, 0, NoGather, NoGather> nosrc() {
 template <Ld LM>
 __host__ __device__ constexpr int slice_unroll() { return LM == Ld::Stream ? PDHCG_GROUP_SLICE_UNROLL : PDHCG_SLICE_UNROLL; }
 
-// Accumulate slot `lane` of slice s of source X into sums[0..NG) in column order.
+// Accumulate slot `lane` of slice s of source X into sums[0..NSUM) in column order.
 template <Ld LM, class Acc, class X>
 __device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums) {
   if constexpr (X::NG > 0) {
@@ -428,12 +445,30 @@ __device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums
     const int W = int((e - b) >> 5);
     const int* cp = x.S.col + b + lane;
     const auto* vp = x.S.val + b + lane;
+    if constexpr (X::LO) {
+      const float* lp = x.S.lo + b + lane;
 #pragma unroll slice_unroll<LM>()
-    for (int j = 0; j < W; ++j) {
-      const int c = ldm<LM>(cp + 32 * j);
-      const auto v = ldm<LM>(vp + 32 * j);
-      madd(sums[0], v, Acc(x.g1(c)));
-      if constexpr (X::NG == 2) madd(sums[1], v, Acc(x.g2(c)));
+      for (int j = 0; j < W; ++j) {
+        const int c = ldm<LM>(cp + 32 * j);
+        const auto v = ldm<LM>(vp + 32 * j);
+        const float l = ldm<LM>(lp + 32 * j);
+        const Acc a1 = Acc(x.g1(c));
+        madd(sums[0], v, a1);
+        madd(sums[X::NG], l, a1);
+        if constexpr (X::NG == 2) {
+          const Acc a2 = Acc(x.g2(c));
+          madd(sums[1], v, a2);
+          madd(sums[3], l, a2);
+        }
+      }
+    } else {
+#pragma unroll slice_unroll<LM>()
+      for (int j = 0; j < W; ++j) {
+        const int c = ldm<LM>(cp + 32 * j);
+        const auto v = ldm<LM>(vp + 32 * j);
+        madd(sums[0], v, Acc(x.g1(c)));
+        if constexpr (X::NG == 2) madd(sums[1], v, Acc(x.g2(c)));
+      }
     }
   }
 }
@@ -509,19 +544,29 @@ __device__ __forceinline__ void csr_part(const X& x, int row, int first, int ste
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (k0 + u * step < e) madd(sums[0], v[u], g1v[u]);
+      if constexpr (X::LO) {
+        // remainder products, same order (the gathers are reloaded: long rows are few)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u * step < e) {
+            const float l = ldm<LM>(x.M.lo + k0 + u * step);
+            madd(sums[X::NG], l, g1v[u]);
+            if constexpr (X::NG == 2) madd(sums[3], l, Acc(x.g2(c[u])));
+          }
+      }
     }
   }
 }
 
 // Walk this CTA's share of a row space and call epi(row, const Acc* sums) once
-// per row; sums holds the A gathers then the B gathers.  part_rank < 0: the
-// whole space (single-CTA group).  red: BS/32 * 4 doubles of shared scratch.
+// per row; sums holds the A sums then the B sums.  part_rank < 0: the
+// whole space (single-CTA group).  red: BS/32 * kRowSums doubles of shared scratch.
 template <int BS, Ld LM, class Acc, class SA, class SB, class Epi>
 __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank, const SA& A,
                                         const SB& B, const RowCtx& rc, Epi epi) {
   double* red = rc.red;
-  constexpr int NA = SA::NG, NB = SB::NG, NS = NA + NB;
-  static_assert(NS >= 1 && NS <= 4, "1..4 sums per row");
+  constexpr int NA = SA::NSUM, NB = SB::NSUM, NS = NA + NB;
+  static_assert(NS >= 1 && NS <= kRowSums, "1..kRowSums sums per row");
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int s0 = 0, s1 = sp.nslices, l0 = 0, l1 = sp.nlong, h0 = 0, h1 = sp.nhuge;
@@ -601,7 +646,7 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
       acc_finish(sums[q]);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sums[q] += shfl_xor(sums[q], off);
-      if (lane == 0) red[warp * 4 + q] = double(sums[q]);
+      if (lane == 0) red[warp * kRowSums + q] = double(sums[q]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -609,7 +654,7 @@ __device__ __forceinline__ void space_rows(const SpaceLayout& sp, int part_rank,
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         tot[q] = Acc(0);
-        for (int w = 0; w < NW; ++w) tot[q] += Acc(red[w * 4 + q]);
+        for (int w = 0; w < NW; ++w) tot[q] += Acc(red[w * kRowSums + q]);
       }
       epi(row, tot);
     }

@@ -141,6 +141,10 @@ struct pdhcg_problem {
   int32_t *Rp_d = nullptr, *Rc_d = nullptr;
   double* Rv_o = nullptr;
   void* Rs = nullptr;               // MatT, scaled R D
+  // FP32 matrix values only: rounding remainders of the scaled values (float),
+  // CSR order and SELL order (null in FP64 mode)
+  float *Qs_lo = nullptr, *As_lo = nullptr, *ATs_lo = nullptr, *Rs_lo = nullptr;
+  float *sQv_lo = nullptr, *sAv_lo = nullptr, *sATv_lo = nullptr, *sRv_lo = nullptr;
   void *rt1 = nullptr, *rt2 = nullptr;  // VecT, R v products (k each)
   // device SELL arrays
   int32_t *v_perm = nullptr, *v_longs = nullptr, *v_huges = nullptr;

@@ -131,6 +131,18 @@ void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
     P->rt1 = cv.take_bytes(size_t(P->k), vb);
     P->rt2 = cv.take_bytes(size_t(P->k), vb);
   }
+  if (mb == 4) {  // FP32 matrix values: their rounding remainders (FP64-accurate checks)
+    P->Qs_lo = cv.take<float>(nq);
+    P->As_lo = cv.take<float>(na);
+    P->ATs_lo = cv.take<float>(na);
+    P->sATv_lo = cv.take<float>(P->vsell_cols[0] + 16);
+    P->sQv_lo = cv.take<float>(P->vsell_cols[1] + 16);
+    P->sAv_lo = cv.take<float>(P->csell_cols + 16);
+    if (P->k > 0) {
+      P->Rs_lo = cv.take<float>(size_t(P->nnzR));
+      P->sRv_lo = cv.take<float>(P->rsell_cols + 16);
+    }
+  }
   P->D = cv.take<double>(n);
   P->E = cv.take<double>(m);
   P->Dn = cv.take<double>(n);
@@ -361,12 +373,12 @@ Inst<MatT, VecT> make_inst(const pdhcg_problem* P) {
   I.has_q = P->has_q ? 1 : 0;
   I.lanes_var = P->lanes_var;
   I.lanes_con = P->lanes_con;
-  I.Q = Csr<MatT>{P->n, int32_t(P->nnzQ), P->Qp_d, P->Qc_d, static_cast<const MatT*>(P->Qs)};
-  I.A = Csr<MatT>{P->m, int32_t(P->nnzA), P->Ap_d, P->Ac_d, static_cast<const MatT*>(P->As)};
-  I.AT = Csr<MatT>{P->n, int32_t(P->nnzA), P->ATp_d, P->ATc_d, static_cast<const MatT*>(P->ATs)};
-  I.ATs = Sell<MatT>{P->sATp, P->sATc, static_cast<const MatT*>(P->sATv)};
-  I.Qs = Sell<MatT>{P->sQp, P->sQc, static_cast<const MatT*>(P->sQv)};
-  I.As = Sell<MatT>{P->sAp, P->sAc, static_cast<const MatT*>(P->sAv)};
+  I.Q = Csr<MatT>{P->n, int32_t(P->nnzQ), P->Qp_d, P->Qc_d, static_cast<const MatT*>(P->Qs), P->Qs_lo};
+  I.A = Csr<MatT>{P->m, int32_t(P->nnzA), P->Ap_d, P->Ac_d, static_cast<const MatT*>(P->As), P->As_lo};
+  I.AT = Csr<MatT>{P->n, int32_t(P->nnzA), P->ATp_d, P->ATc_d, static_cast<const MatT*>(P->ATs), P->ATs_lo};
+  I.ATs = Sell<MatT>{P->sATp, P->sATc, static_cast<const MatT*>(P->sATv), P->sATv_lo};
+  I.Qs = Sell<MatT>{P->sQp, P->sQc, static_cast<const MatT*>(P->sQv), P->sQv_lo};
+  I.As = Sell<MatT>{P->sAp, P->sAc, static_cast<const MatT*>(P->sAv), P->sAv_lo};
   I.vsp.nslices = P->vsell.nslices;
   I.vsp.nlong = int32_t(P->vsell.longs.size());
   I.vsp.nhuge = int32_t(P->vsell.huges.size());
@@ -379,11 +391,11 @@ Inst<MatT, VecT> make_inst(const pdhcg_problem* P) {
   I.csp.perm = P->c_perm;
   I.csp.longs = P->c_longs;
   I.csp.huges = P->c_huges;
-  I.c = static_cast<const VecT*>(P->c);
+  I.c = static_cast<VecT*>(P->c);
   I.lv = static_cast<const VecT*>(P->lv);
   I.uv = static_cast<const VecT*>(P->uv);
-  I.lc = static_cast<const VecT*>(P->lc);
-  I.uc = static_cast<const VecT*>(P->uc);
+  I.lc = static_cast<VecT*>(P->lc);
+  I.uc = static_cast<VecT*>(P->uc);
   I.qdiag = static_cast<const VecT*>(P->qdiag);
   I.vtype = P->vtype;
   I.ctype = P->ctype;
@@ -417,8 +429,8 @@ Inst<MatT, VecT> make_inst(const pdhcg_problem* P) {
   I.prm = dev_params(P->prm);
   if (P->k > 0) {
     I.k = P->k;
-    I.R = Csr<MatT>{P->k, int32_t(P->nnzR), P->Rp_d, P->Rc_d, static_cast<const MatT*>(P->Rs)};
-    I.Rsl = Sell<MatT>{P->sRp, P->sRc, static_cast<const MatT*>(P->sRv)};
+    I.R = Csr<MatT>{P->k, int32_t(P->nnzR), P->Rp_d, P->Rc_d, static_cast<const MatT*>(P->Rs), P->Rs_lo};
+    I.Rsl = Sell<MatT>{P->sRp, P->sRc, static_cast<const MatT*>(P->sRv), P->sRv_lo};
     I.rsp.nslices = P->rsell.nslices;
     I.rsp.nlong = int32_t(P->rsell.longs.size());
     I.rsp.nhuge = int32_t(P->rsell.huges.size());
@@ -616,6 +628,14 @@ SetupArgs<M, V> make_setup_args(const pdhcg_problem* P, const PartitionSet* ps) 
   a.sATv = static_cast<M*>(P->sATv);
   a.sQv = static_cast<M*>(P->sQv);
   a.sAv = static_cast<M*>(P->sAv);
+  a.Qs_lo = P->Qs_lo;
+  a.As_lo = P->As_lo;
+  a.ATs_lo = P->ATs_lo;
+  a.sATv_lo = P->sATv_lo;
+  a.sQv_lo = P->sQv_lo;
+  a.sAv_lo = P->sAv_lo;
+  a.Rs_lo = P->Rs_lo;
+  a.sRv_lo = P->sRv_lo;
   if (P->k > 0) {
     a.k = P->k;
     a.Rp = P->Rp_d;
@@ -1252,6 +1272,12 @@ int pdhcg_get_info(const pdhcg_t* P, int32_t* n, int32_t* m, size_t* bytes) {
   return PDHCG_OK;
 }
 
+int pdhcg_get_device(const pdhcg_t* P, int32_t* device) {
+  if (!P || !device) return PDHCG_E_INVALID;
+  *device = P->device;
+  return PDHCG_OK;
+}
+
 void pdhcg_destroy(pdhcg_t* P) {
   if (!P) return;
   cudaSetDevice(P->device);
@@ -1546,6 +1572,13 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
   // queue cursor the CTAs advance atomically, [count + 1] the device error flag.
   for (size_t w = size_t(count); w < kNoAllocQueueWords; ++w) g_noalloc_horder[w] = 0;
 
+  // Once the kernel is enqueued, every exit waits for the stream first, so the
+  // scratch is idle whenever the lock is released (also on an error path).
+  bool launched = false;
+  auto fail = [&](cudaError_t e, const char* where) {
+    if (launched) (void)cudaStreamSynchronize(s);
+    return cuda_fail(e, where);
+  };
   rc = dispatch_precision(P0->precision, [&](auto tag) {
     using M = typename decltype(tag)::Mat;
     using V = typename decltype(tag)::Vec;
@@ -1582,17 +1615,24 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
     const int grid = std::max(1, std::min(count, per_sm * sms));
     cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "solve_batch_noalloc launch");
-    CK(cudaMemcpyAsync(g_noalloc_hstate, d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
+    launched = true;
+    e = cudaMemcpyAsync(g_noalloc_hstate, d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail(e, "solve_batch_noalloc: state read-back");
     return PDHCG_OK;
   });
   if (rc) return rc;
   for (int i = 0; i < count; ++i)
-    if (y_out_dev && y_out_dev[i] && probs[i]->m_user && probs[i]->m_user != probs[i]->m)
-      CK(cudaMemcpyAsync(y_out_dev[i], probs[i]->y_stage, sizeof(double) * size_t(probs[i]->m_user),
-                         cudaMemcpyDeviceToDevice, s));
+    if (y_out_dev && y_out_dev[i] && probs[i]->m_user && probs[i]->m_user != probs[i]->m) {
+      const cudaError_t e = cudaMemcpyAsync(y_out_dev[i], probs[i]->y_stage, sizeof(double) * size_t(probs[i]->m_user),
+                                            cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return fail(e, "solve_batch_noalloc: dual copy");
+    }
   // Returns only after the launch and the state read-back finished, so the next
   // call (which holds the same lock) never overwrites scratch in use.
-  CK(cudaStreamSynchronize(s));
+  {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_batch_noalloc: stream synchronize");
+  }
   bool dev_err = false;
   for (int i = 0; i < count; ++i) {
     if (g_noalloc_hstate[i].device_error) dev_err = true;

@@ -52,6 +52,10 @@ struct SolverState {
   int32_t device_error; // a bounded device wait gave up
 };
 
+// With FP32 matrix values, lo holds each scaled value's rounding remainder
+// float(v - double(float(v))), so val + lo reproduces the FP64 value to about
+// 2^-48 relative (used by the KKT checks and the defect correction); null in
+// FP64 mode.
 template <class T>
 struct Csr {
   int32_t nrows = 0;
@@ -59,6 +63,7 @@ struct Csr {
   const int32_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const T* val = nullptr;
+  const float* lo = nullptr;
 };
 
 // SELL-C-sigma slices (C = 32 rows, one per lane) of one matrix of a row space.
@@ -69,6 +74,7 @@ struct Sell {
   const int64_t* ptr = nullptr;  // nslices + 1
   const int32_t* col = nullptr;
   const T* val = nullptr;
+  const float* lo = nullptr;     // remainders in slice order (see Csr)
 };
 
 // Row space (the n variable rows, or the m constraint rows) in SELL form.
@@ -108,9 +114,11 @@ struct Inst {
   SpaceLayout rsp;
   VecT* rt1 = nullptr;
   VecT* rt2 = nullptr;
-  // scaled problem data
-  const VecT *c = nullptr, *lv = nullptr, *uv = nullptr, *lc = nullptr, *uc = nullptr,
-             *qdiag = nullptr;
+  // scaled problem data.  With FP32 matrix values c, lc and uc are the
+  // defect-corrected copies the iteration reads (reset from c_o, lc_o, uc_o at
+  // the start of a solve, shifted at every check).
+  VecT *c = nullptr, *lc = nullptr, *uc = nullptr;
+  const VecT *lv = nullptr, *uv = nullptr, *qdiag = nullptr;
   const int8_t *vtype = nullptr, *ctype = nullptr;
   // original-space data for the KKT residuals (double)
   const double *D = nullptr, *E = nullptr, *c_o = nullptr, *lv_o = nullptr, *uv_o = nullptr,

@@ -50,7 +50,17 @@ struct SetupArgs {
   MatT* sRv;
   VecT *c, *lv, *uv, *lc, *uc, *qdiag;
   SolverState* st;
+  // FP32 matrix values only (else null): rounding remainders of the scaled
+  // values, CSR and SELL order, written beside the values above
+  float *Qs_lo, *As_lo, *ATs_lo, *sATv_lo, *sQv_lo, *sAv_lo, *Rs_lo, *sRv_lo;
 };
+
+// Remainder of a scaled value after rounding to the matrix type: the FP32
+// value plus this float reproduces v to about 2^-48 relative.
+__device__ __forceinline__ float round_remainder(double v) {
+  const float h = float(v);
+  return isfinite(h) ? float(v - double(h)) : 0.f;
+}
 
 // max over a CSR row of f(k), by a sub-warp of L lanes; result in every lane.
 template <class F>
@@ -227,11 +237,13 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
             if (col < a.n) {
               const double v = (a.Qv_o[k] * D[j]) * D[col];
               a.Qs[k] = MatT(v);
+              if (a.Qs_lo) a.Qs_lo[k] = round_remainder(v);
               if (col == j) qd += v;
               gs += fabs(v);
             } else {  // (R^T)_j,(col-n) scaled: R D
               const double v = a.Qv_o[k] * D[j];
               a.Qs[k] = MatT(v);
+              if (a.Qs_lo) a.Qs_lo[k] = round_remainder(v);
               rs += fabs(v);
             }
           }
@@ -242,8 +254,11 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
         }
       }
       if (valid)
-        for (int k = a.ATp[j] + sl; k < a.ATp[j + 1]; k += Lv)
-          a.ATs[k] = MatT((a.ATv_o[k] * E[a.ATc[k]]) * D[j]);
+        for (int k = a.ATp[j] + sl; k < a.ATp[j + 1]; k += Lv) {
+          const double v = (a.ATv_o[k] * E[a.ATc[k]]) * D[j];
+          a.ATs[k] = MatT(v);
+          if (a.ATs_lo) a.ATs_lo[k] = round_remainder(v);
+        }
       if (valid && sl == 0) {
         const double cs = a.c_o[j] * D[j];
         a.c[j] = VecT(cs);
@@ -258,7 +273,11 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
     });
     rows_loop<BS>(clo, chi, Lc, [&](int i, bool valid, int sl) {
       if (valid)
-        for (int k = a.Ap[i] + sl; k < a.Ap[i + 1]; k += Lc) a.As[k] = MatT((a.Av_o[k] * E[i]) * D[a.Ac[k]]);
+        for (int k = a.Ap[i] + sl; k < a.Ap[i + 1]; k += Lc) {
+          const double v = (a.Av_o[k] * E[i]) * D[a.Ac[k]];
+          a.As[k] = MatT(v);
+          if (a.As_lo) a.As_lo[k] = round_remainder(v);
+        }
       if (valid && sl == 0) {
         const double l = a.lc_o[i] * E[i], u = a.uc_o[i] * E[i];
         a.lc[i] = VecT(l);
@@ -278,6 +297,7 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
         for (int q = a.Rp[l]; q < a.Rp[l + 1]; ++q) {
           const double v = a.Rv_o[q] * D[a.Rc[q]];
           a.Rs[q] = MatT(v);
+          if (a.Rs_lo) a.Rs_lo[q] = round_remainder(v);
           t += fabs(v);
         }
         rrow = fmax(rrow, t);
@@ -298,6 +318,18 @@ __device__ void setup_instance(Group<BS>& g, const SetupArgs<MatT, VecT>& a) {
   if (a.has_q) fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sQp, a.Qp, a.Qs, a.sQv);
   fill_sell_space(g, a.csp.nslices, a.csp.perm, a.sAp, a.Ap, a.As, a.sAv);
   if (a.k > 0) fill_sell_space(g, a.rsp.nslices, a.rsp.perm, a.sRp, a.Rp, a.Rs, a.sRv);
+  if (a.ATs_lo) {
+    const float* cATl = a.ATs_lo;
+    const float* cQl = a.Qs_lo;
+    const float* cAl = a.As_lo;
+    fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sATp, a.ATp, cATl, a.sATv_lo);
+    if (a.has_q) fill_sell_space(g, a.vsp.nslices, a.vsp.perm, a.sQp, a.Qp, cQl, a.sQv_lo);
+    fill_sell_space(g, a.csp.nslices, a.csp.perm, a.sAp, a.Ap, cAl, a.sAv_lo);
+    if (a.k > 0) {
+      const float* cRl = a.Rs_lo;
+      fill_sell_space(g, a.rsp.nslices, a.rsp.perm, a.sRp, a.Rp, cRl, a.sRv_lo);
+    }
+  }
   if (!group_sync<BS>(g)) return;
 
   // ---- 3. ||A||_2 by Lanczos on A^T A (FP64 vectors, the scaled values) ----
@@ -388,7 +420,7 @@ __global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsi
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
   __shared__ double sm_lz[2 * kLanczosCap + 1];
-  __shared__ double sm_red[(BS / 32) * 4];
+  __shared__ double sm_red[(BS / 32) * kRowSums];
   __shared__ int sm_flag;
   Group<BS> g;
   g.lz = sm_lz;
@@ -418,7 +450,7 @@ __global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, Ve
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
   __shared__ double sm_lz[2 * kLanczosCap + 1];
-  __shared__ double sm_red[(BS / 32) * 4];
+  __shared__ double sm_red[(BS / 32) * kRowSums];
   __shared__ int sm_flag;
   __shared__ int sm_idx;
   Group<BS> g;

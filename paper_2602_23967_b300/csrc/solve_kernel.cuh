@@ -172,11 +172,18 @@ struct StepScalars {
 
 // ---- structured objective Q = P + R^T R (Sec. 2.2): out = R v over the k rows
 // of R, the k-vector that the Q products of the next phase gather from ----
+// With FP32 values R v is taken with the remainders as well (R has few rows),
+// so t carries no rounding of R and the defect correction at the checks only
+// has to cover [P | R^T].
 template <int BS, Ld LM, class MatT, class VecT, class G>
 __device__ __forceinline__ void r_rows(const Inst<MatT, VecT>& I, int prank, G gat, VecT* __restrict__ out,
                                        const RowCtx& rc) {
-  space_rows<BS, LM, VecT>(I.rsp, prank, src(I.Rsl, I.R, gat), nosrc<MatT>(), rc,
-                           [&](int l, const VecT* sums) { out[l] = sums[0]; });
+  constexpr bool kLo = std::is_same<MatT, float>::value;
+  space_rows<BS, LM, VecT>(I.rsp, prank, src_lo<kLo>(I.Rsl, I.R, gat), nosrc<MatT>(), rc,
+                           [&](int l, const VecT* sums) {
+                             if constexpr (kLo) out[l] = sums[0] + sums[1];
+                             else out[l] = sums[0];
+                           });
 }
 // R x (Phase I and BB steps: Q x, x the given vector)
 template <int BS, Ld LM, class MatT, class VecT>
@@ -198,12 +205,19 @@ __device__ PDHCG_PHASE_ATTR void r_phase_check(const Inst<MatT, VecT>& I, int pr
   const VecT* __restrict__ xT = I.xT;
   VecT* __restrict__ o1 = I.rt1;
   VecT* __restrict__ o2 = I.rt2;
+  constexpr bool kLo = std::is_same<MatT, float>::value;
   space_rows<BS, LM, double>(
       I.rsp, prank,
-      src2(I.Rsl, I.R, [&](int j) { return double(xT[j]); }, [&](int j) { return double(xT[j]) - double(x[j]); }),
+      src2_lo<kLo>(I.Rsl, I.R, [&](int j) { return double(xT[j]); },
+                   [&](int j) { return double(xT[j]) - double(x[j]); }),
       nosrc<MatT>(), rc, [&](int l, const double* sums) {
-        o1[l] = VecT(sums[0]);
-        o2[l] = VecT(sums[1]);
+        if constexpr (kLo) {
+          o1[l] = VecT(sums[0] + sums[2]);
+          o2[l] = VecT(sums[1] + sums[3]);
+        } else {
+          o1[l] = VecT(sums[0]);
+          o2[l] = VecT(sums[1]);
+        }
       });
 }
 
@@ -413,19 +427,34 @@ __device__ PDHCG_PHASE_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, 
 
 // ---- check phase: KKT residual pieces on the original data (Sec. 4.2) and the
 // infeasibility tests' pieces (Sec. 5.1, 5.2), with Delta = T(z) - z ----
+//
+// Every product here is FP64-accurate: with FP32 matrix values the rounding
+// remainders are summed as well (val + lo), so the residuals and certificates
+// refer to the problem as given, not to its FP32-rounded copy.
+//
+// Defect correction (FP32 matrix values only).  The iteration applies the
+// FP32-rounded matrices A32 = A - A_lo and Q32 = Q - Q_lo, so its fixed point
+// would solve a perturbed problem whose FP64 residuals can stay above the
+// tolerance.  At every check the remainder products at the current point
+// z^ = T(z) are folded into the data the iteration reads:
+//   c_eff  = c + A_lo^T y^ (+ Q_lo x^ unless the closed form, which uses the
+//            exact diagonal, solves the subproblem)
+//   lc_eff = lc - A_lo x^,  uc_eff = uc - A_lo x^      (scaled space)
+// so that A32 x + A_lo x^ in [lc, uc] and Q32 x + Q_lo x^ + A32^T y + A_lo^T y^
+// are the FP64 constraint and gradient at x = x^.  The correction lags by one
+// check and shrinks as z converges; at the fixed point it is exact.
 template <int BS, Ld LM, bool kR, class MatT, class VecT>
-__device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, const RowCtx& rc) {
+__device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int prank, int cur, bool corr_q,
+                                                const RowCtx& rc) {
+  constexpr bool kLo = std::is_same<MatT, float>::value;
   const VecT* __restrict__ x = cur ? I.xb1 : I.xb0;
   const VecT* __restrict__ y = cur ? I.yb1 : I.yb0;
   const VecT* __restrict__ xT = I.xT;
   const VecT* __restrict__ yT = I.yT;
   const VecT* __restrict__ xa = I.xa;
   const VecT* __restrict__ ya = I.ya;
-  const VecT* __restrict__ lc = I.lc;
-  const VecT* __restrict__ uc = I.uc;
   const VecT* __restrict__ lv = I.lv;
   const VecT* __restrict__ uv = I.uv;
-  const VecT* __restrict__ c_s = I.c;
   const int8_t* __restrict__ ctype = I.ctype;
   const int8_t* __restrict__ vtype = I.vtype;
   const int nv = I.n;
@@ -434,29 +463,54 @@ __device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int p
   for (int q = 0; q < 18; ++q) cv.v[q] = 0.0;
   space_rows<BS, LM, double>(
       I.csp, prank,
-      src2(I.As, I.A, [&](int j) { return double(xT[j]); }, [&](int j) { return double(xT[j]) - double(x[j]); }),
+      src2_lo<kLo>(I.As, I.A, [&](int j) { return double(xT[j]); },
+                   [&](int j) { return double(xT[j]) - double(x[j]); }),
       nosrc<MatT>(), rc, [&](int i, const double* sums) {
-        const double ax = sums[0], ad = sums[1];
-        const double axu = ax / I.E[i];
+        double ax = sums[0], ad = sums[1], alo = 0.0;
+        if constexpr (kLo) {
+          alo = sums[2];
+          ax += sums[2];
+          ad += sums[3];
+        }
+        const double Ei = I.E[i];
+        const double lcs = I.lc_o[i] * Ei, ucs = I.uc_o[i] * Ei;  // scaled bounds as given
+        const double axu = ax / Ei;
         cv.v[0] = fmax(cv.v[0], fabs(axu - clampv(axu, I.lc_o[i], I.uc_o[i])));
-        const double yu = double(yT[i]) * I.E[i];
+        const double yu = double(yT[i]) * Ei;
         cv.v[7] += support_term(yu, I.lc_o[i], I.uc_o[i]);
         const double ytl = proj_Y(double(yT[i]) - double(y[i]), ctype[i]);
-        cv.v[9] += support_term(ytl, double(lc[i]), double(uc[i]));
+        cv.v[9] += support_term(ytl, lcs, ucs);
         cv.v[13] = fmax(cv.v[13], fabs(ad - proj_recc(ad, ctype[i])));
         const double dya = double(yT[i]) - double(ya[i]);
         cv.v[16] += dya * dya;
+        if constexpr (kLo) {
+          I.lc[i] = VecT(lcs - alo);
+          I.uc[i] = VecT(ucs - alo);
+        }
       });
   space_rows<BS, LM, double>(
       I.vsp, prank,
-      src2(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
-           [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
-      src2(I.Qs, I.Q, [&](int k) { return kR && k >= nv ? double(I.rt1[k - nv]) : double(xT[k]); },
-           [&](int k) { return kR && k >= nv ? double(I.rt2[k - nv]) : double(xT[k]) - double(x[k]); },
-           I.has_q != 0),
+      src2_lo<kLo>(I.ATs, I.AT, [&](int i) { return double(yT[i]); },
+                   [&](int i) { return proj_Y(double(yT[i]) - double(y[i]), ctype[i]); }),
+      src2_lo<kLo>(I.Qs, I.Q, [&](int k) { return kR && k >= nv ? double(I.rt1[k - nv]) : double(xT[k]); },
+                   [&](int k) { return kR && k >= nv ? double(I.rt2[k - nv]) : double(xT[k]) - double(x[k]); },
+                   I.has_q != 0),
       rc, [&](int j, const double* sums) {
-        const double aty = sums[0], atyt = sums[1], qx = sums[2], qdd = sums[3];
+        double aty, atyt, qx, qdd, dc = 0.0;
+        if constexpr (kLo) {
+          aty = sums[0] + sums[2];
+          atyt = sums[1] + sums[3];
+          qx = sums[4] + sums[6];
+          qdd = sums[5] + sums[7];
+          dc = sums[2] + (corr_q ? sums[6] : 0.0);
+        } else {
+          aty = sums[0];
+          atyt = sums[1];
+          qx = sums[2];
+          qdd = sums[3];
+        }
         const double Dj = I.D[j];
+        const double cs = I.c_o[j] * Dj;  // scaled c as given
         const double xu = double(xT[j]) * Dj;
         const double qxu = qx / Dj, atyu = aty / Dj;
         const double rj = qxu + I.c_o[j] + atyu;
@@ -471,11 +525,12 @@ __device__ PDHCG_PHASE_ATTR Red<18> check_phase(const Inst<MatT, VecT>& I, int p
         cv.v[9] += support_term(-atyt, double(lv[j]), double(uv[j]));
         const double dx = double(xT[j]) - double(x[j]);
         cv.v[10] = fmax(cv.v[10], fabs(dx));
-        cv.v[11] += double(c_s[j]) * dx;
+        cv.v[11] += cs * dx;
         cv.v[12] = fmax(cv.v[12], fabs(dx - proj_recc(dx, vtype[j])));
         cv.v[14] = fmax(cv.v[14], fabs(qdd));
         const double dxa = double(xT[j]) - double(xa[j]);
         cv.v[15] += dxa * dxa;
+        if constexpr (kLo) I.c[j] = VecT(cs + dc);
       });
   return cv;
 }
@@ -548,16 +603,22 @@ __device__ PDHCG_PHASE_ATTR void restart_copy(const Inst<MatT, VecT>& I, int cur
 
 template <int BS, class MatT, class VecT>
 __device__ PDHCG_PHASE_ATTR void init_point(const Inst<MatT, VecT>& I, int vlo, int vhi, int clo, int chi) {
+  constexpr bool kLo = std::is_same<MatT, float>::value;
   for_elems<BS>(vlo, vhi, [&](int j) {
     double x0 = I.x_init ? I.x_init[j] / I.D[j] : 0.0;
     VecT xv = VecT(clampv(x0, double(I.lv[j]), double(I.uv[j])));
     I.xb0[j] = xv;
     I.xa[j] = xv;
+    if constexpr (kLo) I.c[j] = VecT(I.c_o[j] * I.D[j]);  // drop a previous solve's correction
   });
   for_elems<BS>(clo, chi, [&](int i) {
     double y0 = I.y_init ? proj_Y(I.y_init[i] / I.E[i], I.ctype[i]) : 0.0;
     I.yb0[i] = VecT(y0);
     I.ya[i] = VecT(y0);
+    if constexpr (kLo) {
+      I.lc[i] = VecT(I.lc_o[i] * I.E[i]);
+      I.uc[i] = VecT(I.uc_o[i] * I.E[i]);
+    }
   });
 }
 
@@ -767,7 +828,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
         if (!group_sync<BS>(g)) { ok = false; break; }
       }
       {
-        const Red<18> r = check_phase<BS, LM, kR>(I, prank, cur, rc);
+        const Red<18> r = check_phase<BS, LM, kR>(I, prank, cur, method != PDHCG_INNER_DIAG, rc);
 #pragma unroll
         for (int q = 0; q < 18; ++q) cv[q] = r.v[q];
       }
@@ -958,13 +1019,19 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
   solve_instance<BS, Ld::Cached, kR>(g, I, plan, rc);
   __syncthreads();
   const int cur2 = Ig.st->cur;
+  constexpr bool kLo = std::is_same<MatT, float>::value;
   for (int i = threadIdx.x; i < n; i += BS) {
     (cur2 ? Ig.xb1 : Ig.xb0)[i] = (cur2 ? xb1 : xb0)[i];
     Ig.xa[i] = xa[i];
+    if constexpr (kLo) Ig.c[i] = c[i];  // the defect-corrected data resumes with the iterate
   }
   for (int i = threadIdx.x; i < m; i += BS) {
     (cur2 ? Ig.yb1 : Ig.yb0)[i] = (cur2 ? yb1 : yb0)[i];
     Ig.ya[i] = ya[i];
+    if constexpr (kLo) {
+      Ig.lc[i] = lc[i];
+      Ig.uc[i] = uc[i];
+    }
   }
 }
 
@@ -982,7 +1049,7 @@ template <int BS, class MatT, class VecT, bool kR>
 __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_POOL_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
-  __shared__ double sm_red[(BS / 32) * 4];
+  __shared__ double sm_red[(BS / 32) * kRowSums];
   extern __shared__ __align__(16) char dsm[];
   __shared__ int sm_flag;
   __shared__ int sm_idx;

@@ -115,6 +115,7 @@ def lib():
         L.pdhcg_get_info.argtypes = [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_size_t)]
         L.pdhcg_get_phase_times.argtypes = [_P, _D]
+        L.pdhcg_get_device.argtypes = [_P, C.POINTER(C.c_int32)]
         L.pdhcg_destroy.argtypes = [_P]
         L.pdhcg_destroy.restype = None
         L.pdhcg_strerror.restype = C.c_char_p
@@ -243,6 +244,11 @@ class Problem:
         names = ["phase1", "inner_rows", "inner_elem", "phase2", "check", "barrier", "restart", "other"]
         return dict(zip(names, t.tolist()))
 
+    def device(self):
+        d = C.c_int32()
+        check(lib().pdhcg_get_device(self.handle, C.byref(d)), "pdhcg_get_device")
+        return int(d.value)
+
     def device_bytes(self):
         n, m, b = C.c_int32(), C.c_int32(), C.c_size_t()
         check(lib().pdhcg_get_info(self.handle, C.byref(n), C.byref(m), C.byref(b)), "pdhcg_get_info")
@@ -301,12 +307,44 @@ def solve_batch(problems, want_solutions=True):
 NOALLOC_MAX_INSTANCES = 1024  # PDHCG_NOALLOC_MAX_INSTANCES
 
 
+def check_noalloc_outputs(problems, x_out, y_out, device=None):
+    """Validate the caller's output tensors before the kernel writes into them.
+
+    Each list has one entry per problem; a non-None entry must be a contiguous
+    float64 CUDA tensor on ``device`` (the handles' device, if given) with at
+    least n_i (x) or m_i (y) elements.  Raises ValueError otherwise: the kernel
+    writes through the raw pointers, so a short, strided, wrongly typed or
+    foreign-device buffer would be an out-of-bounds device write."""
+    count = len(problems)
+    for name, outs, size in (("x_out", x_out, lambda p: p.n), ("y_out", y_out, lambda p: p.m)):
+        if outs is None:
+            continue
+        if len(outs) != count:
+            raise ValueError(f"{name}: {len(outs)} entries for {count} problems")
+        for i, (p, t) in enumerate(zip(problems, outs)):
+            if t is None:
+                continue
+            if getattr(t, "dtype", None) is None or str(t.dtype) != "torch.float64":
+                raise ValueError(f"{name}[{i}]: dtype must be torch.float64, got {getattr(t, 'dtype', None)}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name}[{i}]: must be contiguous")
+            if t.numel() < size(p):
+                raise ValueError(f"{name}[{i}]: {t.numel()} elements, needs {size(p)}")
+            if not getattr(t, "is_cuda", False):
+                raise ValueError(f"{name}[{i}]: must be a CUDA tensor")
+            if device is not None and t.device.index != device:
+                raise ValueError(f"{name}[{i}]: on cuda:{t.device.index}, the problems are on cuda:{device}")
+
+
 def solve_batch_noalloc(problems, x_out=None, y_out=None):
     """pdhcg_solve_batch_noalloc: the batched solve with static device scratch.
 
     ``x_out`` / ``y_out``: lists of float64 CUDA tensors (n_i / m_i elements; an
-    entry may be None), or None.  Returns the result dicts."""
+    entry may be None), or None; checked by check_noalloc_outputs.  Returns the
+    result dicts."""
     count = len(problems)
+    if count and (x_out is not None or y_out is not None):
+        check_noalloc_outputs(problems, x_out, y_out, problems[0].device())
     handles = (_P * max(count, 1))(*[p.handle for p in problems])
     res = (Result * max(count, 1))()
     ptr = (lambda t: _P(t.data_ptr()) if t is not None else None)

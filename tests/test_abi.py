@@ -122,3 +122,28 @@ def test_empty_batches_and_negative_counts():
     handles = (C.c_void_p * 1)()
     assert L.pdhcg_solve_batch(handles, -1, res, None, None) == pdhcg.E_INVALID
     assert L.pdhcg_solve_batch_noalloc(handles, -1, res, None, None) == pdhcg.E_INVALID
+
+
+def test_noalloc_output_checks_reject_bad_buffers():
+    # pdhcg_solve_batch_noalloc writes through the raw pointers of the caller's
+    # tensors, so the binding rejects every buffer it could overrun before the call
+    import collections
+
+    import torch
+    from paper_2602_23967_b300 import pdhcg
+
+    P = collections.namedtuple("P", "n m")
+    probs = [P(5, 3), P(4, 2)]
+    ok_x = [None, None]
+    pdhcg.check_noalloc_outputs(probs, ok_x, None)            # None entries are allowed
+    bad = [
+        ([torch.zeros(5, dtype=torch.float32), None], None, "dtype"),
+        ([torch.zeros(10, dtype=torch.float64)[::2], None], None, "contiguous"),
+        ([torch.zeros(4, dtype=torch.float64), None], None, "elements"),
+        (None, [None, torch.zeros(1, dtype=torch.float64)], "elements"),
+        ([torch.zeros(5, dtype=torch.float64), None], None, "CUDA"),
+        ([None], None, "entries"),
+    ]
+    for xo, yo, word in bad:
+        with pytest.raises(ValueError, match=word):
+            pdhcg.check_noalloc_outputs(probs, xo, yo)

@@ -2,7 +2,7 @@
 pairs on the FP32 pipe) against the FP64 oracle and against the FP64-vector
 (mixed) mode on the same FP32 matrix values.
 
-Bars: relative KKT (oracle's evaluator on the GPU solution) <= 3 eps and
+Bars: relative KKT (oracle's evaluator on the GPU solution) <= eps and
 relative objective difference to the oracle <= 1e-6, as for the mixed mode;
 after 100 PDHG steps the double-float iterates equal the mixed-mode iterates to
 1e-9 relative (both round the matrix to FP32 identically, so the difference is
@@ -52,7 +52,7 @@ def test_dfloat_optimal_parity(name):
     x, y, r = solve(qp, precision="dfloat", eps_tol=eps, max_iter=200000)
     assert r["status_name"] == "OPTIMAL", r
     rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
-    assert max(rp, rd, rg) <= 3 * eps, (rp, rd, rg)
+    assert max(rp, rd, rg) <= eps, (rp, rd, rg)
     xo, yo, ro = oracle.solve(qp, oracle.default_params(eps_tol=eps))
     assert ro["status_name"] == "OPTIMAL"
     assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
@@ -64,7 +64,7 @@ def test_dfloat_long_row_multi_cta():
     x, y, r = solve(qp, precision="dfloat", eps_tol=1e-6, group_blocks=16, max_iter=200000)
     assert r["status_name"] == "OPTIMAL", r
     rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
-    assert max(rp, rd, rg) <= 3e-6
+    assert max(rp, rd, rg) <= 1e-6
     xo, yo, ro = oracle.solve(qp, oracle.default_params(eps_tol=1e-6))
     assert rel(pobj, ro["primal_obj"]) <= 1e-6
 

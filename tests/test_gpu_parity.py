@@ -42,7 +42,10 @@ def check_optimal_parity(qp, eps=1e-6, precision="fp64", obj_tol=1e-6, **kw):
     x, y, r, _ = gpu_solve(qp, eps_tol=eps, precision=precision, **kw)
     assert r["status_name"] == "OPTIMAL", r
     rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
-    assert max(rp, rd, rg) <= eps * (1.5 if precision == "fp64" else 3.0), (rp, rd, rg)
+    # the device's stopping test evaluates the residuals with FP64-accurate
+    # products in every precision mode, so the independent FP64 evaluation of
+    # the returned point meets the requested tolerance itself
+    assert max(rp, rd, rg) <= eps, (rp, rd, rg)
     xo, yo, ro = oracle.solve(qp, oracle.default_params(eps_tol=eps, **{k: v for k, v in kw.items()
                                                                        if k in ("inner",)}))
     assert ro["status_name"] == "OPTIMAL"
@@ -277,7 +280,9 @@ def test_cg_lifted_iterates_match_oracle_on_lifted_qp(N):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_cg_lifted_solves_the_original_qp(precision, seed):
     qp = W.random_qp(seed=seed)
-    x, y, r, _ = gpu_solve(qp, eps_tol=1e-6, precision=precision, inner="cg_lifted", max_iter=500000)
+    # the stopping test is on the lifted problem, whose relative residuals are
+    # normalised by its own (larger) bound vector; 1e-7 there meets 1e-6 on the original
+    x, y, r, _ = gpu_solve(qp, eps_tol=1e-7, precision=precision, inner="cg_lifted", max_iter=500000)
     assert r["status_name"] == "OPTIMAL", r
     # the bounds are rows now: satisfied to the relative primal tolerance of Sec. 4.2
     lq = lifted(qp)
@@ -286,7 +291,7 @@ def test_cg_lifted_solves_the_original_qp(precision, seed):
     # the original rows' duals plus the implicit bound multipliers satisfy the
     # original KKT conditions (the bound multipliers are the reduced costs)
     rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
-    assert max(rp, rd, rg) <= 1e-5, (rp, rd, rg)
+    assert max(rp, rd, rg) <= 1e-6, (rp, rd, rg)
     _, _, ro = oracle.solve(qp, oracle.default_params(eps_tol=1e-6))
     assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
 
@@ -309,10 +314,12 @@ def test_structured_q_iterates_match_oracle(N, group_blocks):
 def test_structured_q_solves_to_the_formed_optimum(precision, inner):
     qf = W.random_qp(seed=1, factored=True)
     formed = W.QP(qf.n, qf.m, W._csr(qf.Q + qf.R.T @ qf.R), qf.A, qf.c, qf.lc, qf.uc, qf.lv, qf.uv)
-    x, y, r, _ = gpu_solve(qf, eps_tol=1e-6, precision=precision, inner=inner, max_iter=500000)
+    # CG_LIFTED stops on the lifted problem's residuals (see above): 1e-7 there
+    x, y, r, _ = gpu_solve(qf, eps_tol=1e-6 if inner == "auto" else 1e-7, precision=precision, inner=inner,
+                           max_iter=500000)
     assert r["status_name"] == "OPTIMAL", r
     rp, rd, rg, pobj, _ = kkt_of(formed, x, y)
-    assert max(rp, rd, rg) <= (3e-6 if inner == "auto" else 1e-5), (rp, rd, rg)
+    assert max(rp, rd, rg) <= 1e-6, (rp, rd, rg)
     _, _, ro = oracle.solve(formed, oracle.default_params(eps_tol=1e-6))
     assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
 
@@ -366,7 +373,7 @@ def test_mixed_batch_of_plain_and_structured_problems():
         formed = q if q.R is None else W.QP(q.n, q.m, W._csr(q.Q + q.R.T @ q.R), q.A, q.c, q.lc, q.uc,
                                              q.lv, q.uv)
         rp, rd, rg, pobj, _ = kkt_of(formed, x, y)
-        assert max(rp, rd, rg) <= 3e-6, (rp, rd, rg)
+        assert max(rp, rd, rg) <= 1e-6, (rp, rd, rg)
         _, _, ro = oracle.solve(formed, oracle.default_params(eps_tol=1e-6))
         assert rel(pobj, ro["primal_obj"]) <= 1e-6, (pobj, ro["primal_obj"])
 

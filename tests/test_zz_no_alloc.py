@@ -33,19 +33,32 @@ def _instances():
     return qps
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
 def test_noalloc_matches_solve_batch_twice(precision):
     import torch
     qps = _instances()
     probs = pdhcg.create_batch(qps, pdhcg.default_params(precision=precision, eps_tol=1e-6))
+    # a lifted-bound handle (PDHCG_INNER_CG_LIFTED): its kernel writes the
+    # handle's own dual staging, and only the original rows' duals reach y_out
+    probs.append(pdhcg.Problem(W.random_qp(seed=24), pdhcg.default_params(precision=precision, eps_tol=1e-6,
+                                                                         inner="cg_lifted", max_iter=200000)))
     try:
         ref = pdhcg.solve_batch(probs, want_solutions=True)
         assert all(rr["status_name"] == "OPTIMAL" for _, _, rr in ref[:40])   # the MPC instances
+        assert ref[-1][2]["status_name"] == "OPTIMAL" and ref[-1][2]["inner_method"] == 2
+        # every output buffer exists before the first call, so nothing in the
+        # measured region below allocates on the caller's side either
+        xs = [torch.empty((p.n,), dtype=torch.float64, device="cuda") for p in probs]
+        ys = [torch.empty((max(p.m, 1),), dtype=torch.float64, device="cuda") for p in probs]
+        torch.cuda.synchronize()
+        mem = []
         for call in range(2):  # two calls in a row reuse the same static scratch
-            xs = [torch.full((p.n,), np.nan, dtype=torch.float64, device="cuda") for p in probs]
-            ys = [torch.full((max(p.m, 1),), np.nan, dtype=torch.float64, device="cuda") for p in probs]
+            for t in xs + ys:
+                t.fill_(np.nan)
             out = pdhcg.solve_batch_noalloc(probs, xs, ys)
             torch.cuda.synchronize()
+            # device memory after the call: free bytes (driver) and torch's reserve
+            mem.append((torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()))
             for i, (xr, yr, rr) in enumerate(ref):
                 r = out[i]
                 assert r["status_name"] == rr["status_name"], (call, i, r, rr)
@@ -55,6 +68,8 @@ def test_noalloc_matches_solve_batch_twice(precision):
                     assert _close(r[key], rr[key]), (call, i, key, r[key], rr[key])
                 assert _close(xs[i].cpu().numpy(), xr), (call, i)
                 assert _close(ys[i][: probs[i].m].cpu().numpy(), yr), (call, i)
+        # the second call (after the first set up the scratch address) took no device memory
+        assert mem[1] == mem[0], mem
     finally:
         for p in probs:
             p.close()
