@@ -293,6 +293,19 @@ void pdhcg_server_destroy(pdhcg_server_t* srv);
 const char* pdhcg_strerror(int code);
 const char* pdhcg_last_error(void);
 
+/* Self-test of the bounded device waits (failure detection without a fault).
+ * Every spin-wait of the solve kernel (the group barrier, queue waits) gives
+ * up after params.device_timeout_ms, sets a device error flag and returns, so
+ * that the host reports PDHCG_E_DEVICE_TIMEOUT and the context stays usable.
+ * This call makes both kinds of wait run out on purpose, on the current
+ * device: a two-CTA group barrier whose second CTA never arrives, and a wait
+ * on a flag that nothing sets, each limited to timeout_us microseconds
+ * (1 .. 1e7).  Returns PDHCG_E_DEVICE_TIMEOUT when both gave up and reported
+ * it (the designed outcome), PDHCG_E_CUDA if a wait did not report, and
+ * PDHCG_E_INVALID for a timeout out of range.  *waited_seconds (may be NULL):
+ * device time spent in the two waits. */
+int pdhcg_selftest_bounded_wait(int32_t timeout_us, double* waited_seconds);
+
 #ifdef __cplusplus
 }
 #endif

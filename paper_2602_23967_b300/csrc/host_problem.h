@@ -63,6 +63,7 @@ size_t device_footprint(const HostQP& h, int precision);
 struct PartitionSet {
   int nblk = 0;
   int32_t* d_buf = nullptr;  // 11 tables of nblk + 1 entries
+  bool owned = false;        // d_buf is a cudaMalloc of its own (else it lives in the arena)
   int32_t *v_slice = nullptr, *v_long = nullptr, *v_huge = nullptr;
   int32_t *c_slice = nullptr, *c_long = nullptr, *c_huge = nullptr;
   int32_t *v_even = nullptr, *c_even = nullptr;  // even row splits for elementwise work
@@ -107,10 +108,20 @@ void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res
 // be null).  scratch (device, scratch_bytes) holds the launch descriptors when
 // large enough; the caller then synchronises the stream before reusing it.
 // Without it the call allocates a temporary buffer and blocks until done.
+// Handles whose batch_nblk is above one run on multi-CTA groups: with
+// group_stream given, in a cooperative launch of their own on that stream
+// (ordered after the copies on the handles' stream by ev_ready, and before
+// later work there by ev_done); without it, in one cooperative launch whose
+// remaining CTAs serve the pool.  A large handle that finds no room sits this
+// launch out when a step or time limit makes it a slice.
 int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states,
                       double* const* x_out, double* const* y_out, int64_t iter_budget,
                       const int* slots = nullptr, void* scratch = nullptr, size_t scratch_bytes = 0,
-                      uint64_t slice_ns = 0);
+                      uint64_t slice_ns = 0, cudaStream_t group_stream = nullptr,
+                      cudaEvent_t ev_ready = nullptr, cudaEvent_t ev_done = nullptr);
+// Bytes of device scratch one launch over count instances needs, ngroups of
+// them on multi-CTA groups of group_ctas CTAs in total.
+size_t batch_scratch_bytes(int count, int ngroups, int group_ctas);
 int check_params_c(const pdhcg_params* p);
 
 }  // namespace pdhcg
@@ -181,6 +192,11 @@ struct pdhcg_problem {
   double* part = nullptr;                // 2 * kSlots * max_blk
   int max_blk = 0;
   std::map<int, pdhcg::PartitionSet> partitions;
+  // batched and served solves: CTAs of this instance's group (1 = a pool CTA),
+  // and for batch_nblk > 1 its partition tables, uploaded with the inputs
+  int batch_nblk = 1;
+  int32_t* batch_part = nullptr;
+  std::vector<int32_t> batch_tables;
   // setup results
   pdhcg::SolverState setup_state{};
   pdhcg::SolverState last_state{};  // state at the end of the last pdhcg_solve / _dev

@@ -41,6 +41,18 @@ int pool_blocks_per_sm(size_t smem_vec_bytes) {
 }
 
 template <class MatT, class VecT>
+int group_blocks_per_sm(size_t smem_vec_bytes) {
+  int nb = 0, nr = 0;
+  if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS,
+                                                    smem_vec_bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kGroupBS, MatT, VecT, true>, kGroupBS,
+                                                    smem_vec_bytes) != cudaSuccess)
+    return 0;
+  return std::min(nb, nr);
+}
+
+template <class MatT, class VecT>
 cudaError_t kernel_limits(KernelLimits* out) {
   int dev = 0, sms = 0, nb = 0, nr = 0, ns = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -79,10 +91,12 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
                          cudaStream_t s) {
   LaunchPlan p = plan;
   const Inst<MatT, VecT>* di = d_insts;
-  const size_t extra = plan.group_blocks == 0 ? size_t(plan.smem_vec_bytes) : 0;
+  // dynamic shared memory: the vectors of pool instances (a cooperative launch
+  // with pool CTAs beside its groups gives it to every CTA; groups ignore it)
+  const size_t extra = size_t(plan.smem_vec_bytes);
   cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
   if (e != cudaSuccess) return e;
-  const size_t smem = plan.group_blocks > 0 ? 0 : extra;
+  const size_t smem = extra;
   const bool r = plan.structured != 0;
   if (plan.group_blocks == 0) {
     if (r)
@@ -116,6 +130,7 @@ cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, in
                                                 unsigned long long*, double*, int32_t*,        \
                                                 uint64_t, cudaStream_t);                       \
   template int pool_blocks_per_sm<MatT, VecT>(size_t);                                          \
+  template int group_blocks_per_sm<MatT, VecT>(size_t);                                         \
   template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
                                                      int32_t*, uint64_t, cudaStream_t);           \
   template cudaError_t launch_solve<MatT, VecT>(const Inst<MatT, VecT>*, const LaunchPlan&, int, \

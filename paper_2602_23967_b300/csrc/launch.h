@@ -40,6 +40,12 @@ cudaError_t launch_setup(const SetupArgs<MatT, VecT>& a, int nblk, unsigned long
 template <class MatT, class VecT>
 int pool_blocks_per_sm(size_t smem_vec_bytes);
 
+// Resident CTAs per SM of the group-size solve kernel (both variants) with
+// smem_vec_bytes of dynamic shared memory per CTA: the bound of a cooperative
+// launch that mixes multi-CTA groups with pool CTAs.
+template <class MatT, class VecT>
+int group_blocks_per_sm(size_t smem_vec_bytes);
+
 // Solve launch; cooperative when plan.group_blocks > 0.
 template <class MatT, class VecT>
 cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan, int grid,

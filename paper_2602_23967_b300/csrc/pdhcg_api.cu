@@ -116,6 +116,7 @@ void carve(pdhcg_problem* P, Carver& cv, bool external_state = false) {
     P->sRp = cv.take<int64_t>(P->rsell.ptr[0].size());
     P->sRc = cv.take<int32_t>(P->rsell_cols + 16);
   }
+  if (P->batch_nblk > 1) P->batch_part = cv.take<int32_t>(11 * (size_t(P->batch_nblk) + 1));
   if (!external_state) P->st = cv.take<SolverState>(1);
   P->input_bytes = (cv.off + 255) & ~size_t(255);
   // ---- computed on the device ----
@@ -218,6 +219,7 @@ void pack_inputs(const pdhcg_problem* P, const HostQP& h, char* stage) {
     put(P->sRp, P->rsell.ptr[0].data(), sizeof(int64_t) * P->rsell.ptr[0].size());
     put(P->sRc, P->rsell.col[0].data(), sizeof(int32_t) * P->rsell.col[0].size());
   }
+  if (P->batch_nblk > 1) put(P->batch_part, P->batch_tables.data(), sizeof(int32_t) * P->batch_tables.size());
   if (static_cast<const char*>(static_cast<const void*>(P->st)) >= base &&
       static_cast<const char*>(static_cast<const void*>(P->st)) < base + P->input_bytes) {
     SolverState S{};
@@ -270,14 +272,11 @@ std::vector<int32_t> even_split(int32_t rows, int nblk) {
   return b;
 }
 
-int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
-  auto it = P->partitions.find(nblk);
-  if (it != P->partitions.end()) {
-    *out = &it->second;
-    return PDHCG_OK;
-  }
-  PartitionSet ps;
-  ps.nblk = nblk;
+// The 11 row-partition tables of a group of nblk CTAs (nblk + 1 entries each):
+// SELL slices / long rows / huge rows of the variable space, the same for the
+// constraint space, even element splits of both, and the three tables of the
+// rows of R.  Host work only.
+std::vector<int32_t> partition_tables(const pdhcg_problem* P, int nblk) {
   auto slice_w = [](const SellHost& sh, int nmat) {
     std::vector<int64_t> w(size_t(sh.nslices), 0);
     for (int k = 0; k < nmat; ++k)
@@ -319,25 +318,50 @@ int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
   } else {
     for (auto& t : rt) t.assign(size_t(nblk) + 1, 0);
   }
-  const size_t per = size_t(nblk) + 1;
-  CK(cudaMalloc(&ps.d_buf, sizeof(int32_t) * per * 11));
   std::vector<int32_t> flat;
+  flat.reserve(11 * (size_t(nblk) + 1));
   for (auto& t : tabs) flat.insert(flat.end(), t.begin(), t.end());
   flat.insert(flat.end(), ev.begin(), ev.end());
   flat.insert(flat.end(), ec.begin(), ec.end());
   for (auto& t : rt) flat.insert(flat.end(), t.begin(), t.end());
-  CK(cudaMemcpy(ps.d_buf, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
-  ps.v_slice = ps.d_buf;
-  ps.v_long = ps.d_buf + per;
-  ps.v_huge = ps.d_buf + 2 * per;
-  ps.c_slice = ps.d_buf + 3 * per;
-  ps.c_long = ps.d_buf + 4 * per;
-  ps.c_huge = ps.d_buf + 5 * per;
-  ps.v_even = ps.d_buf + 6 * per;
-  ps.c_even = ps.d_buf + 7 * per;
-  ps.r_slice = ps.d_buf + 8 * per;
-  ps.r_long = ps.d_buf + 9 * per;
-  ps.r_huge = ps.d_buf + 10 * per;
+  return flat;
+}
+
+// The device tables of a PartitionSet at d (11 * (nblk + 1) int32).
+void bind_partition(PartitionSet& ps, int32_t* d, int nblk) {
+  const size_t per = size_t(nblk) + 1;
+  ps.nblk = nblk;
+  ps.d_buf = d;
+  ps.v_slice = d;
+  ps.v_long = d + per;
+  ps.v_huge = d + 2 * per;
+  ps.c_slice = d + 3 * per;
+  ps.c_long = d + 4 * per;
+  ps.c_huge = d + 5 * per;
+  ps.v_even = d + 6 * per;
+  ps.c_even = d + 7 * per;
+  ps.r_slice = d + 8 * per;
+  ps.r_long = d + 9 * per;
+  ps.r_huge = d + 10 * per;
+}
+
+int get_partition(pdhcg_problem* P, int nblk, PartitionSet** out) {
+  auto it = P->partitions.find(nblk);
+  if (it != P->partitions.end()) {
+    *out = &it->second;
+    return PDHCG_OK;
+  }
+  const std::vector<int32_t> flat = partition_tables(P, nblk);
+  int32_t* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(int32_t) * flat.size()));
+  const cudaError_t e = cudaMemcpy(d, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "partition tables");
+  }
+  PartitionSet ps;
+  bind_partition(ps, d, nblk);
+  ps.owned = true;
   auto res = P->partitions.emplace(nblk, ps);
   *out = &res.first->second;
   return PDHCG_OK;
@@ -550,6 +574,27 @@ int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
   const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ + P->nnzR : 0) + 2 * P->nnzA + P->n + P->m;
   if (work < 150000) return 1;
   return int(std::max<int64_t>(2, std::min<int64_t>(maxblk, work / 8192)));
+}
+
+// Batched and served solves: instances below kGroupWork (nonzeros and vector
+// entries one PDHG step touches, inner products counted once) run on one pool
+// CTA each; larger ones on a multi-CTA group of about one CTA per
+// kWorkPerGroupCta, at most kMaxBatchGroup.
+constexpr int64_t kGroupWork = 150000;
+constexpr int64_t kWorkPerGroupCta = 65536;
+constexpr int kMaxBatchGroup = 32;
+
+int batch_group_blocks(const pdhcg_problem* P) {
+  const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ + P->nnzR : 0) + 2 * P->nnzA + P->n + P->m;
+  if (work < kGroupWork) return 1;
+  return int(std::max<int64_t>(2, std::min<int64_t>(kMaxBatchGroup, work / kWorkPerGroupCta)));
+}
+
+// Pooled handles: the group size for batched launches and its partition tables
+// (uploaded with the inputs, so no launch has to allocate them).
+void set_batch_grouping(pdhcg_problem* P) {
+  P->batch_nblk = batch_group_blocks(P);
+  if (P->batch_nblk > 1) P->batch_tables = partition_tables(P, P->batch_nblk);
 }
 
 template <class M, class V>
@@ -927,7 +972,10 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
   for (int i = 0; i < count; ++i) {
     P[size_t(i)]->device = dev;
     P[size_t(i)]->max_blk = pooled ? 1 : std::max(mb, 1);
-    if (pooled) P[size_t(i)]->prm.group_blocks = 1;
+    if (pooled) {
+      P[size_t(i)]->prm.group_blocks = 1;
+      set_batch_grouping(P[size_t(i)]);
+    }
     Carver sizing;
     carve(P[size_t(i)], sizing, batch);
     P[size_t(i)]->arena_bytes = (sizing.off + 255) & ~size_t(255);
@@ -1078,6 +1126,12 @@ int create_impl(int count, const CreateInput* in, const pdhcg_params* params, vo
       std::vector<int32_t>().swap(P[size_t(i)]->vsell.col[k]);
       std::vector<int32_t>().swap(P[size_t(i)]->csell.col[k]);
     }
+    if (P[size_t(i)]->batch_nblk > 1) {
+      PartitionSet ps;
+      bind_partition(ps, P[size_t(i)]->batch_part, P[size_t(i)]->batch_nblk);
+      P[size_t(i)]->partitions[P[size_t(i)]->batch_nblk] = ps;
+      std::vector<int32_t>().swap(P[size_t(i)]->batch_tables);
+    }
     out[i] = P[size_t(i)];
   }
   return PDHCG_OK;
@@ -1089,6 +1143,7 @@ int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes) 
   int rc = prepare_problem(in, prm, nullptr, &P, &h);
   if (rc) return rc;
   P->max_blk = 1;
+  set_batch_grouping(P);
   Carver sizing;
   carve(P, sizing, false);
   *bytes = ((sizing.off + 255) & ~size_t(255)) + (1u << 12);
@@ -1098,9 +1153,191 @@ int footprint_of(const CreateInput& in, const pdhcg_params& prm, size_t* bytes) 
 
 int check_params_c(const pdhcg_params* p) { return check_params(p); }
 
+// ---- persistent launches over many instances (batched solves and serving slices) ----
+//
+// Small instances run on pool CTAs that take them from an atomic queue.  An
+// instance whose batch_group_blocks() is above one runs on a multi-CTA group
+// of the group-size kernel, in a cooperative launch (every group's CTAs
+// co-resident).  Two ways to combine them:
+//   * one launch (batched solves): the cooperative launch's CTAs beyond the
+//     groups serve the pool; groups take at most half of the co-resident CTAs
+//     while pool instances wait;
+//   * two launches (serving slices, group_stream given): the pool keeps its own
+//     128-thread kernel, so a small request's arithmetic does not depend on
+//     what else is live, and the groups run in a cooperative launch of their
+//     own on group_stream, concurrently; groups take at most three quarters
+//     of the co-resident CTAs while pool instances are live.
+// A large instance that finds no room runs on a pool CTA (skip_unplaced =
+// false), or sits the launch out (skip_unplaced = true: a serving slice, where
+// it gets its group in a later slice).
+//
+// Device scratch, carved from d: the descriptors, the queue, the group
+// tables, one zeroed barrier block and the partial sums per group.
+
+size_t batch_scratch_bytes(int count, int ngroups, int group_ctas) {
+  Carver c;
+  c.take_bytes(size_t(std::max(count, 1)), sizeof(Inst<double, double>));
+  c.take<int32_t>(size_t(count) + 8);
+  c.take<int32_t>(3 * size_t(std::max(ngroups, 1)));
+  c.take<int64_t>(size_t(std::max(ngroups, 1)));
+  c.take_bytes(size_t(std::max(ngroups, 1)) * kBarBytes, 1);
+  c.take<double>(size_t(2) * kSlots * size_t(std::max(group_ctas, 1)));
+  return c.off + 256;
+}
+
+struct BatchGroups {
+  std::vector<int32_t> inst, nblk;  // group g: instance, CTAs
+  std::vector<int32_t> pool;        // pool instances in queue order
+  int ctas = 0;                     // CTAs of all groups
+};
+
+// Which instances get groups (in the caller's order) within gcap group CTAs.
+BatchGroups plan_groups(pdhcg_problem* const* probs, const int32_t* order, int count, int gcap,
+                        bool skip_unplaced) {
+  BatchGroups b;
+  for (int q = 0; q < count; ++q) {
+    const int i = order[q];
+    const int nb = batch_group_blocks(probs[i]);
+    if (nb > 1 && b.ctas + nb <= gcap) {
+      b.inst.push_back(i);
+      b.nblk.push_back(nb);
+      b.ctas += nb;
+    } else if (nb <= 1 || !skip_unplaced) {
+      b.pool.push_back(i);
+    }
+  }
+  return b;
+}
+
+// Streams and events of the two-launch form.
+struct SplitLaunch {
+  cudaStream_t group_stream = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;  // inputs copied / groups finished
+};
+
+template <class M, class V>
+int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>& hi, const int32_t* order,
+                 int64_t iter_budget, uint64_t slice_ns, char* d, size_t bytes, cudaStream_t s,
+                 bool skip_unplaced, const SplitLaunch* split) {
+  const pdhcg_problem* P0 = probs[0];
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P0->device));
+  size_t need = 0;
+  int nsmall = 0;
+  for (int i = 0; i < count; ++i) {
+    const size_t b = smem_need(probs[i]);
+    if (b <= kSmemVecBudget) need = std::max(need, b);
+    nsmall += batch_group_blocks(probs[i]) <= 1;
+  }
+  const bool any_large = nsmall < count;
+  // co-resident CTAs of the cooperative launch (its dynamic shared memory:
+  // the pool vectors in the one-launch form, none in the two-launch form)
+  const size_t coop_smem = split ? 0 : need;
+  const int cap = any_large ? std::max(1, group_blocks_per_sm<M, V>(coop_smem)) * sms : 0;
+  int gcap = cap;
+  if (nsmall > 0) gcap = split ? (3 * cap) / 4 : std::max(0, cap - std::min(nsmall, cap / 2));
+  BatchGroups bg;
+  if (any_large) bg = plan_groups(probs, order, count, gcap, skip_unplaced);
+  else bg.pool.assign(order, order + count);
+  const int ng = int(bg.inst.size());
+  if (batch_scratch_bytes(count, ng, bg.ctas) > bytes) {
+    set_error("batched launch: scratch too small");
+    return PDHCG_E_INVALID;
+  }
+  if (ng == 0 && bg.pool.empty()) return PDHCG_OK;
+  // group instances: their partitions (precomputed for pooled handles)
+  std::vector<int64_t> part_off(size_t(std::max(ng, 1)), 0);
+  for (int g = 0; g < ng; ++g) {
+    pdhcg_problem* P = probs[bg.inst[size_t(g)]];
+    PartitionSet* ps = nullptr;
+    int rc = get_partition(P, bg.nblk[size_t(g)], &ps);
+    if (rc) return rc;
+    set_partition(hi[size_t(bg.inst[size_t(g)])], *ps, P);
+    if (g + 1 < ng) part_off[size_t(g) + 1] = part_off[size_t(g)] + int64_t(2) * kSlots * bg.nblk[size_t(g)];
+  }
+  Carver cv;
+  cv.base = d;
+  void* d_inst = cv.take_bytes(size_t(std::max(count, 1)), sizeof(Inst<double, double>));
+  int32_t* d_pool = cv.take<int32_t>(size_t(count) + 8);
+  int32_t* d_gtab = cv.take<int32_t>(3 * size_t(std::max(ng, 1)));
+  int64_t* d_poff = cv.take<int64_t>(size_t(std::max(ng, 1)));
+  unsigned long long* d_bar =
+      static_cast<unsigned long long*>(cv.take_bytes(size_t(std::max(ng, 1)) * kBarBytes, 1));
+  double* d_part = cv.take<double>(size_t(2) * kSlots * size_t(std::max(bg.ctas, 1)));
+  const int npool = int(bg.pool.size());
+  std::vector<int32_t> qw(size_t(npool) + 8, 0);
+  for (size_t q = 0; q < bg.pool.size(); ++q) qw[q] = bg.pool[q];
+  std::vector<int32_t> gt(3 * size_t(std::max(ng, 1)), 0);
+  for (int g = 0, first = 0; g < ng; ++g) {
+    gt[size_t(g)] = first;
+    gt[size_t(ng + g)] = bg.nblk[size_t(g)];
+    gt[size_t(2 * ng + g)] = bg.inst[size_t(g)];
+    first += bg.nblk[size_t(g)];
+  }
+  CK(cudaMemcpyAsync(d_inst, hi.data(), sizeof(Inst<M, V>) * size_t(count), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_pool, qw.data(), sizeof(int32_t) * qw.size(), cudaMemcpyHostToDevice, s));
+  if (ng > 0) {
+    CK(cudaMemcpyAsync(d_gtab, gt.data(), sizeof(int32_t) * gt.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_poff, part_off.data(), sizeof(int64_t) * size_t(ng), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_bar, 0, size_t(ng) * kBarBytes, s));
+  }
+  LaunchPlan base;
+  for (int i = 0; i < count; ++i) base.structured |= probs[i]->k > 0;
+  base.iter_budget = iter_budget;
+  base.slice_ns = slice_ns;
+  base.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
+  base.err = d_pool + npool + 1;
+  LaunchPlan pool = base;  // pool CTAs
+  pool.npool = npool;
+  pool.pool_inst = d_pool;
+  pool.pool_next = d_pool + npool;
+  pool.smem_vec_bytes = int64_t(need);
+  LaunchPlan grp = base;   // the groups (and, in the one-launch form, the pool too)
+  if (ng > 0) {
+    grp.ngroups = ng;
+    grp.group_blocks = bg.ctas;
+    grp.g_first = d_gtab;
+    grp.g_nblk = d_gtab + ng;
+    grp.g_inst = d_gtab + 2 * ng;
+    grp.g_bar = d_bar;
+    grp.g_part = d_part;
+    grp.g_part_off = d_poff;
+  }
+  const Inst<M, V>* di = static_cast<const Inst<M, V>*>(d_inst);
+  if (ng > 0 && !split) {  // one cooperative launch: groups, then pool CTAs
+    grp.npool = pool.npool;
+    grp.pool_inst = pool.pool_inst;
+    grp.pool_next = pool.pool_next;
+    grp.smem_vec_bytes = pool.smem_vec_bytes;
+    const cudaError_t e = launch_solve<M, V>(di, grp, std::min(cap, bg.ctas + npool), s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    return PDHCG_OK;
+  }
+  if (ng > 0) {  // the groups' cooperative launch on the second stream, after the copies above
+    CK(cudaEventRecord(split->ready, s));
+    CK(cudaStreamWaitEvent(split->group_stream, split->ready, 0));
+    const cudaError_t e = launch_solve<M, V>(di, grp, bg.ctas, split->group_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "group launch");
+  }
+  if (npool > 0) {
+    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    const cudaError_t e = launch_solve<M, V>(di, pool, std::max(1, std::min(npool, per_sm * sms)), s);
+    if (e != cudaSuccess) {
+      if (ng > 0) (void)cudaStreamSynchronize(split->group_stream);
+      return cuda_fail(e, "pool launch");
+    }
+  }
+  if (ng > 0) {  // later work on s (state read-back) waits for the groups too
+    CK(cudaEventRecord(split->done, split->group_stream));
+    CK(cudaStreamWaitEvent(s, split->done, 0));
+  }
+  return PDHCG_OK;
+}
+
 int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_states, double* const* x_out,
                       double* const* y_out, int64_t iter_budget, const int* slots, void* scratch,
-                      size_t scratch_bytes, uint64_t slice_ns) {
+                      size_t scratch_bytes, uint64_t slice_ns, cudaStream_t group_stream, cudaEvent_t ev_ready,
+                      cudaEvent_t ev_done) {
   if (count <= 0) return PDHCG_OK;
   const pdhcg_problem* P0 = probs[0];
   CK(cudaSetDevice(P0->device));
@@ -1109,44 +1346,35 @@ int launch_pool_slice(pdhcg_problem* const* probs, int count, SolverState* d_sta
     using M = typename decltype(tag)::Mat;
     using V = typename decltype(tag)::Vec;
     std::vector<Inst<M, V>> hi(static_cast<size_t>(count));
-    std::vector<int32_t> order(static_cast<size_t>(count) + 8, 0);
-    size_t need = 0;
+    std::vector<int32_t> order(static_cast<size_t>(count));
+    int ngmax = 0, ctas = 0;
     for (int i = 0; i < count; ++i) {
       hi[size_t(i)] = make_inst<M, V>(probs[i]);
       hi[size_t(i)].st = d_states + (slots ? slots[i] : i);
       hi[size_t(i)].x_out = x_out ? x_out[i] : nullptr;
       hi[size_t(i)].y_out = y_out ? y_out[i] : nullptr;
       order[size_t(i)] = i;
-      const size_t b = smem_need(probs[i]);
-      if (b <= kSmemVecBudget) need = std::max(need, b);
+      const int nb = batch_group_blocks(probs[i]);
+      if (nb > 1) {
+        ngmax++;
+        ctas += nb;
+      }
     }
-    const size_t ib = sizeof(Inst<M, V>) * size_t(count), ob = sizeof(int32_t) * order.size();
+    const size_t need = batch_scratch_bytes(count, ngmax, ctas);
     char* d = static_cast<char*>(scratch);
     std::unique_ptr<char, void (*)(char*)> guard(nullptr, [](char* q) { cudaFree(q); });
-    if (!d || scratch_bytes < ib + ob) {
-      CK(cudaMalloc(&d, ib + ob));
+    if (!d || scratch_bytes < need) {
+      CK(cudaMalloc(&d, need));
       guard.reset(d);
     }
-    CK(cudaMemcpyAsync(d, hi.data(), ib, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d + ib, order.data(), ob, cudaMemcpyHostToDevice, s));
-    int32_t* d_i32 = reinterpret_cast<int32_t*>(d + ib);
-    LaunchPlan plan;
-    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
-    plan.npool = count;
-    plan.pool_inst = d_i32;
-    plan.pool_next = d_i32 + count;
-    plan.err = d_i32 + count + 1;
-    plan.iter_budget = iter_budget;
-    plan.slice_ns = slice_ns;
-    plan.smem_vec_bytes = int64_t(need);
-    plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
-    const int grid = std::max(1, std::min(count, per_sm * sms));
-    cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d), plan, grid, s);
-    if (e != cudaSuccess) return cuda_fail(e, "slice launch");
+    SplitLaunch split{group_stream, ev_ready, ev_done};
+    int rc = launch_batch<M, V>(probs, count, hi, order.data(), iter_budget, slice_ns, d,
+                                guard ? need : scratch_bytes, s, slice_ns > 0 || iter_budget > 0,
+                                group_stream ? &split : nullptr);
+    if (rc) {
+      if (guard) (void)cudaStreamSynchronize(s);
+      return rc;
+    }
     // the descriptors must outlive the launch: synchronise before a temporary
     // buffer is freed (a caller's scratch stays valid until it synchronises)
     if (guard) CK(cudaStreamSynchronize(s));
@@ -1282,7 +1510,8 @@ void pdhcg_destroy(pdhcg_t* P) {
   if (!P) return;
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
-  for (auto& kv : P->partitions) cudaFree(kv.second.d_buf);
+  for (auto& kv : P->partitions)
+    if (kv.second.owned) cudaFree(kv.second.d_buf);
   P->arena_owner.reset();  // frees the allocation with its last handle
   delete P;
 }
@@ -1364,38 +1593,39 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
     sum_n += size_t(probs[i]->n);
     sum_m += size_t(probs[i]->m);
   }
-  const size_t inst_sz = sizeof(Inst<double, double>);
+  // longest-processing-time-first order for the work queue
+  std::vector<int32_t> order(static_cast<size_t>(count));
+  std::vector<int64_t> work(static_cast<size_t>(count));
+  int ngmax = 0, gctas = 0;
+  for (int i = 0; i < count; ++i) {
+    work[i] = (probs[i]->method != PDHCG_INNER_DIAG ? 4 * probs[i]->nnzQ : 0) + 2 * probs[i]->nnzA +
+              probs[i]->n + probs[i]->m;
+    order[i] = i;
+    const int nb = batch_group_blocks(probs[i]);
+    if (nb > 1) {
+      ngmax++;
+      gctas += nb;
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
   Carver sizing;
   sizing.take<SolverState>(size_t(count));
-  sizing.take_bytes(size_t(count), inst_sz);
-  sizing.take<int32_t>(size_t(count) + 8);
   sizing.take<double>(sum_n);
   sizing.take<double>(sum_m);
+  const size_t launch_bytes = batch_scratch_bytes(count, ngmax, gctas);
+  sizing.take_bytes(launch_bytes, 1);
   void* buf = nullptr;
   int rc = batch_buffer(P0->device, sizing.off + 256, &buf);
   if (rc) return rc;
   Carver cv;
   cv.base = static_cast<char*>(buf);
   SolverState* d_st = cv.take<SolverState>(size_t(count));
-  void* d_inst = cv.take_bytes(size_t(count), inst_sz);
-  int32_t* d_i32 = cv.take<int32_t>(size_t(count) + 8);
   double* d_x = cv.take<double>(sum_n);
   double* d_y = cv.take<double>(sum_m);
+  char* d_launch = static_cast<char*>(cv.take_bytes(launch_bytes, 1));
 
   std::vector<SolverState> hs(static_cast<size_t>(count));
   for (int i = 0; i < count; ++i) hs[i] = initial_state(probs[i]);
-  // longest-processing-time-first order for the work queue
-  std::vector<int32_t> order(static_cast<size_t>(count) + 8, 0);
-  std::vector<int64_t> work(static_cast<size_t>(count));
-  for (int i = 0; i < count; ++i)
-    work[i] = (probs[i]->method != PDHCG_INNER_DIAG ? 4 * probs[i]->nnzQ : 0) + 2 * probs[i]->nnzA +
-              probs[i]->n + probs[i]->m;
-  std::vector<int32_t> idx(static_cast<size_t>(count));
-  for (int i = 0; i < count; ++i) idx[i] = i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
-  for (int i = 0; i < count; ++i) order[i] = idx[i];
-  order[size_t(count)] = 0;      // pool cursor
-  order[size_t(count) + 1] = 0;  // error flag
 
   rc = dispatch_precision(P0->precision, [&](auto tag) {
     using M = typename decltype(tag)::Mat;
@@ -1408,32 +1638,13 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
       hi[i].y_out = d_y + yoff[i];
     }
     CK(cudaMemcpyAsync(d_st, hs.data(), sizeof(SolverState) * size_t(count), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_inst, hi.data(), sizeof(Inst<M, V>) * size_t(count), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_i32, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, s));
-    KernelLimits kl{};
-    cudaError_t e = kernel_limits<M, V>(&kl);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel_limits");
-    LaunchPlan plan;
-    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
-    plan.npool = count;
-    plan.pool_inst = d_i32;
-    plan.pool_next = d_i32 + count;
-    plan.err = d_i32 + count + 1;
-    plan.iter_budget = iter_budget;
-    plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
-    size_t need = 0;
-    for (int i = 0; i < count; ++i) {
-      const size_t b = smem_need(probs[i]);
-      if (b <= kSmemVecBudget) need = std::max(need, b);
+    // every instance is placed: one that finds no group runs on a pool CTA
+    int lrc = launch_batch<M, V>(const_cast<pdhcg_problem* const*>(probs), count, hi, order.data(), iter_budget, 0,
+                                 d_launch, launch_bytes, s, false, nullptr);
+    if (lrc) {
+      (void)cudaStreamSynchronize(s);
+      return lrc;
     }
-    plan.smem_vec_bytes = int64_t(need);
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
-    const int grid = std::max(1, std::min(count, per_sm * sms));
-    e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
-    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     CK(cudaMemcpyAsync(hs.data(), d_st, sizeof(SolverState) * size_t(count), cudaMemcpyDeviceToHost, s));
     return PDHCG_OK;
   });

@@ -101,6 +101,10 @@ struct pdhcg_server {
   std::vector<pdhcg::Live> ready;   // created and set up, waiting for a slot
   int reserved = 0;                 // requests taken for creation, ready or live (<= max_slots)
   cudaStream_t admit_stream = nullptr;
+  // large requests' multi-CTA groups run in a cooperative launch of their own on
+  // group_stream, beside the pool launch of the slice
+  cudaStream_t group_stream = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
   std::thread admitter;
   cudaMemPool_t pool = nullptr;     // device arenas of admitted requests (stream-ordered)
   void* pinned_stage = nullptr;     // creation's host staging, reused
@@ -212,6 +216,9 @@ static void admit_loop(pdhcg_server* S) {
 static void worker_loop(pdhcg_server* S) {
   cudaSetDevice(S->device);
   while (true) {
+    // a failed copy or synchronisation of this round: every live solve then
+    // retires with PDHCG_NUMERICAL_ERROR (its state cannot be trusted)
+    cudaError_t ce = cudaSuccess;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       if (S->live.empty())
@@ -222,8 +229,9 @@ static void worker_loop(pdhcg_server* S) {
         l.slot = S->free_slots.back();
         S->free_slots.pop_back();
         S->h_init[l.slot] = initial_state(l.P);
-        cudaMemcpyAsync(S->d_states + l.slot, S->h_init + l.slot, sizeof(SolverState), cudaMemcpyHostToDevice,
-                        S->stream);
+        const cudaError_t e = cudaMemcpyAsync(S->d_states + l.slot, S->h_init + l.slot, sizeof(SolverState),
+                                              cudaMemcpyHostToDevice, S->stream);
+        if (ce == cudaSuccess) ce = e;
         S->live.push_back(l);
       }
       S->ready.clear();
@@ -243,11 +251,20 @@ static void worker_loop(pdhcg_server* S) {
       yo[size_t(i)] = l.P->y_stage;
       slots[size_t(i)] = l.slot;
     }
-    int rc = launch_pool_slice(probs.data(), count, S->d_states, xo.data(), yo.data(), S->slice_iters,
-                               slots.data(), S->d_launch, S->launch_bytes, S->slice_ns);
-    cudaMemcpyAsync(S->h_states, S->d_states, sizeof(SolverState) * size_t(S->max_slots),
-                    cudaMemcpyDeviceToHost, S->stream);
-    cudaStreamSynchronize(S->stream);
+    int rc = ce == cudaSuccess ? launch_pool_slice(probs.data(), count, S->d_states, xo.data(), yo.data(),
+                                                   S->slice_iters, slots.data(), S->d_launch, S->launch_bytes,
+                                                   S->slice_ns, S->group_stream, S->ev_ready, S->ev_done)
+                               : PDHCG_E_CUDA;
+    {
+      cudaError_t e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(SolverState) * size_t(S->max_slots),
+                                      cudaMemcpyDeviceToHost, S->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+      if (e != cudaSuccess && rc == PDHCG_OK) rc = PDHCG_E_CUDA;
+    }
+    if (rc != PDHCG_OK) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->worker_error = std::string("slice: ") + (ce != cudaSuccess ? cudaGetErrorString(ce) : "launch or copy failed");
+    }
     const auto t_slice1 = std::chrono::steady_clock::now();
     // ---- retire finished solves: their solutions come back in one batch ----
     std::vector<int> fin;
@@ -266,18 +283,22 @@ static void worker_loop(pdhcg_server* S) {
       if (cudaMallocHost(&S->h_sol, sizeof(double) * need * 2) == cudaSuccess) S->h_sol_len = need * 2;
     }
     size_t off = 0;
+    bool sol_ok = S->h_sol != nullptr;
     if (S->h_sol) {
+      cudaError_t e = cudaSuccess;
       for (int i : fin) {
         const pdhcg_problem* P = S->live[size_t(i)].P;
-        cudaMemcpyAsync(S->h_sol + off, P->x_stage, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost,
-                        S->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(S->h_sol + off, P->x_stage, sizeof(double) * size_t(P->n), cudaMemcpyDeviceToHost,
+                              S->stream);
         off += size_t(P->n);
-        if (P->m_user)
-          cudaMemcpyAsync(S->h_sol + off, P->y_stage, sizeof(double) * size_t(P->m_user), cudaMemcpyDeviceToHost,
-                          S->stream);
+        if (P->m_user && e == cudaSuccess)
+          e = cudaMemcpyAsync(S->h_sol + off, P->y_stage, sizeof(double) * size_t(P->m_user),
+                              cudaMemcpyDeviceToHost, S->stream);
         off += size_t(P->m_user);
       }
-      cudaStreamSynchronize(S->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+      sol_ok = e == cudaSuccess;
     }
     std::vector<Live> keep;
     keep.reserve(size_t(count));
@@ -295,7 +316,7 @@ static void worker_loop(pdhcg_server* S) {
       const SolverState& st = S->h_states[l.slot];
       Done d;
       fill_result(l.P, st, &d.res);
-      if (st.device_error || rc != PDHCG_OK || !S->h_sol) d.res.status = PDHCG_NUMERICAL_ERROR;
+      if (st.device_error || rc != PDHCG_OK || !sol_ok) d.res.status = PDHCG_NUMERICAL_ERROR;
       const size_t n = size_t(l.P->n), m = size_t(l.P->m_user);
       if (S->h_sol) {
         d.x.assign(S->h_sol + off, S->h_sol + off + n);
@@ -355,16 +376,24 @@ int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_para
   S->max_queue = size_t(max_slots) * 64;
   S->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&S->device);
-  S->launch_bytes = sizeof(Inst<double, double>) * size_t(max_slots) + sizeof(int32_t) * (size_t(max_slots) + 8);
+  // one slice's descriptors, queue and group scratch (at most 2048 group CTAs)
+  S->launch_bytes = batch_scratch_bytes(max_slots, std::min(max_slots, 1024), 2048);
   if (cudaMalloc(&S->d_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
       cudaMalloc(&S->d_launch, S->launch_bytes) != cudaSuccess ||
       cudaMallocHost(&S->h_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
       cudaMallocHost(&S->h_init, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->group_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming) != cudaSuccess) {
     if (S->d_states) cudaFree(S->d_states);
     if (S->d_launch) cudaFree(S->d_launch);
     if (S->h_states) cudaFreeHost(S->h_states);
     if (S->h_init) cudaFreeHost(S->h_init);
+    if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
+    if (S->group_stream) cudaStreamDestroy(S->group_stream);
+    if (S->ev_ready) cudaEventDestroy(S->ev_ready);
+    if (S->ev_done) cudaEventDestroy(S->ev_done);
     delete S;
     set_error("server_create: allocation failed");
     return PDHCG_E_OOM;
@@ -472,6 +501,12 @@ void pdhcg_server_destroy(pdhcg_server_t* S) {
   for (auto& l : S->ready) pdhcg_destroy(l.P);
   if (S->admit_stream) cudaStreamSynchronize(S->admit_stream);
   if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
+  if (S->group_stream) {
+    cudaStreamSynchronize(S->group_stream);
+    cudaStreamDestroy(S->group_stream);
+  }
+  if (S->ev_ready) cudaEventDestroy(S->ev_ready);
+  if (S->ev_done) cudaEventDestroy(S->ev_done);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   if (S->pinned_stage) cudaFreeHost(S->pinned_stage);
   if (S->h_init) cudaFreeHost(S->h_init);

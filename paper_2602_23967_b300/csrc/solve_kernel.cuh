@@ -915,12 +915,21 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     }
     S.K += 1;
     if (plan.iter_budget > 0 && S.K - K_first >= plan.iter_budget) break;  // paused
-    if (plan.slice_ns > 0 && g.nblk == 1 && ((S.K - K_first) & 15) == 0) {
-      if (threadIdx.x == 0) sm_pause = globaltimer_ns() - t_resume >= plan.slice_ns;
-      __syncthreads();
-      const bool pause = sm_pause != 0;
-      __syncthreads();  // thread 0 rewrites sm_pause only after every thread has read it
-      if (pause) break;  // paused
+    if (plan.slice_ns > 0 && ((S.K - K_first) & 15) == 0) {
+      if (g.nblk == 1) {
+        if (threadIdx.x == 0) sm_pause = globaltimer_ns() - t_resume >= plan.slice_ns;
+        __syncthreads();
+        const bool pause = sm_pause != 0;
+        __syncthreads();  // thread 0 rewrites sm_pause only after every thread has read it
+        if (pause) break;  // paused
+      } else {
+        // a group pauses as one: rank 0's clock decides, and the max-reduction
+        // hands every CTA the same decision
+        double pv[1] = {(g.rank == 0 && threadIdx.x == 0 && globaltimer_ns() - t_resume >= plan.slice_ns) ? 1.0
+                                                                                                        : 0.0};
+        if (!group_reduce<BS, 1>(g, pv, 1u)) { ok = false; break; }
+        if (pv[0] > 0.0) break;  // paused
+      }
     }
   }
   if (!ok) S.device_error = 1;
@@ -1082,6 +1091,7 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
   g.rank = 0;
   g.bar32 = nullptr;
   g.part = nullptr;
+  if (plan.npool <= 0) return;  // a launch of groups only
   while (true) {
     if (threadIdx.x == 0) sm_idx = atomicAdd(plan.pool_next, 1);
     __syncthreads();

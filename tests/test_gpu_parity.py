@@ -409,3 +409,39 @@ def test_golden_step_trace_on_gpu(precision):
             assert r["status_name"] == "ITERATION_LIMIT" and r["iterations"] == K, r
             np.testing.assert_allclose(x, xs, rtol=tol, err_msg=f"theta={case['theta']} K={K}")
             np.testing.assert_allclose(y, ys, rtol=tol, err_msg=f"theta={case['theta']} K={K}")
+
+
+def test_batch_runs_large_instances_on_groups():
+    # a batch mixing small instances (pool CTAs) with large ones, which
+    # pdhcg_solve_batch runs on multi-CTA groups in the same cooperative
+    # launch: FP64 iterates after 100 steps equal the oracle's for every
+    # instance, and a double-float solve of the batch reaches the oracle's
+    # KKT bar and objective
+    qps = [W.mpc_qp(seed=600 + i) for i in range(4)] + [W.random_qp(seed=3)]
+    qps += [W.large_sparse_qp(n=20000, m=10000, seed=3), W.factor_portfolio(n=30000, k=300, seed=4)]
+    N = 100
+    probs = [pdhcg.Problem(q, pdhcg.default_params(max_iter=N)) for q in qps]
+    try:
+        out = pdhcg.solve_batch(probs)
+        etas = [p.eta()[0] for p in probs]
+    finally:
+        for p in probs:
+            p.close()
+    for q, (x, y, r), eta in zip(qps, out, etas):
+        xo, yo, ro = oracle.solve(q, oracle.default_params(max_iter=N, eta_override=eta))
+        assert r["iterations"] == ro["iterations"] == N
+        assert r["inner_iterations"] == ro["inner_iterations"], q.name
+        assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo))), q.name
+        assert np.max(np.abs(y - yo)) <= 1e-10 * (1 + np.max(np.abs(yo))), q.name
+    probs = pdhcg.create_batch(qps, pdhcg.default_params(precision="dfloat", eps_tol=1e-6, max_iter=400000))
+    try:
+        out = pdhcg.solve_batch(probs)
+    finally:
+        for p in probs:
+            p.close()
+    for q, (x, y, r) in zip(qps, out):
+        assert r["status_name"] == "OPTIMAL", (q.name, r)
+        rp, rd, rg, pobj, _ = kkt_of(q, x, y)
+        assert max(rp, rd, rg) <= 1e-6, (q.name, rp, rd, rg)
+        _, _, ro = oracle.solve(q, oracle.default_params(eps_tol=1e-6))
+        assert rel(pobj, ro["primal_obj"]) <= 1e-6, (q.name, pobj, ro["primal_obj"])

@@ -103,3 +103,44 @@ def test_invalid_request_rejected_alone():
         assert got[good][2]["status_name"] == "OPTIMAL"
     finally:
         srv.close()
+
+
+def _served(prm, qps, slots=16, gap=0.001):
+    srv = pdhcg.Server(hbm_budget_bytes=8 << 30, max_slots=slots, params=prm)
+    try:
+        tickets = []
+        for q in qps:
+            tickets.append(srv.submit(q))
+            time.sleep(gap)
+        got = wait_all(srv, tickets, timeout=600.0)
+        st = srv.stats()
+    finally:
+        srv.close()
+    return [got[t] for t in tickets], st
+
+
+def test_mix_with_large_requests_equal_alone():
+    # The request mix of the serving workload at test size: MPC QPs on pool
+    # CTAs, and random QPs (one made infeasible by a contradictory equality
+    # row, Sec. 5.1) and a factor-model QP large enough to run on multi-CTA
+    # groups, in a cooperative launch of their own beside the pool launch of
+    # each slice.  Every request's result is the same served alone and in the
+    # mix: pool solves keep their 128-thread kernel and groups their size, so
+    # the arithmetic does not depend on what else is live.
+    prm = pdhcg.default_params(precision="dfloat", eps_tol=1e-6, max_iter=400000)
+    qps = ([W.mpc_qp(seed=500 + i) for i in range(6)] +
+           [W.build_request("random", 61, 8000), W.build_request("random_infeasible", 62, 6000),
+            W.factor_portfolio(n=30000, k=300, seed=63), W.build_request("random", 64, 1500)])
+    mixed, st = _served(prm, qps)
+    assert st["completed"] == len(qps) and st["launches"] > 1
+    for q, (xm, ym, rm) in zip(qps, mixed):
+        alone, _ = _served(prm, [q])
+        xs, ys, rs = alone[0]
+        assert rm["status_name"] == rs["status_name"], (q.name, rm, rs)
+        assert rm["iterations"] == rs["iterations"], q.name
+        assert np.max(np.abs(xm - xs)) <= 1e-12 * (1 + np.max(np.abs(xs))), q.name
+        if q.m:
+            assert np.max(np.abs(ym - ys)) <= 1e-12 * (1 + np.max(np.abs(ys))), q.name
+    names = [r[2]["status_name"] for r in mixed]
+    assert names[7] == "PRIMAL_INFEASIBLE", names
+    assert all(n == "OPTIMAL" for i, n in enumerate(names) if i != 7), names
