@@ -117,6 +117,13 @@ typedef struct {
   double omega_clamp;         /* omega kept within [omega0/c, omega0*c] (1e5)                */
   int32_t group_blocks;       /* CTAs per instance in pdhcg_solve: 0 = auto                  */
   int32_t device_timeout_ms;  /* bound on any device-side wait (8000)                        */
+  /* Row layout (read at create; 0 = default): rows are sorted by length inside
+   * windows of sell_sigma rows and packed 32 to a slice, one lane per row
+   * (1024); rows longer than long_row get a warp each (64); rows of huge_row
+   * entries or more a whole CTA (2048). */
+  int32_t sell_sigma, long_row, huge_row;
+  int32_t pool_ctas_per_sm;   /* cap on resident pool CTAs per SM in batched solves: 0 = as
+                                 many as fit                                                 */
 } pdhcg_params;
 
 typedef struct {
@@ -232,6 +239,30 @@ int pdhcg_solve_batch(pdhcg_t* const* probs, int count, pdhcg_result* res, doubl
 #define PDHCG_NOALLOC_MAX_INSTANCES 1024
 int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* res,
                               double* const* x_out_dev, double* const* y_out_dev);
+
+/* ---- autotuner of the launch shape and row layout ----
+ * The paper has no counterpart (its kernels are not described).  Candidate
+ * settings of the row layout (sell_sigma, long_row, huge_row) and of the launch
+ * shape (group_blocks for a single problem; pool_ctas_per_sm for a batch) are
+ * timed on the device with CUDA events over a fixed number of PDHG steps of
+ * the given problems (count == 1: one multi-CTA solve; count > 1: one batched
+ * launch), and the fastest is written into *params.  The defaults are kept
+ * unless a candidate is faster by more than 3 %.  Results are cached per
+ * shape class (precision, batch or single, inner solver, size and row-length
+ * histogram bucket) for the life of the process: a later call of the same
+ * class returns the cached choice without timing (out->from_cache = 1).
+ * params: in, the base parameters; out, with the chosen fields set.
+ * The call creates and destroys its own handles and synchronises stream.
+ * Errors as pdhcg_create_batch. */
+typedef struct {
+  int32_t sell_sigma, long_row, huge_row, group_blocks, pool_ctas_per_sm; /* chosen (0 = default) */
+  int32_t candidates;               /* configurations timed (0 when taken from the cache)       */
+  int32_t from_cache;               /* 1: the shape class was tuned before in this process       */
+  double seconds_per_step;          /* chosen configuration: device seconds per PDHG step       */
+  double default_seconds_per_step;  /* the defaults, timed the same way                          */
+} pdhcg_tuning;
+int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdhcg_params* params, void* cuda_stream,
+                   pdhcg_tuning* out);
 
 /* eta used by the iteration and the ||A||_2 estimate of the scaled A (Sec. 3.2). */
 int pdhcg_get_eta(const pdhcg_t* prob, double* eta, double* norm_A);

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libpdhcg.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_f64.cu", "kernels_f32.cu", "kernels_mixed.cu", "kernels_dfloat.cu", "pdhcg_api.cu",
-              "pdhcg_server.cu", "selftest.cu"]
+              "pdhcg_server.cu", "selftest.cu", "autotune.cu"]
 CPP_SOURCES = ["host_prep.cpp"]
 
 

@@ -235,8 +235,29 @@ void lift_box_rows(HostQP* h) {
   transpose(h->m, n, h->Ap, h->Ac, h->Av, h->ATp, h->ATc, h->ATv);
 }
 
+SellLayout sell_layout_of(const pdhcg_params& p) {
+  SellLayout l;
+  if (p.sell_sigma > 0) l.sigma = p.sell_sigma;
+  if (p.long_row > 0) l.long_row = p.long_row;
+  if (p.huge_row > 0) l.huge_row = p.huge_row;
+  return l;
+}
+
+int pick_fastest(const std::vector<double>& seconds, double margin) {
+  int best = -1;
+  for (size_t i = 0; i < seconds.size(); ++i) {
+    const double t = seconds[i];
+    if (!(t > 0.0) || !std::isfinite(t)) continue;
+    if (best < 0 || t < seconds[size_t(best)]) best = int(i);
+  }
+  if (best <= 0) return best < 0 ? -1 : 0;
+  const double t0 = seconds[0];
+  if (t0 > 0.0 && std::isfinite(t0) && seconds[size_t(best)] >= t0 * (1.0 - margin)) return 0;
+  return best;
+}
+
 void build_sell(int32_t nrows, int nmat, const std::vector<int32_t>* rp[2],
-                const std::vector<int32_t>* ci[2], SellHost* out) {
+                const std::vector<int32_t>* ci[2], SellHost* out, const SellLayout& lay) {
   out->perm.clear();
   out->longs.clear();
   out->huges.clear();
@@ -246,16 +267,17 @@ void build_sell(int32_t nrows, int nmat, const std::vector<int32_t>* rp[2],
   for (int32_t r = 0; r < nrows; ++r) {
     int64_t mx = 0;
     for (int k = 0; k < nmat; ++k) mx = std::max(mx, len(k, r));
-    if (mx >= kHugeRow) out->huges.push_back(r);
-    else if (mx > kLongRow) out->longs.push_back(r);
+    if (mx >= lay.huge_row) out->huges.push_back(r);
+    else if (mx > lay.long_row) out->longs.push_back(r);
     else regular.push_back(r);
   }
   // sort by combined length (descending) inside windows of sigma rows
   std::vector<int64_t> tot(size_t(nrows), 0);
   for (int32_t r : regular)
     for (int k = 0; k < nmat; ++k) tot[size_t(r)] += len(k, r);
-  for (size_t w0 = 0; w0 < regular.size(); w0 += kSellSigma) {
-    const size_t w1 = std::min(regular.size(), w0 + kSellSigma);
+  const size_t sigma = size_t(std::max(lay.sigma, 1));
+  for (size_t w0 = 0; w0 < regular.size(); w0 += sigma) {
+    const size_t w1 = std::min(regular.size(), w0 + sigma);
     std::stable_sort(regular.begin() + long(w0), regular.begin() + long(w1),
                      [&](int32_t a, int32_t b) { return tot[size_t(a)] > tot[size_t(b)]; });
   }

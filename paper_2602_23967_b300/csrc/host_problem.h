@@ -52,8 +52,21 @@ struct SellHost {
 constexpr int kSellSigma = 1024;
 constexpr int64_t kLongRow = 64;
 constexpr int64_t kHugeRow = 2048;
+// Row layout: rows sorted by length inside windows of sigma rows; rows longer
+// than long_row are summed by a warp each, rows of huge_row or more by a CTA.
+struct SellLayout {
+  int32_t sigma = kSellSigma;
+  int64_t long_row = kLongRow;
+  int64_t huge_row = kHugeRow;
+};
+// The layout a params struct asks for (0 fields = the defaults above).
+SellLayout sell_layout_of(const pdhcg_params& p);
 void build_sell(int32_t nrows, int nmat, const std::vector<int32_t>* rp[2],
-                const std::vector<int32_t>* ci[2], SellHost* out);
+                const std::vector<int32_t>* ci[2], SellHost* out, const SellLayout& lay = SellLayout{});
+// Autotuner selection: the index of the fastest timing, except that candidate
+// 0 (the defaults) is kept unless another one is faster by more than the
+// relative margin; negative or non-finite timings (failed runs) never win.
+int pick_fastest(const std::vector<double>& seconds, double margin);
 // Split items with the given weights into nblk contiguous ranges (nblk + 1 bounds).
 std::vector<int32_t> split_balanced(const std::vector<int64_t>& w, int nblk);
 

@@ -829,6 +829,10 @@ int pdhcg_default_params(pdhcg_params* p) {
   p->omega_clamp = 1e5;
   p->group_blocks = 0;
   p->device_timeout_ms = 8000;
+  p->sell_sigma = 0;
+  p->long_row = 0;
+  p->huge_row = 0;
+  p->pool_ctas_per_sm = 0;
   return PDHCG_OK;
 }
 
@@ -840,7 +844,9 @@ static int check_params(const pdhcg_params* p) {
   if (p->precision < 0 || p->precision > 3 || p->k_eval < 1 || p->max_iter < 1 ||
       !(p->eps_tol > 0) || !(p->eps_inf > 0) || p->max_inner_iter < 0 || p->ruiz_iters < 0 ||
       p->inner < 0 || p->inner > 4 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
-      (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1))))) {
+      (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1)))) ||
+      p->sell_sigma < 0 || p->long_row < 0 || p->huge_row < 0 || p->pool_ctas_per_sm < 0 ||
+      sell_layout_of(*p).long_row >= sell_layout_of(*p).huge_row) {
     set_error("params: value out of range");
     return PDHCG_E_INVALID;
   }
@@ -894,12 +900,13 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
     P->lanes_con = lanes_for(avg_a);
     if (prm.lanes_override) P->lanes_var = P->lanes_con = prm.lanes_override;
   }
+  const SellLayout lay = sell_layout_of(prm);
   const std::vector<int32_t>* vrp[2] = {&h->ATp, &h->Qp};
   const std::vector<int32_t>* vci[2] = {&h->ATc, &h->Qc};
-  build_sell(h->n, h->has_q ? 2 : 1, vrp, vci, &P->vsell);
+  build_sell(h->n, h->has_q ? 2 : 1, vrp, vci, &P->vsell, lay);
   const std::vector<int32_t>* crp[2] = {&h->Ap, nullptr};
   const std::vector<int32_t>* cci[2] = {&h->Ac, nullptr};
-  build_sell(h->m, 1, crp, cci, &P->csell);
+  build_sell(h->m, 1, crp, cci, &P->csell, lay);
   P->vsell_cols[0] = P->vsell.col[0].size();
   P->vsell_cols[1] = P->vsell.col[1].size();
   P->csell_cols = P->csell.col[0].size();
@@ -909,7 +916,7 @@ int prepare_problem(const CreateInput& in, const pdhcg_params& prm, void* stream
     P->Rp = h->Rp;
     const std::vector<int32_t>* rrp[2] = {&h->Rp, nullptr};
     const std::vector<int32_t>* rci[2] = {&h->Rc, nullptr};
-    build_sell(h->k, 1, rrp, rci, &P->rsell);
+    build_sell(h->k, 1, rrp, rci, &P->rsell, lay);
     P->rsell_cols = P->rsell.col[0].size();
   }
   *out = P;
@@ -1165,8 +1172,9 @@ int check_params_c(const pdhcg_params* p) { return check_params(p); }
 //   * two launches (serving slices, group_stream given): the pool keeps its own
 //     128-thread kernel, so a small request's arithmetic does not depend on
 //     what else is live, and the groups run in a cooperative launch of their
-//     own on group_stream, concurrently; groups take at most three quarters
-//     of the co-resident CTAs while pool instances are live.
+//     own on group_stream (created at low priority, so waiting pool CTAs are
+//     scheduled first), concurrently; groups take at most half of the
+//     co-resident CTAs while pool instances are live.
 // A large instance that finds no room runs on a pool CTA (skip_unplaced =
 // false), or sits the launch out (skip_unplaced = true: a serving slice, where
 // it gets its group in a later slice).
@@ -1235,7 +1243,7 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
   const size_t coop_smem = split ? 0 : need;
   const int cap = any_large ? std::max(1, group_blocks_per_sm<M, V>(coop_smem)) * sms : 0;
   int gcap = cap;
-  if (nsmall > 0) gcap = split ? (3 * cap) / 4 : std::max(0, cap - std::min(nsmall, cap / 2));
+  if (nsmall > 0) gcap = split ? cap / 2 : std::max(0, cap - std::min(nsmall, cap / 2));
   BatchGroups bg;
   if (any_large) bg = plan_groups(probs, order, count, gcap, skip_unplaced);
   else bg.pool.assign(order, order + count);
@@ -1320,7 +1328,8 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
     if (e != cudaSuccess) return cuda_fail(e, "group launch");
   }
   if (npool > 0) {
-    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    if (P0->prm.pool_ctas_per_sm > 0) per_sm = std::min(per_sm, P0->prm.pool_ctas_per_sm);
     const cudaError_t e = launch_solve<M, V>(di, pool, std::max(1, std::min(npool, per_sm * sms)), s);
     if (e != cudaSuccess) {
       if (ng > 0) (void)cudaStreamSynchronize(split->group_stream);

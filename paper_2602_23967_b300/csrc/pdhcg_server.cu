@@ -103,7 +103,8 @@ struct pdhcg_server {
   cudaStream_t admit_stream = nullptr;
   // large requests' multi-CTA groups run in a cooperative launch of their own on
   // group_stream, beside the pool launch of the slice
-  cudaStream_t group_stream = nullptr;
+  cudaStream_t group_stream = nullptr;  // lowest priority: waiting pool CTAs go first
+  int prio_low = 0, prio_high = 0;
   cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
   std::thread admitter;
   cudaMemPool_t pool = nullptr;     // device arenas of admitted requests (stream-ordered)
@@ -383,7 +384,8 @@ int pdhcg_server_create(size_t hbm_budget_bytes, int max_slots, const pdhcg_para
       cudaMallocHost(&S->h_states, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
       cudaMallocHost(&S->h_init, sizeof(SolverState) * size_t(max_slots)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->group_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&S->prio_low, &S->prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&S->group_stream, cudaStreamNonBlocking, S->prio_low) != cudaSuccess ||
       cudaEventCreateWithFlags(&S->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming) != cudaSuccess) {
     if (S->d_states) cudaFree(S->d_states);

@@ -799,16 +799,21 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       if (!group_sync<BS>(g)) { ok = false; break; }
     }
 
-    // Phase II
-    double red2[3];
+    // Phase II.  Slot 3 carries a group's pause decision for time slices: rank
+    // 0's clock decides, and the max-reduction hands every CTA the same value.
+    double red2[4];
     {
       const Red<3> r = phase2<BS, LM>(I, prank, method, cur, vlo, vhi, sc, rc);
       red2[0] = r.v[0];
       red2[1] = r.v[1];
       red2[2] = r.v[2];
+      red2[3] = (plan.slice_ns > 0 && g.nblk > 1 && g.rank == 0 && threadIdx.x == 0 &&
+                 globaltimer_ns() - t_resume >= plan.slice_ns)
+                    ? 1.0
+                    : 0.0;
     }
     PDHCG_CLK(3);
-    if (!group_reduce<BS, 3, kWT>(g, red2, 0u)) { ok = false; break; }
+    if (!group_reduce<BS, 4, kWT>(g, red2, 1u << 3)) { ok = false; break; }
     PDHCG_CLK(5);
     const double dy2 = red2[0];
     const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
@@ -915,21 +920,13 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     }
     S.K += 1;
     if (plan.iter_budget > 0 && S.K - K_first >= plan.iter_budget) break;  // paused
-    if (plan.slice_ns > 0 && ((S.K - K_first) & 15) == 0) {
-      if (g.nblk == 1) {
-        if (threadIdx.x == 0) sm_pause = globaltimer_ns() - t_resume >= plan.slice_ns;
-        __syncthreads();
-        const bool pause = sm_pause != 0;
-        __syncthreads();  // thread 0 rewrites sm_pause only after every thread has read it
-        if (pause) break;  // paused
-      } else {
-        // a group pauses as one: rank 0's clock decides, and the max-reduction
-        // hands every CTA the same decision
-        double pv[1] = {(g.rank == 0 && threadIdx.x == 0 && globaltimer_ns() - t_resume >= plan.slice_ns) ? 1.0
-                                                                                                        : 0.0};
-        if (!group_reduce<BS, 1>(g, pv, 1u)) { ok = false; break; }
-        if (pv[0] > 0.0) break;  // paused
-      }
+    if (plan.slice_ns > 0 && g.nblk > 1 && red2[3] > 0.0) break;  // paused (group, every step)
+    if (plan.slice_ns > 0 && g.nblk == 1 && ((S.K - K_first) & 15) == 0) {
+      if (threadIdx.x == 0) sm_pause = globaltimer_ns() - t_resume >= plan.slice_ns;
+      __syncthreads();
+      const bool pause = sm_pause != 0;
+      __syncthreads();  // thread 0 rewrites sm_pause only after every thread has read it
+      if (pause) break;  // paused
     }
   }
   if (!ok) S.device_error = 1;

@@ -51,6 +51,8 @@ class Params(C.Structure):
         ("power_tol", C.c_double), ("eta_override", C.c_double), ("omega0_override", C.c_double),
         ("omega_clamp", C.c_double),
         ("group_blocks", C.c_int32), ("device_timeout_ms", C.c_int32),
+        ("sell_sigma", C.c_int32), ("long_row", C.c_int32), ("huge_row", C.c_int32),
+        ("pool_ctas_per_sm", C.c_int32),
     ]
 
 
@@ -75,6 +77,13 @@ class ProblemData(C.Structure):
     _fields_ = [("Q", C.POINTER(Csr)), ("A", C.POINTER(Csr)), ("c", C.POINTER(C.c_double)),
                 ("lc", C.POINTER(C.c_double)), ("uc", C.POINTER(C.c_double)),
                 ("lv", C.POINTER(C.c_double)), ("uv", C.POINTER(C.c_double))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("sell_sigma", C.c_int32), ("long_row", C.c_int32), ("huge_row", C.c_int32),
+                ("group_blocks", C.c_int32), ("pool_ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
+                ("from_cache", C.c_int32), ("seconds_per_step", C.c_double),
+                ("default_seconds_per_step", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -116,6 +125,7 @@ def lib():
                                      C.POINTER(C.c_size_t)]
         L.pdhcg_get_phase_times.argtypes = [_P, _D]
         L.pdhcg_get_device.argtypes = [_P, C.POINTER(C.c_int32)]
+        L.pdhcg_autotune.argtypes = [C.c_int, C.POINTER(ProblemData), C.POINTER(Params), _P, C.POINTER(Tuning)]
         L.pdhcg_destroy.argtypes = [_P]
         L.pdhcg_destroy.restype = None
         L.pdhcg_strerror.restype = C.c_char_p
@@ -266,18 +276,37 @@ class Problem:
             pass
 
 
-def create_batch(qps, params: Params | None = None, stream=None):
-    """Create many Problems at once (pdhcg_create_batch: shared allocation, one setup launch)."""
-    if any(getattr(q, "R", None) is not None for q in qps):
-        raise ValueError("create_batch takes plain Q; create structured (Q + R^T R) problems one by one")
-    params = params if params is not None else default_params()
+def _problem_table(qps):
+    """The pdhcg_problem_data array of qps (with the buffers it points into)."""
     holds = [_qp_args(q) for q in qps]
-    # the pdhcg_problem_data array: seven pointers per problem, filled as integers
     addr = np.array([(C.addressof(h["Q"].s) if "Q" in h else 0, C.addressof(h["A"].s), h["c"].ctypes.data,
                       h["lc"].ctypes.data if h["lc"].size else 0, h["uc"].ctypes.data if h["uc"].size else 0,
                       h["lv"].ctypes.data, h["uv"].ctypes.data) for h in holds],
                     dtype=np.uint64).reshape(len(qps), 7)
     assert C.sizeof(ProblemData) == 7 * 8
+    return holds, addr
+
+
+def autotune(qps, params: Params | None = None, stream=None):
+    """pdhcg_autotune: time the row-layout and launch-shape candidates on qps
+    (one problem: a single solve; several: a batched launch) and return
+    (params with the chosen settings, report dict)."""
+    p = Params()
+    C.memmove(C.byref(p), C.byref(params if params is not None else default_params()), C.sizeof(Params))
+    holds, addr = _problem_table(qps)
+    t = Tuning()
+    check(lib().pdhcg_autotune(len(qps), addr.ctypes.data_as(C.POINTER(ProblemData)), C.byref(p),
+                               _P(stream) if stream else None, C.byref(t)), "pdhcg_autotune")
+    return p, {k: getattr(t, k) for k, _ in t._fields_}
+
+
+def create_batch(qps, params: Params | None = None, stream=None):
+    """Create many Problems at once (pdhcg_create_batch: shared allocation, one setup launch)."""
+    if any(getattr(q, "R", None) is not None for q in qps):
+        raise ValueError("create_batch takes plain Q; create structured (Q + R^T R) problems one by one")
+    params = params if params is not None else default_params()
+    # the pdhcg_problem_data array: seven pointers per problem, filled as integers
+    holds, addr = _problem_table(qps)
     data = addr.ctypes.data_as(C.POINTER(ProblemData))
     handles = (_P * len(qps))()
     check(lib().pdhcg_create_batch(len(qps), data, C.byref(params), _P(stream) if stream else None,

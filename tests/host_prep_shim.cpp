@@ -34,6 +34,33 @@ int shim_build_sell(int32_t nrows, const int32_t* rp1, const int32_t* ci1, const
   return 0;
 }
 
+// The same with a row layout of its own (sort window, long and huge row lengths).
+int shim_build_sell_layout(int32_t nrows, const int32_t* rp1, const int32_t* ci1, const int32_t* rp2,
+                           const int32_t* ci2, int32_t sigma, int64_t long_row, int64_t huge_row) {
+  const int nmat = rp2 ? 2 : 1;
+  const int32_t* rps[2] = {rp1, rp2};
+  const int32_t* cis[2] = {ci1, ci2};
+  const std::vector<int32_t>* rp[2] = {nullptr, nullptr};
+  const std::vector<int32_t>* ci[2] = {nullptr, nullptr};
+  for (int k = 0; k < nmat; ++k) {
+    g_rp[k].assign(rps[k], rps[k] + nrows + 1);
+    g_ci[k].assign(cis[k], cis[k] + rps[k][nrows]);
+    rp[k] = &g_rp[k];
+    ci[k] = &g_ci[k];
+  }
+  pdhcg::SellLayout lay;
+  lay.sigma = sigma;
+  lay.long_row = long_row;
+  lay.huge_row = huge_row;
+  pdhcg::build_sell(nrows, nmat, rp, ci, &g_sell, lay);
+  return 0;
+}
+
+// The autotuner's selection rule on given timings.
+int shim_pick_fastest(const double* seconds, int32_t n, double margin) {
+  return pdhcg::pick_fastest(std::vector<double>(seconds, seconds + n), margin);
+}
+
 // sizes[0..5]: nslices, longs, huges, columns of matrix 0, of matrix 1, nmat-1 slots used.
 void shim_sizes(int64_t* sizes) {
   sizes[0] = g_sell.nslices;

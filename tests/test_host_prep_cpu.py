@@ -44,14 +44,19 @@ def _p(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
 
-def pack(L, mats):
-    """Run build_sell on one or two CSR matrices with the same row count."""
+def pack(L, mats, layout=None):
+    """Run build_sell on one or two CSR matrices with the same row count
+    (layout: (sigma, long_row, huge_row), or None for the defaults)."""
     rps = [np.ascontiguousarray(M.indptr, dtype=np.int32) for M in mats]
     cis = [np.ascontiguousarray(M.indices, dtype=np.int32) for M in mats]
     nrows = mats[0].shape[0]
     two = len(mats) == 2
-    L.shim_build_sell(C.c_int32(nrows), _p(rps[0], C.c_int32), _p(cis[0], C.c_int32),
-                      _p(rps[1], C.c_int32) if two else None, _p(cis[1], C.c_int32) if two else None)
+    args = (C.c_int32(nrows), _p(rps[0], C.c_int32), _p(cis[0], C.c_int32),
+            _p(rps[1], C.c_int32) if two else None, _p(cis[1], C.c_int32) if two else None)
+    if layout is None:
+        L.shim_build_sell(*args)
+    else:
+        L.shim_build_sell_layout(*args, C.c_int32(layout[0]), C.c_int64(layout[1]), C.c_int64(layout[2]))
     sz = np.zeros(6, dtype=np.int64)
     L.shim_sizes(_p(sz, C.c_int64))
     ns, nl, nh, c0, c1, p1 = (int(v) for v in sz)
@@ -75,7 +80,7 @@ def random_rows(rng, nrows, ncols, lengths):
     return sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(nrows, ncols))
 
 
-def check_layout(mats, out):
+def check_layout(mats, out, SIGMA=SIGMA, LONG=LONG, HUGE=HUGE):
     nrows = mats[0].shape[0]
     lens = np.array([np.diff(M.indptr) for M in mats])        # nmat x nrows
     mx, tot = lens.max(axis=0), lens.sum(axis=0)
@@ -196,3 +201,32 @@ def test_lift_box_rows(shim):
     np.testing.assert_array_equal(lc2, np.concatenate([lc, lv[boxed]]))
     np.testing.assert_array_equal(uc2, np.concatenate([uc, uv[boxed]]))
     assert np.all(np.isneginf(lv2)) and np.all(np.isposinf(uv2)) and np.all(vt == 0)
+
+
+@pytest.mark.parametrize("layout", [(128, 64, 2048), (8192, 32, 2048), (1024, 16, 200), (32, 128, 8192)])
+def test_sell_packing_other_layouts(shim, layout):
+    # the layouts the autotuner tries: other sort windows and long / huge thresholds
+    rng = np.random.default_rng(11)
+    nrows, ncols = 3000, 5000
+    lengths = rng.integers(0, 40, nrows)
+    lengths[rng.integers(0, nrows, 5)] = rng.integers(100, 400, 5)
+    lengths[rng.integers(0, nrows)] = 2500
+    M = random_rows(rng, nrows, ncols, lengths)
+    sg, lo, hu = layout
+    check_layout([M], pack(shim, [M], layout), SIGMA=sg, LONG=lo, HUGE=hu)
+
+
+def test_autotune_selection_rule(shim):
+    shim.shim_pick_fastest.restype = C.c_int
+
+    def pick(ts, margin=0.03):
+        a = np.array(ts, dtype=np.float64)
+        return shim.shim_pick_fastest(_p(a, C.c_double), C.c_int32(len(a)), C.c_double(margin))
+
+    assert pick([1.0, 0.5, 0.9]) == 1               # a clear winner
+    assert pick([1.0, 0.98, 0.99]) == 0             # within the margin: keep the defaults
+    assert pick([1.0, 0.96]) == 1                   # 4 % faster beats a 3 % margin
+    assert pick([1.0, -1.0, float("nan"), 0.2]) == 3  # failed runs never win
+    assert pick([-1.0, 2.0, 1.5]) == 2              # the defaults failed: the fastest that ran
+    assert pick([-1.0, float("inf")]) == -1         # nothing ran
+    assert pick([0.7]) == 0
