@@ -54,6 +54,8 @@ def parse():
                     help="instead of the benchmark: the adaptive inner tolerance (Sec. 3.3) against fixed ones")
     ap.add_argument("--large-iters", type=int, default=128,
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
+    ap.add_argument("--large-n", type=int, default=2_000_000,
+                    help="variables of that QP (m = n/2); smaller values are for profiling captures")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[200.0, 2000.0],
                     help="Poisson arrival rates (requests/s) of the serving traces; none skips serving")
     ap.add_argument("--serve-eps", type=float, nargs="*", default=[1e-4, 1e-6])
@@ -305,7 +307,7 @@ def large_instance_leg(args, stream, peak_gbs):
     number of PDHG steps, and the algorithmic bytes they stream."""
     import torch
     from paper_2602_23967_b300 import pdhcg
-    qp = W.large_sparse_qp(seed=0)
+    qp = W.large_sparse_qp(n=args.large_n, m=args.large_n // 2, seed=0)
     prm = pdhcg.default_params(precision=args.precision, eps_tol=1e-12, max_iter=args.large_iters)
     tune = None
     if args.autotune:

@@ -124,6 +124,11 @@ typedef struct {
   int32_t sell_sigma, long_row, huge_row;
   int32_t pool_ctas_per_sm;   /* cap on resident pool CTAs per SM in batched solves: 0 = as
                                  many as fit                                                 */
+  int32_t pipeline;           /* pdhcg_solve of a large problem as a CUDA graph of one kernel
+                                 per phase, with device-driven conditional nodes: 0 = when
+                                 the problem is large enough to fill the GPU (and Q is not
+                                 structured), 1 = always (error if the graph cannot be
+                                 built), -1 = never (the persistent multi-CTA kernel)         */
 } pdhcg_params;
 
 typedef struct {

@@ -210,6 +210,10 @@ struct pdhcg_problem {
   int batch_nblk = 1;
   int32_t* batch_part = nullptr;
   std::vector<int32_t> batch_tables;
+  // pipeline form of pdhcg_solve (built at the first solve that uses it)
+  int pipe_grid = 0;
+  void* pipe_scratch = nullptr;        // PipeState, then kSlots * pipe_grid partial sums
+  cudaGraphExec_t pipe_exec = nullptr;
   // setup results
   pdhcg::SolverState setup_state{};
   pdhcg::SolverState last_state{};  // state at the end of the last pdhcg_solve / _dev

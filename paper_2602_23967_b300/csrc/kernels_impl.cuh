@@ -1,6 +1,7 @@
 // kernels_impl.cuh — launch wrappers, included once per precision.
 #pragma once
 #include "launch.h"
+#include "pipeline_kernel.cuh"
 #include "setup_kernel.cuh"
 #include "solve_kernel.cuh"
 
@@ -124,6 +125,123 @@ cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, in
   return cudaGetLastError();
 }
 
+// ---- the pipeline graph of one large instance (pipeline_kernel.cuh) ----
+namespace {
+struct GraphBuilder {
+  cudaError_t err = cudaSuccess;
+  cudaGraphNode_t kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* fn, int grid, void* args) {
+    cudaGraphNode_t n = nullptr;
+    if (err != cudaSuccess) return n;
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = dim3(unsigned(grid));
+    kp.blockDim = dim3(kPipeBS);
+    kp.sharedMemBytes = 0;
+    void* params[] = {args};
+    kp.kernelParams = params;
+    err = cudaGraphAddKernelNode(&n, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+    return n;
+  }
+  // A conditional node (IF or WHILE) after dep; *body receives its body graph.
+  cudaGraphNode_t cond(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType t,
+                       cudaGraph_t* body) {
+    cudaGraphNode_t n = nullptr;
+    if (err != cudaSuccess) return n;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = t;
+    np.conditional.size = 1;
+    err = cudaGraphAddNode(&n, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &np);
+    if (err == cudaSuccess) *body = np.conditional.phGraph_out[0];
+    return n;
+  }
+  cudaGraphConditionalHandle handle(cudaGraph_t g, unsigned dflt) {
+    cudaGraphConditionalHandle h{};
+    if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&h, g, dflt, cudaGraphCondAssignDefault);
+    return h;
+  }
+};
+}  // namespace
+
+template <class MatT, class VecT>
+cudaError_t pipeline_build(const Inst<MatT, VecT>* d_inst, int grid, int method, void* state, double* part,
+                           cudaGraphExec_t* exec_out) {
+  *exec_out = nullptr;
+  cudaGraph_t root = nullptr;
+  cudaError_t e = cudaGraphCreate(&root, 0);
+  if (e != cudaSuccess) return e;
+  GraphBuilder B;
+  PipeArgs a{};
+  a.inst = d_inst;
+  a.ps = static_cast<PipeState*>(state);
+  a.part = part;
+  // conditional nodes first (a handle is made in the graph that holds its
+  // node), so that every kernel node gets the complete set of handles
+  cudaGraph_t body = nullptr, inner = nullptr, chk = nullptr, rst = nullptr, out = nullptr;
+  a.h.outer = B.handle(root, 1u);
+  const cudaGraphNode_t c_outer = B.cond(root, nullptr, a.h.outer, cudaGraphCondTypeWhile, &body);
+  cudaGraphNode_t c_inner = nullptr, c_check = nullptr, c_rst = nullptr, c_out = nullptr;
+  if (method != PDHCG_INNER_DIAG) {
+    a.h.inner = B.handle(body, 0u);
+    c_inner = B.cond(body, nullptr, a.h.inner, cudaGraphCondTypeWhile, &inner);
+  }
+  a.h.check = B.handle(body, 0u);
+  c_check = B.cond(body, nullptr, a.h.check, cudaGraphCondTypeIf, &chk);
+  a.h.restart = B.handle(chk, 0u);
+  c_rst = B.cond(chk, nullptr, a.h.restart, cudaGraphCondTypeIf, &rst);
+  a.h.out = B.handle(chk, 0u);
+  c_out = B.cond(chk, nullptr, a.h.out, cudaGraphCondTypeIf, &out);
+  // kernels, each after the node before it
+  auto dep = [&](cudaGraph_t g, cudaGraphNode_t from, cudaGraphNode_t to) {
+    if (B.err == cudaSuccess && from && to) B.err = cudaGraphAddDependencies(g, &from, &to, nullptr, 1);
+  };
+  const cudaGraphNode_t k_init = B.kernel(root, nullptr, (const void*)pipe_init<MatT, VecT>, grid, &a);
+  dep(root, k_init, c_outer);
+  const cudaGraphNode_t k_p1 = B.kernel(body, nullptr, (const void*)pipe_phase1<MatT, VecT>, grid, &a);
+  const cudaGraphNode_t k_xbar = B.kernel(body, nullptr, (const void*)pipe_xbar<MatT, VecT>, grid, &a);
+  const cudaGraphNode_t k_p2 = B.kernel(body, nullptr, (const void*)pipe_phase2<MatT, VecT>, grid, &a);
+  if (c_inner) {
+    dep(body, k_p1, c_inner);
+    dep(body, c_inner, k_xbar);
+    const bool cg = method == PDHCG_INNER_CG;
+    const cudaGraphNode_t i1 =
+        B.kernel(inner, nullptr, cg ? (const void*)pipe_cg_a<MatT, VecT> : (const void*)pipe_bb_b<MatT, VecT>, grid, &a);
+    const cudaGraphNode_t i2 =
+        B.kernel(inner, nullptr, cg ? (const void*)pipe_cg_b<MatT, VecT> : (const void*)pipe_bb_a<MatT, VecT>, grid, &a);
+    dep(inner, i1, i2);
+  } else {
+    dep(body, k_p1, k_xbar);
+  }
+  dep(body, k_xbar, k_p2);
+  dep(body, k_p2, c_check);
+  const cudaGraphNode_t k_chk = B.kernel(chk, nullptr, (const void*)pipe_check<MatT, VecT>, grid, &a);
+  dep(chk, k_chk, c_rst);
+  dep(chk, c_rst, c_out);
+  B.kernel(rst, nullptr, (const void*)pipe_restart<MatT, VecT>, grid, &a);
+  const cudaGraphNode_t k_rays = B.kernel(out, nullptr, (const void*)pipe_rays<MatT, VecT>, grid, &a);
+  const cudaGraphNode_t k_write = B.kernel(out, nullptr, (const void*)pipe_write<MatT, VecT>, grid, &a);
+  dep(out, k_rays, k_write);
+  if (B.err == cudaSuccess) B.err = cudaGraphInstantiate(exec_out, root, 0);
+  cudaGraphDestroy(root);
+  if (B.err != cudaSuccess) *exec_out = nullptr;
+  return B.err;
+}
+
+// Resident CTAs per SM of the pipeline's row kernels (the smallest of them).
+template <class MatT, class VecT>
+int pipeline_blocks_per_sm() {
+  int lo = 1 << 30;
+  for (const void* f : {(const void*)pipe_phase1<MatT, VecT>, (const void*)pipe_phase2<MatT, VecT>,
+                        (const void*)pipe_bb_a<MatT, VecT>, (const void*)pipe_cg_a<MatT, VecT>,
+                        (const void*)pipe_check<MatT, VecT>}) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kPipeBS, 0) != cudaSuccess) return 0;
+    lo = std::min(lo, nb);
+  }
+  return lo;
+}
+
 #define PDHCG_INSTANTIATE(MatT, VecT)                                                          \
   template cudaError_t kernel_limits<MatT, VecT>(KernelLimits*);                               \
   template cudaError_t launch_setup<MatT, VecT>(const SetupArgs<MatT, VecT>&, int,             \
@@ -134,6 +252,9 @@ cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, in
   template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
                                                      int32_t*, uint64_t, cudaStream_t);           \
   template cudaError_t launch_solve<MatT, VecT>(const Inst<MatT, VecT>*, const LaunchPlan&, int, \
-                                                cudaStream_t);
+                                                cudaStream_t);                                   \
+  template cudaError_t pipeline_build<MatT, VecT>(const Inst<MatT, VecT>*, int, int, void*, double*, \
+                                                  cudaGraphExec_t*);                              \
+  template int pipeline_blocks_per_sm<MatT, VecT>();
 
 }  // namespace pdhcg

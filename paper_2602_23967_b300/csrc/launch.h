@@ -51,6 +51,23 @@ template <class MatT, class VecT>
 cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan, int grid,
                          cudaStream_t s);
 
+// Pipeline form of one large instance (pipeline_kernel.cuh): the iteration as
+// a CUDA graph of ordinary kernels with device-driven conditional nodes, grid
+// CTAs each (the row partition of d_inst must be for grid CTAs).  state: a
+// device PipeState (its tickets zeroed before each launch), part: kSlots * grid
+// doubles.  On success *exec_out is the instantiated graph, launched once per
+// solve after the state and descriptor are uploaded.
+template <class MatT, class VecT>
+cudaError_t pipeline_build(const Inst<MatT, VecT>* d_inst, int grid, int method, void* state, double* part,
+                           cudaGraphExec_t* exec_out);
+template <class MatT, class VecT>
+int pipeline_blocks_per_sm();
+constexpr size_t kPipeStateBytes = 1024;  // >= sizeof(PipeState), checked where it is defined
+// The leading timer fields of PipeState (PDHCG_PIPE_TIMERS builds), as the host reads them.
+struct PipeClockView {
+  unsigned long long neg_first[12], ns_busy[12], count[12], t_last_end, ns_gap;
+};
+
 // Setup of count instances in one launch (one CTA per instance at a time).
 template <class MatT, class VecT>
 cudaError_t launch_setup_pool(const SetupArgs<MatT, VecT>* d_args, int count, int* next, int32_t* err,

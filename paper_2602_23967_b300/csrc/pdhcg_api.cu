@@ -726,10 +726,87 @@ int run_setup(pdhcg_problem* P) {
 }
 
 
+// Problems at least this large (the work measure of choose_group_blocks) run
+// pdhcg_solve in the pipeline form when params.pipeline is 0.
+constexpr int64_t kPipelineWork = int64_t(1) << 21;
+
+bool use_pipeline(const pdhcg_problem* P) {
+  if (P->prm.pipeline < 0 || P->k > 0 || P->max_blk <= 1) return false;
+  if (P->prm.pipeline > 0) return true;
+  const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ : 0) + 2 * P->nnzA + P->n + P->m;
+  return work >= kPipelineWork;
+}
+
+// One solve in the pipeline form: descriptor and initial state up, one graph
+// launch, state back.  The graph is built at the first call.
+int solve_pipeline(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_result* res,
+                   double* x_out_d, double* y_out_d) {
+  return dispatch_precision(P->precision, [&](auto tag) -> int {
+    using M = typename decltype(tag)::Mat;
+    using V = typename decltype(tag)::Vec;
+    if (!P->pipe_exec) {
+      int sms = 0;
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+      const int per_sm = pipeline_blocks_per_sm<M, V>();
+      if (per_sm < 1) {
+        set_error("pipeline: its kernels cannot be resident");
+        return PDHCG_E_CUDA;
+      }
+      const int grid = per_sm * sms;
+      if (!P->pipe_scratch) CK(cudaMalloc(&P->pipe_scratch, kPipeStateBytes + sizeof(double) * kSlots * size_t(grid)));
+      PartitionSet* ps = nullptr;
+      int rc = get_partition(P, grid, &ps);
+      if (rc) return rc;
+      double* part = reinterpret_cast<double*>(static_cast<char*>(P->pipe_scratch) + kPipeStateBytes);
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e = pipeline_build<M, V>(static_cast<const Inst<M, V>*>(P->inst_d), grid, P->method,
+                                                 P->pipe_scratch, part, &ex);
+      if (e != cudaSuccess) return cuda_fail(e, "pipeline graph");
+      P->pipe_exec = ex;
+      P->pipe_grid = grid;
+    }
+    PartitionSet* ps = nullptr;
+    int rc = get_partition(P, P->pipe_grid, &ps);
+    if (rc) return rc;
+    SolverState S = initial_state(P);
+    CK(cudaMemcpyAsync(P->st, &S, sizeof(S), cudaMemcpyHostToDevice, P->stream));
+    Inst<M, V> I = make_inst<M, V>(P);
+    I.x_init = x0_d;
+    I.y_init = y0_d;
+    I.x_out = x_out_d;
+    I.y_out = y_out_d;
+    set_partition(I, *ps, P);
+    CK(cudaMemcpyAsync(P->inst_d, &I, sizeof(I), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemsetAsync(P->pipe_scratch, 0, kPipeStateBytes, P->stream));
+    CK(cudaGraphLaunch(P->pipe_exec, P->stream));
+    CK(cudaMemcpyAsync(&S, P->st, sizeof(S), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+#if PDHCG_PIPE_TIMERS
+    {  // the kernels' device times into the phase-time categories
+      PipeClockView v{};
+      CK(cudaMemcpy(&v, P->pipe_scratch, sizeof(v), cudaMemcpyDeviceToHost));
+      const int cat[12] = {7, 0, 1, 2, 2, 1, 6, 3, 4, 6, 6, 6};
+      for (double& t : S.tm) t = 0.0;
+      for (int k = 0; k < 12; ++k) S.tm[cat[k]] += double(v.ns_busy[k]);
+      S.tm[5] += double(v.ns_gap);
+    }
+#endif
+    if (res) fill_result(P, S, res);
+    P->last_state = S;
+    return PDHCG_OK;
+  });
+}
+
 // One solve of one handle (device pointers for warm start / outputs).
 int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_result* res,
               double* x_out_d, double* y_out_d) {
   CK(cudaSetDevice(P->device));
+  if (use_pipeline(P)) {
+    const int rc = solve_pipeline(P, x0_d, y0_d, res, x_out_d, y_out_d);
+    if (rc == PDHCG_OK || P->prm.pipeline > 0) return rc;
+    // automatic choice: the persistent kernel when the graph is unavailable
+    P->prm.pipeline = -1;
+  }
   const int nblk = choose_group_blocks(P, P->max_blk);
   PartitionSet* ps = nullptr;
   if (nblk > 1) {
@@ -833,6 +910,7 @@ int pdhcg_default_params(pdhcg_params* p) {
   p->long_row = 0;
   p->huge_row = 0;
   p->pool_ctas_per_sm = 0;
+  p->pipeline = 0;
   return PDHCG_OK;
 }
 
@@ -846,6 +924,7 @@ static int check_params(const pdhcg_params* p) {
       p->inner < 0 || p->inner > 4 || !(p->omega_clamp >= 1.0) || p->power_max_iter < 1 ||
       (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1)))) ||
       p->sell_sigma < 0 || p->long_row < 0 || p->huge_row < 0 || p->pool_ctas_per_sm < 0 ||
+      p->pipeline < -1 || p->pipeline > 1 ||
       sell_layout_of(*p).long_row >= sell_layout_of(*p).huge_row) {
     set_error("params: value out of range");
     return PDHCG_E_INVALID;
@@ -1521,6 +1600,8 @@ void pdhcg_destroy(pdhcg_t* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (auto& kv : P->partitions)
     if (kv.second.owned) cudaFree(kv.second.d_buf);
+  if (P->pipe_exec) cudaGraphExecDestroy(P->pipe_exec);
+  if (P->pipe_scratch) cudaFree(P->pipe_scratch);
   P->arena_owner.reset();  // frees the allocation with its last handle
   delete P;
 }

@@ -170,6 +170,53 @@ struct StepScalars {
   CT itau, isig, sig, wk, ak, th, th1;
 };
 
+// The step's scalars 1/tau, 1/sigma, sigma, (k+1)/(k+2), 1/(k+2), theta,
+// 1 + theta: lane q computes scalar q as one quotient and converts it to the
+// vector type, so the warp issues one FP64 division and one conversion for all
+// seven (the FP64 pipe is narrow); the values are the same as computing each on
+// its own.  Every lane then takes them by shuffle.  Called by whole warps.
+template <class CT>
+__device__ __forceinline__ StepScalars<CT> step_scalars(const SolverState& S, const DevParams& P, double& inv_tau,
+                                                       double& inv_sigma) {
+  StepScalars<CT> sc;
+  const int ln = threadIdx.x & 31;
+  const double kp2 = double(S.k + 2);
+  const double num = ln == 2 ? S.sigma : ln == 3 ? double(S.k + 1) : ln == 5 ? P.theta : ln == 6 ? 1.0 + P.theta : 1.0;
+  const double den = ln == 0 ? S.tau : ln == 1 ? S.sigma : (ln == 3 || ln == 4) ? kp2 : 1.0;
+  const double q = num / den;
+  const CT qc = CT(q);
+  inv_tau = __shfl_sync(kFull, q, 0);
+  inv_sigma = __shfl_sync(kFull, q, 1);
+  sc.itau = shfl_idx(qc, 0);
+  sc.isig = shfl_idx(qc, 1);
+  sc.sig = shfl_idx(qc, 2);
+  sc.wk = shfl_idx(qc, 3);
+  sc.ak = shfl_idx(qc, 4);
+  sc.th = shfl_idx(qc, 5);
+  sc.th1 = shfl_idx(qc, 6);
+  return sc;
+}
+
+// Inner tolerance of this step (Sec. 3.3), updating S.eps_in.  With FP32 or
+// double-float vectors the subproblem residual cannot be resolved below the
+// rounding error of the gradient H x - b: the inner solve stops there instead
+// of running to its step cap (FP64 vectors: the paper's rule unchanged).
+// FP32: a few units in the last place of b.  Double-float: 16 units of 2^-48
+// times ||H|| ||x|| + ||b||, bounded with ||x|| <= tau ||b|| and
+// ||H|| <= gersh + 1/tau by (1 + gersh tau) ||b||.
+template <class VecT>
+__device__ __forceinline__ double inner_tolerance(SolverState& S, const DevParams& P, int method, double bb2,
+                                                  double inv_tau) {
+  if (S.K == 0) S.eps_in = P.eps_inner_first * fmax(1.0, sqrt(bb2));
+  else S.eps_in = fmin(S.eps_in, fmax(P.gamma_inner * S.omega * S.mv * inv_tau, P.eps_inner_min));
+  double floor_abs = 0.0;
+  if (method != PDHCG_INNER_DIAG) {
+    if (sizeof(VecT) == 4) floor_abs = 0x1p-20 * sqrt(bb2);
+    else if (std::is_same<VecT, dfloat>::value) floor_abs = 0x1p-44 * (1.0 + S.gersh * S.tau) * sqrt(bb2);
+  }
+  return fmax(S.eps_in, floor_abs);
+}
+
 // ---- structured objective Q = P + R^T R (Sec. 2.2): out = R v over the k rows
 // of R, the k-vector that the Q products of the next phase gather from ----
 // With FP32 values R v is taken with the remainders as well (R has few rows),
@@ -622,6 +669,64 @@ __device__ PDHCG_PHASE_ATTR void init_point(const Inst<MatT, VecT>& I, int vlo, 
   });
 }
 
+// After the check's reduction (cv as check_phase fills it, cv[17] the device
+// time): the residuals of Sec. 4.2, recorded in S, and the status they give:
+// OPTIMAL, PRIMAL_INFEASIBLE (Sec. 5.1), DUAL_INFEASIBLE (Sec. 5.2), the limits,
+// or 0 to continue.
+__device__ __forceinline__ int check_status(SolverState& S, const DevParams& P, double bscale, double cinf,
+                                            const double* cv) {
+  const double r_primal = cv[0] / (1.0 + bscale);
+  const double r_dual = cv[1] / (1.0 + fmax(fmax(cv[2], cv[3]), cinf));
+  const double xQx = cv[4], cx = cv[5], pr = cv[6], py = cv[7];
+  const double pobj = 0.5 * xQx + cx;
+  const double dobj = -pr - 0.5 * xQx - py;
+  const double gap = fabs(xQx + cx + pr + py);
+  const double r_gap = gap / (1.0 + fmax(fabs(pobj), fabs(0.5 * xQx + pr + py)));
+  const double rmax = fmax(r_primal, fmax(r_dual, r_gap));
+  S.r_primal = r_primal;
+  S.r_dual = r_dual;
+  S.r_gap = r_gap;
+  S.pobj = pobj;
+  S.dobj = dobj;
+  int status = 0;
+  if (!isfinite(rmax)) status = PDHCG_NUMERICAL_ERROR;
+  else if (rmax <= P.eps_tol) status = PDHCG_OPTIMAL;
+  if (!status) {
+    const double neg = cv[9] < 0.0 ? -cv[9] : 0.0;
+    if (neg > 0.0 && cv[8] <= P.eps_inf * neg) status = PDHCG_PRIMAL_INFEASIBLE;
+  }
+  if (!status) {
+    const double dn = cv[10];
+    if (dn > 0.0) {
+      const double vmax = fmax(cv[12] / dn, fmax(cv[13] / dn, cv[14] / dn));
+      if (cv[11] / dn < -P.eps_tol && vmax <= P.eps_inf) status = PDHCG_DUAL_INFEASIBLE;
+    }
+  }
+  if (!status && S.K + 1 >= P.max_iter) status = PDHCG_ITERATION_LIMIT;
+  if (!status && cv[17] - S.t_start_ns >= P.time_limit_ns) status = PDHCG_TIME_LIMIT;
+  return status;
+}
+
+// Restart test on the fixed-point residual (reading of the unstated rule) and,
+// at a restart, the PID update of the primal weight (Eq. pid) with the new step
+// sizes.  Returns whether to restart.
+__device__ __forceinline__ bool restart_decision(SolverState& S, const DevParams& P, double fpr, const double* cv) {
+  bool do_restart = false;
+  if (S.k >= 1) {
+    if (fpr <= P.restart_sufficient * S.fpr_anchor) do_restart = true;
+    else if (fpr <= P.restart_necessary * S.fpr_anchor && fpr > S.fpr_last) do_restart = true;
+    else if (double(S.k + 1) >= P.restart_artificial * double(S.K + 1)) do_restart = true;
+  }
+  S.fpr_last = fpr;
+  if (do_restart) {
+    pid_update(S, P, sqrt(cv[15]), sqrt(cv[16]));
+    S.omega = exp(S.log_omega);
+    S.tau = S.eta / S.omega;
+    S.sigma = S.eta * S.omega;
+  }
+  return do_restart;
+}
+
 // The control loop: scalar state, decisions and group reductions; the row and
 // elementwise work is in the phase functions above.
 // kR: the structured-Q variant (instances with a factor R); the plain variant
@@ -663,31 +768,8 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
 
   while (ok) {
     const int cur = S.cur;
-    // The step's scalars 1/tau, 1/sigma, sigma, (k+1)/(k+2), 1/(k+2), theta,
-    // 1 + theta: lane q computes scalar q as one quotient and converts it to the
-    // vector type, so the warp issues one FP64 division and one conversion for
-    // all seven (the FP64 pipe is narrow); the values are the same as computing
-    // each on its own.  Every lane then takes them by shuffle.
     double inv_tau, inv_sigma;
-    StepScalars<CT> sc;
-    {
-      const int ln = threadIdx.x & 31;
-      const double kp2 = double(S.k + 2);
-      const double num = ln == 2 ? S.sigma : ln == 3 ? double(S.k + 1) : ln == 5 ? P.theta
-                       : ln == 6 ? 1.0 + P.theta : 1.0;
-      const double den = ln == 0 ? S.tau : ln == 1 ? S.sigma : (ln == 3 || ln == 4) ? kp2 : 1.0;
-      const double q = num / den;
-      const CT qc = CT(q);
-      inv_tau = __shfl_sync(kFull, q, 0);
-      inv_sigma = __shfl_sync(kFull, q, 1);
-      sc.itau = shfl_idx(qc, 0);
-      sc.isig = shfl_idx(qc, 1);
-      sc.sig = shfl_idx(qc, 2);
-      sc.wk = shfl_idx(qc, 3);
-      sc.ak = shfl_idx(qc, 4);
-      sc.th = shfl_idx(qc, 5);
-      sc.th1 = shfl_idx(qc, 6);
-    }
+    const StepScalars<CT> sc = step_scalars<CT>(S, P, inv_tau, inv_sigma);
 
     // Phase I (structured Q: R x first)
     if (kR && I.k > 0 && method != PDHCG_INNER_DIAG) {
@@ -705,20 +787,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     PDHCG_CLK(5);
 
     // adaptive inner tolerance (Sec. 3.3)
-    if (S.K == 0) S.eps_in = P.eps_inner_first * fmax(1.0, sqrt(red1[1]));
-    else S.eps_in = fmin(S.eps_in, fmax(P.gamma_inner * S.omega * S.mv * inv_tau, P.eps_inner_min));
-    // With FP32 or double-float vectors the subproblem residual cannot be
-    // resolved below the rounding error of the gradient H x - b: the inner solve
-    // stops there instead of running to its step cap (FP64 vectors: the paper's
-    // rule unchanged).  FP32: a few units in the last place of b.  Double-float:
-    // 16 units of 2^-48 times ||H|| ||x|| + ||b||, bounded with ||x|| <= tau ||b||
-    // and ||H|| <= gersh + 1/tau by (1 + gersh tau) ||b||.
-    double floor_abs = 0.0;
-    if (method != PDHCG_INNER_DIAG) {
-      if (sizeof(VecT) == 4) floor_abs = 0x1p-20 * sqrt(red1[1]);
-      else if (std::is_same<VecT, dfloat>::value) floor_abs = 0x1p-44 * (1.0 + S.gersh * S.tau) * sqrt(red1[1]);
-    }
-    const double eps = fmax(S.eps_in, floor_abs);
+    const double eps = inner_tolerance<VecT>(S, P, method, red1[1], inv_tau);
 
     // inner solve (Sec. 2.2)
     if (method == PDHCG_INNER_CG) {
@@ -845,36 +914,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       if (!group_reduce<BS, 18>(g, cv, mm)) { ok = false; break; }
       PDHCG_CLK(5);
 
-      const double r_primal = cv[0] / (1.0 + I.bscale);
-      const double r_dual = cv[1] / (1.0 + fmax(fmax(cv[2], cv[3]), I.cinf));
-      const double xQx = cv[4], cx = cv[5], pr = cv[6], py = cv[7];
-      const double pobj = 0.5 * xQx + cx;
-      const double dobj = -pr - 0.5 * xQx - py;
-      const double gap = fabs(xQx + cx + pr + py);
-      const double r_gap = gap / (1.0 + fmax(fabs(pobj), fabs(0.5 * xQx + pr + py)));
-      const double rmax = fmax(r_primal, fmax(r_dual, r_gap));
-      S.r_primal = r_primal;
-      S.r_dual = r_dual;
-      S.r_gap = r_gap;
-      S.pobj = pobj;
-      S.dobj = dobj;
-      int status = 0;
-      if (!isfinite(rmax)) status = PDHCG_NUMERICAL_ERROR;
-      else if (rmax <= P.eps_tol) status = PDHCG_OPTIMAL;
-      if (!status) {
-        const double neg = cv[9] < 0.0 ? -cv[9] : 0.0;
-        if (neg > 0.0 && cv[8] <= P.eps_inf * neg) status = PDHCG_PRIMAL_INFEASIBLE;
-      }
-      if (!status) {
-        const double dn = cv[10];
-        if (dn > 0.0) {
-          const double vmax = fmax(cv[12] / dn, fmax(cv[13] / dn, cv[14] / dn));
-          if (cv[11] / dn < -P.eps_tol && vmax <= P.eps_inf) status = PDHCG_DUAL_INFEASIBLE;
-        }
-      }
-      if (!status && S.K + 1 >= P.max_iter) status = PDHCG_ITERATION_LIMIT;
-      if (!status && cv[17] - S.t_start_ns >= P.time_limit_ns) status = PDHCG_TIME_LIMIT;
-
+      const int status = check_status(S, P, I.bscale, I.cinf, cv);
       if (status) {
         const double dn = cv[10];
         double mx[2] = {0.0, 0.0};
@@ -891,19 +931,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
         break;
       }
 
-      // restart test on the fixed-point residual (reading of the unstated rule)
-      if (S.k >= 1) {
-        if (fpr <= P.restart_sufficient * S.fpr_anchor) do_restart = true;
-        else if (fpr <= P.restart_necessary * S.fpr_anchor && fpr > S.fpr_last) do_restart = true;
-        else if (double(S.k + 1) >= P.restart_artificial * double(S.K + 1)) do_restart = true;
-      }
-      S.fpr_last = fpr;
-      if (do_restart) {
-        pid_update(S, P, sqrt(cv[15]), sqrt(cv[16]));
-        S.omega = exp(S.log_omega);
-        S.tau = S.eta / S.omega;
-        S.sigma = S.eta * S.omega;
-      }
+      do_restart = restart_decision(S, P, fpr, cv);
     }
 
     if (do_restart) {

@@ -52,7 +52,7 @@ class Params(C.Structure):
         ("omega_clamp", C.c_double),
         ("group_blocks", C.c_int32), ("device_timeout_ms", C.c_int32),
         ("sell_sigma", C.c_int32), ("long_row", C.c_int32), ("huge_row", C.c_int32),
-        ("pool_ctas_per_sm", C.c_int32),
+        ("pool_ctas_per_sm", C.c_int32), ("pipeline", C.c_int32),
     ]
 
 
