@@ -56,6 +56,8 @@ def parse():
                     help="PDHG steps timed on the large sparse QP (n=2e6); 0 skips it")
     ap.add_argument("--large-n", type=int, default=2_000_000,
                     help="variables of that QP (m = n/2); smaller values are for profiling captures")
+    ap.add_argument("--large-form", default="auto", choices=["auto", "pipeline", "persistent"],
+                    help="how that QP runs: the library's choice, the pipeline graph, or the persistent kernel")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[200.0, 2000.0],
                     help="Poisson arrival rates (requests/s) of the serving traces; none skips serving")
     ap.add_argument("--serve-eps", type=float, nargs="*", default=[1e-4, 1e-6])
@@ -215,8 +217,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 425_223_424, "instances": 512,
-                   "sources_sha256": "58fb6ef4585b9c53d30c1cf4b63e92eda6623f5b9a45535fe4dfe8e31537c652",
+TRAFFIC_CAPTURE = {"bytes": 285_549_312 + 141_981_440, "instances": 512,
+                   "sources_sha256": "0ed34b75fd5b2c5df3e159f4cc44ea65be63b15986a7acea680dc22923a507f7",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
@@ -308,7 +310,8 @@ def large_instance_leg(args, stream, peak_gbs):
     import torch
     from paper_2602_23967_b300 import pdhcg
     qp = W.large_sparse_qp(n=args.large_n, m=args.large_n // 2, seed=0)
-    prm = pdhcg.default_params(precision=args.precision, eps_tol=1e-12, max_iter=args.large_iters)
+    prm = pdhcg.default_params(precision=args.precision, eps_tol=1e-12, max_iter=args.large_iters,
+                               pipeline={"auto": 0, "pipeline": 1, "persistent": -1}[args.large_form])
     tune = None
     if args.autotune:
         prm, tune = pdhcg.autotune([qp], prm, stream=stream.cuda_stream)
@@ -329,8 +332,10 @@ def large_instance_leg(args, stream, peak_gbs):
     mb, vb = {"fp64": (8, 8), "fp32": (4, 4)}.get(args.precision, (4, 8))
     alg = large_bytes(qp, r["iterations"], r["inner_iterations"], mat_bytes=mb, vec_bytes=vb)
     gbs = alg / (ms * 1e-3) / 1e9
+    forms = {0: "one CTA", 1: "persistent multi-CTA group", 2: "pipeline graph (one kernel per phase)"}
     return {"workload": f"large sparse QP n={qp.n}, m={qp.m}, nnz(Q)={qp.Q.nnz}, nnz(A)={qp.A.nnz}, "
-                        f"{r['iterations']} PDHG steps ({r['inner_iterations']} BB steps), one multi-CTA group",
+                        f"{r['iterations']} PDHG steps ({r['inner_iterations']} BB steps)",
+            "form": forms.get(r["form"], r["form"]),
             "us_per_step": ms * 1e3 / r["iterations"], "algorithmic_bytes": alg,
             "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak_gbs, "autotune": tune}
 
@@ -373,9 +378,14 @@ def serve_trace(prm, stream, trace, qps, slots, drain_s=90.0):
     by_kind = {}
     for kind in sorted(set(kinds.values())):
         lk = np.array([out[tk]["latency_seconds"] for tk in out if kinds[tk] == kind])
+        # device span of the solve (first step to last, pauses included) and the rest of
+        # the latency (queue, admission, setup, retirement)
+        sk = np.array([out[tk]["solve_seconds"] for tk in out if kinds[tk] == kind])
         by_kind[kind] = {"requests": sum(1 for v in kinds.values() if v == kind), "completed": int(len(lk)),
                          "latency_p50_ms": float(np.percentile(lk, 50) * 1e3) if len(lk) else None,
-                         "latency_p99_ms": float(np.percentile(lk, 99) * 1e3) if len(lk) else None}
+                         "latency_p99_ms": float(np.percentile(lk, 99) * 1e3) if len(lk) else None,
+                         "solve_span_p50_ms": float(np.percentile(sk, 50) * 1e3) if len(sk) else None,
+                         "wait_p50_ms": float(np.percentile(lk - sk, 50) * 1e3) if len(sk) else None}
     statuses = [r["status_name"] for r in out.values()]
     return {"requests": len(trace), "completed": len(out),
             "optimal": statuses.count("OPTIMAL"), "primal_infeasible": statuses.count("PRIMAL_INFEASIBLE"),
@@ -473,7 +483,7 @@ def whole_solve_leg(args, stream):
                          "create_s": t_create,
                          "solves_per_s": 1.0 / r["solve_seconds"] if r["status_name"] == "OPTIMAL" else 0.0,
                          "iterations_per_s": r["iterations"] / r["solve_seconds"],
-                         "kkt_fp64": k, "objective": r["primal_obj"]})
+                         "kkt_fp64": k, "objective": r["primal_obj"], "form": r["form"]})
     return rows
 
 

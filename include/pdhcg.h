@@ -144,6 +144,9 @@ typedef struct {
   int32_t power_iters;        /* Lanczos steps taken by the ||A||_2 estimate                 */
   int32_t precision;
   double latency_seconds;     /* serving loop: pdhcg_submit to result ready (wall clock); 0 otherwise */
+  int32_t form;               /* how the solve ran: 0 one CTA (pool), 1 a multi-CTA group of the
+                                 persistent kernel, 2 the pipeline graph (pdhcg_params.pipeline) */
+  int32_t reserved;
 } pdhcg_result;
 
 typedef struct pdhcg_problem pdhcg_t;
@@ -248,7 +251,8 @@ int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* re
 /* ---- autotuner of the launch shape and row layout ----
  * The paper has no counterpart (its kernels are not described).  Candidate
  * settings of the row layout (sell_sigma, long_row, huge_row) and of the launch
- * shape (group_blocks for a single problem; pool_ctas_per_sm for a batch) are
+ * shape (for a single problem: the pipeline form against the persistent kernel
+ * at several group_blocks; for a batch: pool_ctas_per_sm) are
  * timed on the device with CUDA events over a fixed number of PDHG steps of
  * the given problems (count == 1: one multi-CTA solve; count > 1: one batched
  * launch), and the fastest is written into *params.  The defaults are kept
@@ -261,6 +265,7 @@ int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* re
  * Errors as pdhcg_create_batch. */
 typedef struct {
   int32_t sell_sigma, long_row, huge_row, group_blocks, pool_ctas_per_sm; /* chosen (0 = default) */
+  int32_t pipeline;                 /* chosen pdhcg_params.pipeline                              */
   int32_t candidates;               /* configurations timed (0 when taken from the cache)       */
   int32_t from_cache;               /* 1: the shape class was tuned before in this process       */
   double seconds_per_step;          /* chosen configuration: device seconds per PDHG step       */

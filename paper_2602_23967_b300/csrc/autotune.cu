@@ -4,8 +4,9 @@
 // Knobs:
 //   * row layout (read at create): the SELL sort window sell_sigma, and the
 //     row lengths above which a row gets a warp (long_row) or a CTA (huge_row);
-//   * launch shape: CTAs of the group of a single large solve (group_blocks),
-//     and the cap on resident pool CTAs per SM of a batched launch.
+//   * launch shape: for a single solve, the pipeline form against the
+//     persistent multi-CTA kernel at several group sizes (group_blocks); for
+//     a batched launch, the cap on resident pool CTAs per SM.
 // Search: coordinate descent from the defaults, launch shape first (no
 // re-creation needed), then the layout with the best shape.  Each candidate
 // runs kSteps PDHG steps (a warm-up solve, then a timed one) between two CUDA
@@ -33,7 +34,7 @@ constexpr int kSteps = 64;            // PDHG steps per timing (one check period
 constexpr double kMargin = 0.03;      // a candidate must beat the defaults by this much
 
 struct Knobs {
-  int32_t sigma = 0, long_row = 0, huge_row = 0, group_blocks = 0, pool_cap = 0;
+  int32_t sigma = 0, long_row = 0, huge_row = 0, group_blocks = 0, pool_cap = 0, pipeline = 0;
 };
 
 std::mutex g_mu;
@@ -83,6 +84,7 @@ void apply(const Knobs& k, pdhcg_params* p) {
   p->huge_row = k.huge_row;
   p->group_blocks = k.group_blocks;
   p->pool_ctas_per_sm = k.pool_cap;
+  p->pipeline = k.pipeline;
 }
 
 // Device seconds per PDHG step of one configuration (<= 0: it failed).
@@ -146,7 +148,8 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
       *out = it->second;
       out->from_cache = 1;
       out->candidates = 0;
-      Knobs k{out->sell_sigma, out->long_row, out->huge_row, out->group_blocks, out->pool_ctas_per_sm};
+      Knobs k{out->sell_sigma, out->long_row, out->huge_row, out->group_blocks, out->pool_ctas_per_sm,
+              out->pipeline};
       apply(k, params);
       return PDHCG_OK;
     }
@@ -179,9 +182,12 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
       k.pool_cap = 1;
       c.push_back(k);
     } else {
+      // the persistent multi-CTA kernel at several group sizes (the default
+      // may be the pipeline form for a large problem)
       for (int g : {sms, 3 * sms / 2, 2 * sms}) {
         Knobs k = best;
         k.group_blocks = g;
+        k.pipeline = -1;
         c.push_back(k);
       }
     }
@@ -215,6 +221,7 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
   out->huge_row = best.huge_row;
   out->group_blocks = best.group_blocks;
   out->pool_ctas_per_sm = best.pool_cap;
+  out->pipeline = best.pipeline;
   out->candidates = timed;
   out->from_cache = 0;
   out->seconds_per_step = t_best;

@@ -70,6 +70,11 @@ int pick_fastest(const std::vector<double>& seconds, double margin);
 // Split items with the given weights into nblk contiguous ranges (nblk + 1 bounds).
 std::vector<int32_t> split_balanced(const std::vector<int64_t>& w, int nblk);
 
+// Batched and served solves: an instance whose PDHG step touches fewer than
+// this many nonzeros and vector entries runs on one pool CTA; a larger one on
+// a multi-CTA group.
+constexpr int64_t kGroupWork = 150000;
+
 // Device bytes a problem will hold (for admission control).
 size_t device_footprint(const HostQP& h, int precision);
 

@@ -22,7 +22,8 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
   for (const void* f : {(const void*)solve_kernel<kGroupBS, MatT, VecT, false>,
                         (const void*)solve_kernel<kGroupBS, MatT, VecT, true>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, false>,
-                        (const void*)solve_kernel<kPoolBS, MatT, VecT, true>})
+                        (const void*)solve_kernel<kPoolBS, MatT, VecT, true>,
+                        (const void*)solve_kernel<kPoolBS, MatT, VecT, false, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
   return e;
 }
@@ -31,12 +32,15 @@ template <class MatT, class VecT>
 int pool_blocks_per_sm(size_t smem_vec_bytes) {
   int nb = 0, nr = 0;
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
+  int nd = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT, false>, kPoolBS,
                                                     smem_vec_bytes) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kPoolBS, MatT, VecT, true>, kPoolBS,
+                                                    smem_vec_bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, solve_kernel<kPoolBS, MatT, VecT, false, true>, kPoolBS,
                                                     smem_vec_bytes) != cudaSuccess)
     return 0;
-  nb = std::min(nb, nr);
+  nb = std::min(nb, std::min(nr, nd));
   if (PDHCG_POOL_MAX_PER_SM > 0) nb = std::min(nb, int(PDHCG_POOL_MAX_PER_SM));
   return nb;
 }
@@ -102,6 +106,8 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   if (plan.group_blocks == 0) {
     if (r)
       solve_kernel<kPoolBS, MatT, VecT, true><<<grid, kPoolBS, smem, s>>>(di, p);
+    else if (plan.diag_only)
+      solve_kernel<kPoolBS, MatT, VecT, false, true><<<grid, kPoolBS, smem, s>>>(di, p);
     else
       solve_kernel<kPoolBS, MatT, VecT, false><<<grid, kPoolBS, smem, s>>>(di, p);
     return cudaGetLastError();

@@ -530,6 +530,7 @@ void fill_result(const pdhcg_problem* P, const SolverState& S, pdhcg_result* res
   res->solve_seconds = (S.t_end_ns - S.t_start_ns) * 1e-9;
   res->power_iters = S.power_iters;
   res->precision = P->precision;
+  res->form = S.form;
 }
 
 // CTAs of one cooperative group: the solve kernel's co-residency, or (setup)
@@ -580,7 +581,6 @@ int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
 // entries one PDHG step touches, inner products counted once) run on one pool
 // CTA each; larger ones on a multi-CTA group of about one CTA per
 // kWorkPerGroupCta, at most kMaxBatchGroup.
-constexpr int64_t kGroupWork = 150000;
 constexpr int64_t kWorkPerGroupCta = 65536;
 constexpr int kMaxBatchGroup = 32;
 
@@ -850,6 +850,7 @@ int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_re
       plan.npool = 1;
       plan.pool_inst = P->plan_i32 + 3;
       plan.pool_next = P->plan_i32 + 4;
+      plan.diag_only = P->method == PDHCG_INNER_DIAG && P->k == 0;
       const size_t need = smem_need(P);
       plan.smem_vec_bytes = need <= kSmemVecBudget ? int64_t(need) : 0;
     }
@@ -1375,6 +1376,8 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
   base.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
   base.err = d_pool + npool + 1;
   LaunchPlan pool = base;  // pool CTAs
+  pool.diag_only = 1;
+  for (int i : bg.pool) pool.diag_only &= probs[i]->method == PDHCG_INNER_DIAG && probs[i]->k == 0;
   pool.npool = npool;
   pool.pool_inst = d_pool;
   pool.pool_next = d_pool + npool;
@@ -1902,7 +1905,11 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
     CK(cudaMemcpyAsync(d_i32, g_noalloc_horder, sizeof(int32_t) * kNoAllocQueueWords, cudaMemcpyHostToDevice,
                        s));
     LaunchPlan plan;
-    for (int i = 0; i < count; ++i) plan.structured |= probs[i]->k > 0;
+    plan.diag_only = 1;
+    for (int i = 0; i < count; ++i) {
+      plan.structured |= probs[i]->k > 0;
+      plan.diag_only &= probs[i]->method == PDHCG_INNER_DIAG && probs[i]->k == 0;
+    }
     plan.npool = count;
     plan.pool_inst = d_i32;
     plan.pool_next = d_i32 + count;

@@ -50,6 +50,8 @@ struct SolverState {
   int32_t method;       // PDHCG_INNER_DIAG / CG / BB
   int32_t power_iters;
   int32_t device_error; // a bounded device wait gave up
+  int32_t form;         // how the last launch ran it: 0 pool CTA, 1 multi-CTA group, 2 pipeline graph
+  int32_t pad_;
 };
 
 // With FP32 matrix values, lo holds each scaled value's rounding remainder
@@ -177,6 +179,9 @@ struct LaunchPlan {
   // Some instance has a structured Q = P + R^T R: launch the kernel variant
   // with the R phases (the plain variant has none of their cost).
   int32_t structured = 0;
+  // Every pool instance uses the closed form (diagonal Q) and none is
+  // structured: launch the variant without the CG / BB code.
+  int32_t diag_only = 0;
 };
 
 }  // namespace pdhcg

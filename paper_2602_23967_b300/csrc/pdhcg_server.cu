@@ -139,6 +139,61 @@ static void copy_csr(const pdhcg_csr* M, std::vector<int64_t>& rp, std::vector<i
   v.assign(M->val, M->val + M->nnz);
 }
 
+// Creation and device setup of admitted requests on the admission stream (one
+// batch: one allocation, one setup launch), then they join the ready list.
+static void admit_batch(pdhcg_server* S, std::vector<Request>& admit) {
+  const auto t_adm0 = std::chrono::steady_clock::now();
+  std::vector<CreateInput> in;
+  in.reserve(admit.size());
+  for (auto& r : admit) {
+    r.prob.bind();
+    in.push_back(r.prob.input());
+  }
+  std::vector<pdhcg_problem*> handles(admit.size(), nullptr);
+  CreateAlloc al;
+  al.pool = S->pool;
+  al.pinned = &S->pinned_stage;
+  al.pinned_bytes = &S->pinned_stage_bytes;
+  int rc = create_impl(int(admit.size()), in.data(), &S->prm, S->admit_stream, handles.data(), true, &al);
+  if (rc != PDHCG_OK && admit.size() > 1) {
+    // fall back to one-by-one so one bad request fails alone
+    for (size_t i = 0; i < admit.size(); ++i) {
+      rc = create_impl(1, &in[i], &S->prm, S->admit_stream, &handles[i], true, &al);
+      if (rc != PDHCG_OK) handles[i] = nullptr;
+    }
+  } else if (rc != PDHCG_OK) {
+    handles[0] = nullptr;
+  }
+  // creation synchronised its stream; the solves run on the slice stream
+  for (auto* h : handles)
+    if (h) h->stream = S->stream;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t i = 0; i < admit.size(); ++i) {
+      if (!handles[i]) {
+        Done d;
+        d.res.status = PDHCG_NUMERICAL_ERROR;
+        d.res.latency_seconds = seconds_since(admit[i].t_submit);
+        S->done[admit[i].ticket] = std::move(d);
+        S->pending.erase(admit[i].ticket);
+        S->stats.rejected++;
+        S->stats.hbm_in_use -= admit[i].bytes;
+        S->reserved--;
+        continue;
+      }
+      Live l;
+      l.ticket = admit[i].ticket;
+      l.P = handles[i];
+      l.bytes = admit[i].bytes;
+      l.t_submit = admit[i].t_submit;
+      S->ready.push_back(l);
+      S->stats.admitted++;
+    }
+    S->stats.admit_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adm0).count();
+  }
+  S->cv_work.notify_one();
+}
+
 static void admit_loop(pdhcg_server* S) {
   cudaSetDevice(S->device);
   while (true) {
@@ -160,57 +215,21 @@ static void admit_loop(pdhcg_server* S) {
       S->stats.queued = int32_t(S->queue.size());
     }
     if (admit.empty()) continue;
-    // ---- batched creation and device setup on the admission stream ----
-    const auto t_adm0 = std::chrono::steady_clock::now();
-    std::vector<CreateInput> in;
-    in.reserve(admit.size());
+    // Small requests first, as one batch, then each large one on its own: a
+    // large request's host preparation and setup must not hold back the small
+    // ones admitted with it.
+    std::vector<Request> small, large;
     for (auto& r : admit) {
-      r.prob.bind();
-      in.push_back(r.prob.input());
+      const OwnedProblem& p = r.prob;
+      const int64_t work = int64_t(p.qc.size()) + 2 * int64_t(p.ac.size()) + p.n + p.m;
+      (work < kGroupWork ? small : large).push_back(std::move(r));
     }
-    std::vector<pdhcg_problem*> handles(admit.size(), nullptr);
-    CreateAlloc al;
-    al.pool = S->pool;
-    al.pinned = &S->pinned_stage;
-    al.pinned_bytes = &S->pinned_stage_bytes;
-    int rc = create_impl(int(admit.size()), in.data(), &S->prm, S->admit_stream, handles.data(), true, &al);
-    if (rc != PDHCG_OK && admit.size() > 1) {
-      // fall back to one-by-one so one bad request fails alone
-      for (size_t i = 0; i < admit.size(); ++i) {
-        rc = create_impl(1, &in[i], &S->prm, S->admit_stream, &handles[i], true, &al);
-        if (rc != PDHCG_OK) handles[i] = nullptr;
-      }
-    } else if (rc != PDHCG_OK) {
-      handles[0] = nullptr;
+    if (!small.empty()) admit_batch(S, small);
+    for (auto& r : large) {
+      std::vector<Request> one;
+      one.push_back(std::move(r));
+      admit_batch(S, one);
     }
-    // creation synchronised its stream; the solves run on the slice stream
-    for (auto* h : handles)
-      if (h) h->stream = S->stream;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      for (size_t i = 0; i < admit.size(); ++i) {
-        if (!handles[i]) {
-          Done d;
-          d.res.status = PDHCG_NUMERICAL_ERROR;
-          d.res.latency_seconds = seconds_since(admit[i].t_submit);
-          S->done[admit[i].ticket] = std::move(d);
-          S->pending.erase(admit[i].ticket);
-          S->stats.rejected++;
-          S->stats.hbm_in_use -= admit[i].bytes;
-          S->reserved--;
-          continue;
-        }
-        Live l;
-        l.ticket = admit[i].ticket;
-        l.P = handles[i];
-        l.bytes = admit[i].bytes;
-        l.t_submit = admit[i].t_submit;
-        S->ready.push_back(l);
-        S->stats.admitted++;
-      }
-      S->stats.admit_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adm0).count();
-    }
-    S->cv_work.notify_one();
   }
 }
 

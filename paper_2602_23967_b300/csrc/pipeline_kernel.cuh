@@ -216,6 +216,7 @@ PDHCG_PIPE_KERNEL pipe_init(PipeArgs a) {
     S.t_start_ns = t[0];
     S.started = 1;
     S.cur = 0;
+    S.form = 2;
   }
 }
 

@@ -40,6 +40,16 @@ namespace pdhcg {
 #else
 #define PDHCG_PHASE_ATTR __noinline__
 #endif
+// The two row phases every PDHG step runs (Phase I, Phase II) may be inlined
+// into the control loop on their own (PDHCG_INLINE_HOT=1).
+#ifndef PDHCG_INLINE_HOT
+#define PDHCG_INLINE_HOT 0
+#endif
+#if PDHCG_INLINE_PHASES || PDHCG_INLINE_HOT
+#define PDHCG_HOT_ATTR __forceinline__
+#else
+#define PDHCG_HOT_ATTR __noinline__
+#endif
 
 template <int NV>
 struct Red {
@@ -271,7 +281,7 @@ __device__ PDHCG_PHASE_ATTR void r_phase_check(const Inst<MatT, VecT>& I, int pr
 // ---- Phase I: g = A^T y, b = x/tau - c - g, inner-solver start (Eq. primal_update) ----
 // returns {inner start norm^2, ||b||^2, ||x+ - x||^2, ||x_new - x||^2}
 template <int BS, Ld LM, bool kR, class MatT, class VecT>
-__device__ PDHCG_PHASE_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
+__device__ PDHCG_HOT_ATTR Red<4> phase1(const Inst<MatT, VecT>& I, int prank, int method, int cur,
                                       StepScalars<VecT> sc, const RowCtx& rc) {
   using CT = VecT;
   using Acc = VecT;
@@ -433,7 +443,7 @@ __device__ PDHCG_PHASE_ATTR Red<3> bb_phase_a(const Inst<MatT, VecT>& I, int pra
 // ---- Phase II: A xbar, dual step (Eq. dual_update), reflected Halpern (Sec. 3.1) ----
 // returns {||y+ - y||^2, ||x+ - x||^2, ||x_new - x||^2} (the x terms only for CG / BB)
 template <int BS, Ld LM, class MatT, class VecT>
-__device__ PDHCG_PHASE_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int method, int cur, int vlo,
+__device__ PDHCG_HOT_ATTR Red<3> phase2(const Inst<MatT, VecT>& I, int prank, int method, int cur, int vlo,
                                       int vhi, StepScalars<VecT> sc, const RowCtx& rc) {
   using CT = VecT;
   using Acc = VecT;
@@ -727,11 +737,47 @@ __device__ __forceinline__ bool restart_decision(SolverState& S, const DevParams
   return do_restart;
 }
 
+// Write back the fields of the state that a launch changes.  The read-only
+// ones (eta, ||A||, the Gershgorin bound, omega0, the scales, the Lanczos
+// count, the method) are left alone, so the control loop does not keep them
+// live for a whole-struct store at its end.
+__device__ __forceinline__ void store_state(SolverState* d, const SolverState& S) {
+  d->K = S.K;
+  d->k = S.k;
+  d->inner_total = S.inner_total;
+  d->restarts = S.restarts;
+  d->omega = S.omega;
+  d->log_omega = S.log_omega;
+  d->e_sum = S.e_sum;
+  d->e_prev = S.e_prev;
+  d->tau = S.tau;
+  d->sigma = S.sigma;
+  d->eps_in = S.eps_in;
+  d->mv = S.mv;
+  d->fpr_anchor = S.fpr_anchor;
+  d->fpr_last = S.fpr_last;
+  d->r_primal = S.r_primal;
+  d->r_dual = S.r_dual;
+  d->r_gap = S.r_gap;
+  d->pobj = S.pobj;
+  d->dobj = S.dobj;
+  d->t_start_ns = S.t_start_ns;
+  d->t_end_ns = S.t_end_ns;
+#if PDHCG_PHASE_TIMERS
+  for (int q = 0; q < 8; ++q) d->tm[q] = S.tm[q];
+#endif
+  d->status = S.status;
+  d->cur = S.cur;
+  d->started = S.started;
+  d->device_error = S.device_error;
+  d->form = S.form;
+}
+
 // The control loop: scalar state, decisions and group reductions; the row and
 // elementwise work is in the phase functions above.
 // kR: the structured-Q variant (instances with a factor R); the plain variant
 // compiles without the R phases and the split gathers.
-template <int BS, Ld LM, bool kR, class MatT, class VecT>
+template <int BS, Ld LM, bool kR, class MatT, class VecT, bool kDiag = false>
 __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, VecT>& I, const LaunchPlan& plan,
                                             const RowCtx& rc) {
   using CT = VecT;
@@ -739,7 +785,10 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   SolverState S = *I.st;
   if (S.status != 0) return;
   const DevParams& P = I.prm;
-  const int method = S.method;
+  // kDiag: the kernel variant for launches whose instances all use the closed
+  // form (diagonal Q); the inner-solver code is compiled out, which spares the
+  // control loop registers and their spills
+  const int method = kDiag ? int(PDHCG_INNER_DIAG) : S.method;
   int vlo, vhi, clo, chi;
   g.range(I.var_part, I.n, vlo, vhi);
   g.range(I.con_part, I.m, clo, chi);
@@ -760,6 +809,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     S.started = 1;
     S.cur = 0;
   }
+  S.form = g.nblk > 1 ? 1 : 0;
   const int64_t K_first = S.K;
   // device-time slice budget (single-CTA solves): thread 0 reads the clock every
   // 16 steps and shares the decision, so the whole CTA pauses together
@@ -958,7 +1008,7 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     }
   }
   if (!ok) S.device_error = 1;
-  if (g.rank == 0 && threadIdx.x == 0) *I.st = S;
+  if (g.rank == 0 && threadIdx.x == 0) store_state(I.st, S);
 }
 
 
@@ -977,7 +1027,7 @@ __device__ __forceinline__ void copy_inst(Inst<MatT, VecT>& dst, const Inst<MatT
   __syncthreads();
 }
 
-template <int BS, bool kR, class MatT, class VecT>
+template <int BS, bool kR, class MatT, class VecT, bool kDiag = false>
 __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig, Inst<MatT, VecT>& I,
                                            const LaunchPlan& plan, const RowCtx& rc, char* base,
                                            int method) {
@@ -1050,7 +1100,7 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
     I.yb0 = yb0; I.yb1 = yb1; I.yT = yT; I.ya = ya; I.lc = lc; I.uc = uc; I.ctype = ct;
   }
   __syncthreads();
-  solve_instance<BS, Ld::Cached, kR>(g, I, plan, rc);
+  solve_instance<BS, Ld::Cached, kR, MatT, VecT, kDiag>(g, I, plan, rc);
   __syncthreads();
   const int cur2 = Ig.st->cur;
   constexpr bool kLo = std::is_same<MatT, float>::value;
@@ -1079,7 +1129,7 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
 #ifndef PDHCG_POOL_MIN_BLOCKS
 #define PDHCG_POOL_MIN_BLOCKS PDHCG_MIN_BLOCKS
 #endif
-template <int BS, class MatT, class VecT, bool kR>
+template <int BS, class MatT, class VecT, bool kR, bool kDiag = false>
 __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_POOL_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
@@ -1129,9 +1179,9 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
     copy_inst<BS>(sh_inst, Ig);
     if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
-      solve_in_smem<BS, kR>(g, Ig, sh_inst, plan, rc, dsm, method);
+      solve_in_smem<BS, kR, MatT, VecT, kDiag>(g, Ig, sh_inst, plan, rc, dsm, method);
     } else {
-      solve_instance<BS, Ld::Cached, kR>(g, sh_inst, plan, rc);
+      solve_instance<BS, Ld::Cached, kR, MatT, VecT, kDiag>(g, sh_inst, plan, rc);
     }
     __syncthreads();
   }

@@ -64,7 +64,7 @@ class Result(C.Structure):
         ("primal_obj", C.c_double), ("dual_obj", C.c_double),
         ("eta", C.c_double), ("omega", C.c_double), ("norm_A", C.c_double),
         ("solve_seconds", C.c_double), ("power_iters", C.c_int32), ("precision", C.c_int32),
-        ("latency_seconds", C.c_double),
+        ("latency_seconds", C.c_double), ("form", C.c_int32), ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
@@ -81,7 +81,8 @@ class ProblemData(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("sell_sigma", C.c_int32), ("long_row", C.c_int32), ("huge_row", C.c_int32),
-                ("group_blocks", C.c_int32), ("pool_ctas_per_sm", C.c_int32), ("candidates", C.c_int32),
+                ("group_blocks", C.c_int32), ("pool_ctas_per_sm", C.c_int32), ("pipeline", C.c_int32),
+                ("candidates", C.c_int32),
                 ("from_cache", C.c_int32), ("seconds_per_step", C.c_double),
                 ("default_seconds_per_step", C.c_double)]
 

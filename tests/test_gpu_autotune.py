@@ -30,12 +30,12 @@ def test_autotuned_single_solve_matches_oracle():
     tuned, rep = pdhcg.autotune([qp], base)
     assert rep["from_cache"] == 0 and rep["candidates"] >= 5
     assert rep["seconds_per_step"] > 0 and rep["seconds_per_step"] <= rep["default_seconds_per_step"] * 1.10
-    for f in ("sell_sigma", "long_row", "huge_row", "group_blocks"):
+    for f in ("sell_sigma", "long_row", "huge_row", "group_blocks", "pipeline"):
         assert getattr(tuned, f) == rep[f]
     # same shape class: taken from the cache
     _, rep2 = pdhcg.autotune([W.large_sparse_qp(n=20000, m=10000, seed=1)], base)
     assert rep2["from_cache"] == 1 and rep2["candidates"] == 0
-    assert all(rep2[f] == rep[f] for f in ("sell_sigma", "long_row", "huge_row", "group_blocks"))
+    assert all(rep2[f] == rep[f] for f in ("sell_sigma", "long_row", "huge_row", "group_blocks", "pipeline"))
     N = 100
     tuned.max_iter = N
     p = pdhcg.Problem(qp, tuned)

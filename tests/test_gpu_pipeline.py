@@ -49,6 +49,7 @@ def test_pipeline_fp64_iterates(name, N):
     x, y, r, eta = solve(qp, max_iter=N)
     xo, yo, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
     assert r["iterations"] == ro["iterations"] == N
+    assert r["form"] == 2                                   # the pipeline graph ran
     assert r["inner_method"] == ro["inner_method"]
     assert r["inner_iterations"] == ro["inner_iterations"]
     assert np.max(np.abs(x - xo)) <= 1e-10 * (1 + np.max(np.abs(xo)))
@@ -98,5 +99,6 @@ def test_pipeline_and_persistent_kernel_agree():
         xg, yg, rg = p.solve()
     finally:
         p.close()
+    assert rp["form"] == 2 and rg["form"] == 1
     assert rp["inner_iterations"] == rg["inner_iterations"]
     assert np.max(np.abs(xp - xg)) <= 1e-10 * (1 + np.max(np.abs(xg)))
