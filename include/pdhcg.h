@@ -129,6 +129,15 @@ typedef struct {
                                  the problem is large enough to fill the GPU (and Q is not
                                  structured), 1 = always (error if the graph cannot be
                                  built), -1 = never (the persistent multi-CTA kernel)         */
+  int32_t pool_threads;       /* threads of a pool CTA, the one-CTA solve of a small problem
+                                 (alone, batched or served): 0 = 256 (two per SM), or 128
+                                 (four per SM when a problem's vectors fit a quarter of the
+                                 SM's shared memory).  Part of the arithmetic's definition:
+                                 the two widths sum in different orders, and a problem gives
+                                 the same bits alone, batched or served only at one width.
+                                 A batch takes its first problem's value.  In a batched
+                                 launch that also holds multi-CTA groups the pool CTAs are
+                                 256 threads wide whatever this says                          */
 } pdhcg_params;
 
 typedef struct {
@@ -252,7 +261,7 @@ int pdhcg_solve_batch_noalloc(pdhcg_t* const* probs, int count, pdhcg_result* re
  * The paper has no counterpart (its kernels are not described).  Candidate
  * settings of the row layout (sell_sigma, long_row, huge_row) and of the launch
  * shape (for a single problem: the pipeline form against the persistent kernel
- * at several group_blocks; for a batch: pool_ctas_per_sm) are
+ * at several group_blocks; for a batch: pool_threads and pool_ctas_per_sm) are
  * timed on the device with CUDA events over a fixed number of PDHG steps of
  * the given problems (count == 1: one multi-CTA solve; count > 1: one batched
  * launch), and the fastest is written into *params.  The defaults are kept
@@ -270,6 +279,8 @@ typedef struct {
   int32_t from_cache;               /* 1: the shape class was tuned before in this process       */
   double seconds_per_step;          /* chosen configuration: device seconds per PDHG step       */
   double default_seconds_per_step;  /* the defaults, timed the same way                          */
+  int32_t pool_threads;             /* chosen pdhcg_params.pool_threads (0 = default)            */
+  int32_t reserved;
 } pdhcg_tuning;
 int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdhcg_params* params, void* cuda_stream,
                    pdhcg_tuning* out);

@@ -6,7 +6,8 @@
 //     row lengths above which a row gets a warp (long_row) or a CTA (huge_row);
 //   * launch shape: for a single solve, the pipeline form against the
 //     persistent multi-CTA kernel at several group sizes (group_blocks); for
-//     a batched launch, the cap on resident pool CTAs per SM.
+//     a batched launch, the pool CTA width (256 or 128 threads) and the cap on
+//     resident pool CTAs per SM.
 // Search: coordinate descent from the defaults, launch shape first (no
 // re-creation needed), then the layout with the best shape.  Each candidate
 // runs kSteps PDHG steps (a warm-up solve, then a timed one) between two CUDA
@@ -34,7 +35,7 @@ constexpr int kSteps = 64;            // PDHG steps per timing (one check period
 constexpr double kMargin = 0.03;      // a candidate must beat the defaults by this much
 
 struct Knobs {
-  int32_t sigma = 0, long_row = 0, huge_row = 0, group_blocks = 0, pool_cap = 0, pipeline = 0;
+  int32_t sigma = 0, long_row = 0, huge_row = 0, group_blocks = 0, pool_cap = 0, pipeline = 0, pool_threads = 0;
 };
 
 std::mutex g_mu;
@@ -85,6 +86,7 @@ void apply(const Knobs& k, pdhcg_params* p) {
   p->group_blocks = k.group_blocks;
   p->pool_ctas_per_sm = k.pool_cap;
   p->pipeline = k.pipeline;
+  p->pool_threads = k.pool_threads;
 }
 
 // Device seconds per PDHG step of one configuration (<= 0: it failed).
@@ -149,7 +151,7 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
       out->from_cache = 1;
       out->candidates = 0;
       Knobs k{out->sell_sigma, out->long_row, out->huge_row, out->group_blocks, out->pool_ctas_per_sm,
-              out->pipeline};
+              out->pipeline, out->pool_threads};
       apply(k, params);
       return PDHCG_OK;
     }
@@ -179,6 +181,9 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
     std::vector<Knobs> c{best};
     if (count > 1) {
       Knobs k = best;
+      k.pool_threads = 128;  // narrow CTAs, as many per SM as fit
+      c.push_back(k);
+      k = best;
       k.pool_cap = 1;
       c.push_back(k);
     } else {
@@ -222,6 +227,7 @@ extern "C" int pdhcg_autotune(int count, const pdhcg_problem_data* problems, pdh
   out->group_blocks = best.group_blocks;
   out->pool_ctas_per_sm = best.pool_cap;
   out->pipeline = best.pipeline;
+  out->pool_threads = best.pool_threads;
   out->candidates = timed;
   out->from_cache = 0;
   out->seconds_per_step = t_best;

@@ -21,6 +21,7 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
   cudaError_t e = cudaSuccess;
   for (const void* f : {(const void*)solve_kernel<kGroupBS, MatT, VecT, false>,
                         (const void*)solve_kernel<kGroupBS, MatT, VecT, true>,
+                        (const void*)solve_kernel<kGroupBS, MatT, VecT, false, true>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, false>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, true>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, false, true>})
@@ -28,21 +29,47 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
   return e;
 }
 
+// The three pool variants (plain, structured, closed form) of one width.
 template <class MatT, class VecT>
-int pool_blocks_per_sm(size_t smem_vec_bytes) {
-  int nb = 0, nr = 0;
+void pool_kernels(int bs, const void* (&f)[3]) {
+  if (bs == kGroupBS) {
+    f[0] = (const void*)solve_kernel<kGroupBS, MatT, VecT, false>;
+    f[1] = (const void*)solve_kernel<kGroupBS, MatT, VecT, true>;
+    f[2] = (const void*)solve_kernel<kGroupBS, MatT, VecT, false, true>;
+  } else {
+    f[0] = (const void*)solve_kernel<kPoolBS, MatT, VecT, false>;
+    f[1] = (const void*)solve_kernel<kPoolBS, MatT, VecT, true>;
+    f[2] = (const void*)solve_kernel<kPoolBS, MatT, VecT, false, true>;
+  }
+}
+
+template <class MatT, class VecT>
+int pool_blocks_per_sm(size_t smem_vec_bytes, int bs) {
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
-  int nd = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kPoolBS, MatT, VecT, false>, kPoolBS,
-                                                    smem_vec_bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, solve_kernel<kPoolBS, MatT, VecT, true>, kPoolBS,
-                                                    smem_vec_bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, solve_kernel<kPoolBS, MatT, VecT, false, true>, kPoolBS,
-                                                    smem_vec_bytes) != cudaSuccess)
-    return 0;
-  nb = std::min(nb, std::min(nr, nd));
+  const void* f[3];
+  pool_kernels<MatT, VecT>(bs, f);
+  int nb = 1 << 30;
+  for (const void* k : f) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, bs, smem_vec_bytes) != cudaSuccess) return 0;
+    nb = std::min(nb, b);
+  }
   if (PDHCG_POOL_MAX_PER_SM > 0) nb = std::min(nb, int(PDHCG_POOL_MAX_PER_SM));
   return nb;
+}
+
+template <class MatT, class VecT>
+size_t pool_smem_for(int per_sm, int bs) {
+  if (set_solve_attrs<MatT, VecT>(~size_t(0) >> 1) != cudaSuccess) return 0;  // the opt-in maximum
+  const void* f[3];
+  pool_kernels<MatT, VecT>(bs, f);
+  size_t best = ~size_t(0);
+  for (const void* k : f) {
+    size_t b = 0;
+    if (cudaOccupancyAvailableDynamicSMemPerBlock(&b, k, std::max(per_sm, 1), bs) != cudaSuccess) return 0;
+    best = std::min(best, b);
+  }
+  return best & ~size_t(15);
 }
 
 template <class MatT, class VecT>
@@ -103,6 +130,15 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   if (e != cudaSuccess) return e;
   const size_t smem = extra;
   const bool r = plan.structured != 0;
+  if (plan.group_blocks == 0 && plan.pool_bs == kGroupBS) {  // wide pool CTAs
+    if (r)
+      solve_kernel<kGroupBS, MatT, VecT, true><<<grid, kGroupBS, smem, s>>>(di, p);
+    else if (plan.diag_only)
+      solve_kernel<kGroupBS, MatT, VecT, false, true><<<grid, kGroupBS, smem, s>>>(di, p);
+    else
+      solve_kernel<kGroupBS, MatT, VecT, false><<<grid, kGroupBS, smem, s>>>(di, p);
+    return cudaGetLastError();
+  }
   if (plan.group_blocks == 0) {
     if (r)
       solve_kernel<kPoolBS, MatT, VecT, true><<<grid, kPoolBS, smem, s>>>(di, p);
@@ -253,7 +289,8 @@ int pipeline_blocks_per_sm() {
   template cudaError_t launch_setup<MatT, VecT>(const SetupArgs<MatT, VecT>&, int,             \
                                                 unsigned long long*, double*, int32_t*,        \
                                                 uint64_t, cudaStream_t);                       \
-  template int pool_blocks_per_sm<MatT, VecT>(size_t);                                          \
+  template int pool_blocks_per_sm<MatT, VecT>(size_t, int);                                     \
+  template size_t pool_smem_for<MatT, VecT>(int, int);                                          \
   template int group_blocks_per_sm<MatT, VecT>(size_t);                                         \
   template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
                                                      int32_t*, uint64_t, cudaStream_t);           \

@@ -10,14 +10,16 @@ namespace pdhcg {
 template <class MatT, class VecT>
 struct SetupArgs;
 
-// CTA sizes: multi-CTA groups (one large instance) and pooled single-CTA solves.
-// Pool CTAs of 128 threads idle fewer lanes on small instances (an MPC block has
-// a few hundred rows) and halve the per-instance local-memory footprint.
+// CTA sizes: multi-CTA groups (one large instance) and pooled single-CTA
+// solves.  Pool CTAs come in two widths (pdhcg_params.pool_threads): 256
+// threads (the default; the group kernel's own code, two CTAs per SM), or 128
+// threads compiled for four CTAs per SM, which runs more instances at once
+// when their vectors fit a quarter of the SM's shared memory.
 constexpr int kGroupBS = 256;
 #ifndef PDHCG_POOL_BS
 #define PDHCG_POOL_BS 128
 #endif
-constexpr int kPoolBS = PDHCG_POOL_BS;
+constexpr int kPoolBS = PDHCG_POOL_BS;  // the narrow pool width
 // Upper bound on resident pool CTAs per SM (0: as many as fit).
 #ifndef PDHCG_POOL_MAX_PER_SM
 #define PDHCG_POOL_MAX_PER_SM 0
@@ -36,9 +38,15 @@ template <class MatT, class VecT>
 cudaError_t launch_setup(const SetupArgs<MatT, VecT>& a, int nblk, unsigned long long* bar,
                          double* part, int32_t* err, uint64_t timeout_ns, cudaStream_t s);
 
-// Resident pool CTAs per SM when each keeps smem_vec_bytes of vectors on chip.
+// Resident pool CTAs of `bs` threads (kPoolBS or kGroupBS) per SM when each
+// keeps smem_vec_bytes of vectors on chip.
 template <class MatT, class VecT>
-int pool_blocks_per_sm(size_t smem_vec_bytes);
+int pool_blocks_per_sm(size_t smem_vec_bytes, int bs);
+
+// Largest dynamic shared memory per pool CTA of `bs` threads (16-byte multiple)
+// with which per_sm of them fit on one SM; 0 if the runtime cannot say.
+template <class MatT, class VecT>
+size_t pool_smem_for(int per_sm, int bs);
 
 // Resident CTAs per SM of the group-size solve kernel (both variants) with
 // smem_vec_bytes of dynamic shared memory per CTA: the bound of a cooperative

@@ -570,6 +570,9 @@ size_t smem_need(const pdhcg_problem* P) {
   return smem_vector_bytes(P->n, P->m, P->method, vec_bytes(P->precision));
 }
 
+// Threads of the pool CTA that solves P alone, batched or served.
+int pool_width(const pdhcg_problem* P) { return P->prm.pool_threads == 128 ? kPoolBS : kGroupBS; }
+
 int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
   if (P->prm.group_blocks > 0) return std::min(P->prm.group_blocks, maxblk);
   const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ + P->nnzR : 0) + 2 * P->nnzA + P->n + P->m;
@@ -851,8 +854,8 @@ int solve_one(pdhcg_problem* P, const double* x0_d, const double* y0_d, pdhcg_re
       plan.pool_inst = P->plan_i32 + 3;
       plan.pool_next = P->plan_i32 + 4;
       plan.diag_only = P->method == PDHCG_INNER_DIAG && P->k == 0;
-      const size_t need = smem_need(P);
-      plan.smem_vec_bytes = need <= kSmemVecBudget ? int64_t(need) : 0;
+      plan.smem_vec_bytes = int64_t(std::min(smem_need(P), kSmemVecBudget));
+      plan.pool_bs = pool_width(P);
     }
     cudaError_t e = launch_solve<M, V>(static_cast<const Inst<M, V>*>(P->inst_d), plan, grid, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "solve launch");
@@ -912,6 +915,7 @@ int pdhcg_default_params(pdhcg_params* p) {
   p->huge_row = 0;
   p->pool_ctas_per_sm = 0;
   p->pipeline = 0;
+  p->pool_threads = 0;
   return PDHCG_OK;
 }
 
@@ -926,6 +930,7 @@ static int check_params(const pdhcg_params* p) {
       (p->lanes_override != 0 && (p->lanes_override > 32 || (p->lanes_override & (p->lanes_override - 1)))) ||
       p->sell_sigma < 0 || p->long_row < 0 || p->huge_row < 0 || p->pool_ctas_per_sm < 0 ||
       p->pipeline < -1 || p->pipeline > 1 ||
+      (p->pool_threads != 0 && p->pool_threads != 128 && p->pool_threads != 256) ||
       sell_layout_of(*p).long_row >= sell_layout_of(*p).huge_row) {
     set_error("params: value out of range");
     return PDHCG_E_INVALID;
@@ -1310,12 +1315,12 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
   const pdhcg_problem* P0 = probs[0];
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P0->device));
-  size_t need = 0;
+  size_t need = 0;  // vectors of the largest pool instance, up to the budget
   int nsmall = 0;
   for (int i = 0; i < count; ++i) {
-    const size_t b = smem_need(probs[i]);
-    if (b <= kSmemVecBudget) need = std::max(need, b);
-    nsmall += batch_group_blocks(probs[i]) <= 1;
+    const bool small = batch_group_blocks(probs[i]) <= 1;
+    if (small) need = std::max(need, std::min(smem_need(probs[i]), kSmemVecBudget));
+    nsmall += small;
   }
   const bool any_large = nsmall < count;
   // co-resident CTAs of the cooperative launch (its dynamic shared memory:
@@ -1410,8 +1415,14 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
     if (e != cudaSuccess) return cuda_fail(e, "group launch");
   }
   if (npool > 0) {
-    int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    // As many pool CTAs per SM as registers allow (or pool_ctas_per_sm); each
+    // keeps what fits of its instance's vectors in its share of shared memory.
+    const int bs = pool_width(P0);
+    int per_sm = std::max(1, pool_blocks_per_sm<M, V>(0, bs));
     if (P0->prm.pool_ctas_per_sm > 0) per_sm = std::min(per_sm, P0->prm.pool_ctas_per_sm);
+    pool.pool_bs = bs;
+    pool.smem_vec_bytes = int64_t(std::min(need, pool_smem_for<M, V>(per_sm, bs)));
+    per_sm = std::min(per_sm, std::max(1, pool_blocks_per_sm<M, V>(size_t(pool.smem_vec_bytes), bs)));
     const cudaError_t e = launch_solve<M, V>(di, pool, std::max(1, std::min(npool, per_sm * sms)), s);
     if (e != cudaSuccess) {
       if (ng > 0) (void)cudaStreamSynchronize(split->group_stream);
@@ -1916,10 +1927,11 @@ int solve_batch_noalloc_impl(pdhcg_t* const* probs, int count, pdhcg_result* res
     plan.err = d_i32 + count + 1;
     plan.iter_budget = 0;
     plan.smem_vec_bytes = int64_t(need);
+    plan.pool_bs = pool_width(P0);
     plan.timeout_ns = uint64_t(std::max(P0->prm.device_timeout_ms, 1)) * 1000000ull;
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P0->device));
-    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need));
+    const int per_sm = std::max(1, pool_blocks_per_sm<M, V>(need, plan.pool_bs));
     const int grid = std::max(1, std::min(count, per_sm * sms));
     cudaError_t e = launch_solve<M, V>(reinterpret_cast<const Inst<M, V>*>(d_inst), plan, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "solve_batch_noalloc launch");

@@ -174,6 +174,9 @@ struct LaunchPlan {
   // Pool CTAs copy an instance's vectors into dynamic shared memory when they
   // fit in this many bytes (0 = never); see smem_vector_bytes().
   int64_t smem_vec_bytes = 0;
+  // Threads of a pool CTA in a launch without groups: 256 (the group kernel's
+  // width) or 128 (the narrow pool kernel); see pdhcg_params.pool_threads.
+  int32_t pool_bs = 256;
   uint64_t timeout_ns = 8000000000ull;  // bound on any device wait
   int32_t* err = nullptr;               // set to 1 when a bounded wait gave up
   // Some instance has a structured Q = P + R^T R: launch the kernel variant

@@ -1027,70 +1027,92 @@ __device__ __forceinline__ void copy_inst(Inst<MatT, VecT>& dst, const Inst<MatT
   __syncthreads();
 }
 
+// Solve one pool instance with its vectors in the CTA's shared memory
+// (plan.smem_vec_bytes of it).  The vectors are placed in order of how much a
+// PDHG step relies on them, each while it still fits: first those the matrix
+// products gather at random (y for A^T y; xbar for A xbar; with an inner solver
+// also x, T(x) and its work vectors for the Q products), then the iterate and
+// anchor entries every step reads, then the problem data it reads (c, bounds,
+// diag Q), last T(z), which a step only writes.  A vector that does not fit
+// stays in global memory, where the iteration reads and writes it in place, so
+// an instance larger than the budget keeps its hottest vectors on chip and more
+// CTAs fit on an SM.  Placement changes no arithmetic: the results are the same
+// bits as with every vector in global memory.
 template <int BS, bool kR, class MatT, class VecT, bool kDiag = false>
 __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, VecT>& Ig, Inst<MatT, VecT>& I,
                                            const LaunchPlan& plan, const RowCtx& rc, char* base,
                                            int method) {
   const int n = Ig.n, m = Ig.m;
+  const size_t cap = size_t(plan.smem_vec_bytes);
   size_t off = 0;
-  auto take = [&](size_t bytes) {
-    char* p = base + off;
-    off += (bytes + 15) & ~size_t(15);
-    return p;
+  // a shared-memory slot for `count` entries like *p if one is left, else p
+  auto place = [&](auto* p, int count) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(p)>>;
+    const size_t bytes = (size_t(count) * sizeof(T) + 15) & ~size_t(15);
+    if (off + bytes > cap) return const_cast<T*>(p);
+    T* q = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return q;
   };
-  const size_t nb = size_t(n) * sizeof(VecT), mb = size_t(m) * sizeof(VecT);
-  VecT* xb0 = reinterpret_cast<VecT*>(take(nb));
-  VecT* xb1 = reinterpret_cast<VecT*>(take(nb));
-  VecT* xT = reinterpret_cast<VecT*>(take(nb));
-  VecT* xa = reinterpret_cast<VecT*>(take(nb));
-  VecT* xbar = reinterpret_cast<VecT*>(take(nb));
-  VecT* c = reinterpret_cast<VecT*>(take(nb));
-  VecT* lv = reinterpret_cast<VecT*>(take(nb));
-  VecT* uv = reinterpret_cast<VecT*>(take(nb));
-  VecT* qd = reinterpret_cast<VecT*>(take(nb));
-  if (method == PDHCG_INNER_CG || method == PDHCG_INNER_BB) {
-    VecT* e0 = reinterpret_cast<VecT*>(take(nb));
-    VecT* e1 = reinterpret_cast<VecT*>(take(nb));
-    VecT* e2 = reinterpret_cast<VecT*>(take(nb));
-    VecT* e3 = reinterpret_cast<VecT*>(take(nb));
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (method == PDHCG_INNER_CG) {
-        I.r = e0; I.p0 = e1; I.p1 = e2; I.q = e3;
-      } else {
-        I.bv = e0; I.grad = e1; I.gprev = e2; I.xprev = e3;
-      }
-    }
+  const bool inner = method == PDHCG_INNER_CG || method == PDHCG_INNER_BB;
+  VecT *e0 = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr;
+  VecT *xT = Ig.xT, *yT = Ig.yT;
+  VecT* yb0 = place(Ig.yb0, m);
+  VecT* yb1 = place(Ig.yb1, m);
+  VecT *xb0, *xb1, *xbar;
+  if (inner) {
+    xb0 = place(Ig.xb0, n);
+    xb1 = place(Ig.xb1, n);
+    xT = place(Ig.xT, n);
+    e0 = place(method == PDHCG_INNER_CG ? Ig.r : Ig.bv, n);
+    e1 = place(method == PDHCG_INNER_CG ? Ig.p0 : Ig.grad, n);
+    e2 = place(method == PDHCG_INNER_CG ? Ig.p1 : Ig.gprev, n);
+    e3 = place(method == PDHCG_INNER_CG ? Ig.q : Ig.xprev, n);
+    xbar = place(Ig.xbar, n);
+  } else {
+    xbar = place(Ig.xbar, n);
+    xb0 = place(Ig.xb0, n);
+    xb1 = place(Ig.xb1, n);
   }
-  VecT* yb0 = reinterpret_cast<VecT*>(take(mb));
-  VecT* yb1 = reinterpret_cast<VecT*>(take(mb));
-  VecT* yT = reinterpret_cast<VecT*>(take(mb));
-  VecT* ya = reinterpret_cast<VecT*>(take(mb));
-  VecT* lc = reinterpret_cast<VecT*>(take(mb));
-  VecT* uc = reinterpret_cast<VecT*>(take(mb));
-  int8_t* vt = reinterpret_cast<int8_t*>(take(size_t(n)));
-  int8_t* ct = reinterpret_cast<int8_t*>(take(size_t(m)));
+  VecT* xa = place(Ig.xa, n);
+  VecT* ya = place(Ig.ya, m);
+  VecT* c = place(Ig.c, n);
+  VecT* qd = place(Ig.qdiag, n);
+  VecT* lv = place(Ig.lv, n);
+  VecT* uv = place(Ig.uv, n);
+  VecT* lc = place(Ig.lc, m);
+  VecT* uc = place(Ig.uc, m);
+  int8_t* vt = place(Ig.vtype, n);
+  int8_t* ct = place(Ig.ctype, m);
+  if (!inner) xT = place(Ig.xT, n);
+  yT = place(Ig.yT, m);
   const SolverState& S0 = *Ig.st;
   const bool started = S0.started != 0;
   const int cur = S0.cur;
+  VecT* xc = cur ? xb1 : xb0;
+  const VecT* xcg = cur ? Ig.xb1 : Ig.xb0;
+  VecT* yc = cur ? yb1 : yb0;
+  const VecT* ycg = cur ? Ig.yb1 : Ig.yb0;
+  // copies into the shared-memory slots only (a vector left in global memory
+  // is already in place)
   for (int i = threadIdx.x; i < n; i += BS) {
-    c[i] = Ig.c[i];
-    lv[i] = Ig.lv[i];
-    uv[i] = Ig.uv[i];
-    qd[i] = Ig.qdiag[i];
-    vt[i] = Ig.vtype[i];
+    if (c != Ig.c) c[i] = Ig.c[i];
+    if (lv != Ig.lv) lv[i] = Ig.lv[i];
+    if (uv != Ig.uv) uv[i] = Ig.uv[i];
+    if (qd != Ig.qdiag) qd[i] = Ig.qdiag[i];
+    if (vt != Ig.vtype) vt[i] = Ig.vtype[i];
     if (started) {
-      (cur ? xb1 : xb0)[i] = (cur ? Ig.xb1 : Ig.xb0)[i];
-      xa[i] = Ig.xa[i];
+      if (xc != xcg) xc[i] = xcg[i];
+      if (xa != Ig.xa) xa[i] = Ig.xa[i];
     }
   }
   for (int i = threadIdx.x; i < m; i += BS) {
-    lc[i] = Ig.lc[i];
-    uc[i] = Ig.uc[i];
-    ct[i] = Ig.ctype[i];
+    if (lc != Ig.lc) lc[i] = Ig.lc[i];
+    if (uc != Ig.uc) uc[i] = Ig.uc[i];
+    if (ct != Ig.ctype) ct[i] = Ig.ctype[i];
     if (started) {
-      (cur ? yb1 : yb0)[i] = (cur ? Ig.yb1 : Ig.yb0)[i];
-      ya[i] = Ig.ya[i];
+      if (yc != ycg) yc[i] = ycg[i];
+      if (ya != Ig.ya) ya[i] = Ig.ya[i];
     }
   }
   __syncthreads();
@@ -1098,36 +1120,51 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
     I.xb0 = xb0; I.xb1 = xb1; I.xT = xT; I.xa = xa; I.xbar = xbar;
     I.c = c; I.lv = lv; I.uv = uv; I.qdiag = qd; I.vtype = vt;
     I.yb0 = yb0; I.yb1 = yb1; I.yT = yT; I.ya = ya; I.lc = lc; I.uc = uc; I.ctype = ct;
+    if (method == PDHCG_INNER_CG) {
+      I.r = e0; I.p0 = e1; I.p1 = e2; I.q = e3;
+    } else if (method == PDHCG_INNER_BB) {
+      I.bv = e0; I.grad = e1; I.gprev = e2; I.xprev = e3;
+    }
   }
   __syncthreads();
   solve_instance<BS, Ld::Cached, kR, MatT, VecT, kDiag>(g, I, plan, rc);
   __syncthreads();
   const int cur2 = Ig.st->cur;
+  VecT* xf = cur2 ? xb1 : xb0;
+  VecT* xfg = cur2 ? Ig.xb1 : Ig.xb0;
+  VecT* yf = cur2 ? yb1 : yb0;
+  VecT* yfg = cur2 ? Ig.yb1 : Ig.yb0;
   constexpr bool kLo = std::is_same<MatT, float>::value;
   for (int i = threadIdx.x; i < n; i += BS) {
-    (cur2 ? Ig.xb1 : Ig.xb0)[i] = (cur2 ? xb1 : xb0)[i];
-    Ig.xa[i] = xa[i];
-    if constexpr (kLo) Ig.c[i] = c[i];  // the defect-corrected data resumes with the iterate
+    if (xf != xfg) xfg[i] = xf[i];
+    if (xa != Ig.xa) Ig.xa[i] = xa[i];
+    if constexpr (kLo) {
+      if (c != Ig.c) Ig.c[i] = c[i];  // the defect-corrected data resumes with the iterate
+    }
   }
   for (int i = threadIdx.x; i < m; i += BS) {
-    (cur2 ? Ig.yb1 : Ig.yb0)[i] = (cur2 ? yb1 : yb0)[i];
-    Ig.ya[i] = ya[i];
+    if (yf != yfg) yfg[i] = yf[i];
+    if (ya != Ig.ya) Ig.ya[i] = ya[i];
     if constexpr (kLo) {
-      Ig.lc[i] = lc[i];
-      Ig.uc[i] = uc[i];
+      if (lc != Ig.lc) Ig.lc[i] = lc[i];
+      if (uc != Ig.uc) Ig.uc[i] = uc[i];
     }
   }
 }
 
-// Register cap: 2 resident CTAs per SM gives the 256-thread group kernel 128
-// registers and the 128-thread pool kernel 255. Measured against a cap of 4 on
-// the same build, it ran 16% more pooled MPC solves per second and cut the
-// per-iteration time of one large instance by 14%.
+// Register caps.  The 256-thread kernel (groups, and the default pool width)
+// is compiled for 2 resident CTAs per SM: 128 registers.  The narrow 128-thread
+// pool kernel is compiled for 4 per SM, also 128 registers; it pays off only
+// where four instances' vectors fit on one SM.  Measured on 4,096 MPC QPs:
+// with T = 20 (33 KB of vectors each) 4 CTAs per SM ran 43 % more solves per
+// second than 2 with 255 registers; with the horizons mixed (up to 88 KB) the
+// 256-thread CTAs ran 8 % more than 2 narrow CTAs per SM, and 17 % more with
+// T = 50.
 #ifndef PDHCG_MIN_BLOCKS
 #define PDHCG_MIN_BLOCKS 2
 #endif
 #ifndef PDHCG_POOL_MIN_BLOCKS
-#define PDHCG_POOL_MIN_BLOCKS PDHCG_MIN_BLOCKS
+#define PDHCG_POOL_MIN_BLOCKS 4
 #endif
 template <int BS, class MatT, class VecT, bool kR, bool kDiag = false>
 __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_POOL_MIN_BLOCKS) solve_kernel(const Inst<MatT, VecT>* insts, LaunchPlan plan) {
@@ -1176,9 +1213,8 @@ __global__ void __launch_bounds__(BS, BS == kGroupBS ? PDHCG_MIN_BLOCKS : PDHCG_
     g.epoch = 0;
     const Inst<MatT, VecT>& Ig = insts[plan.pool_inst[idx]];
     const int method = Ig.st->method;
-    const size_t need = smem_vector_bytes(Ig.n, Ig.m, method, sizeof(VecT));
     copy_inst<BS>(sh_inst, Ig);
-    if (plan.smem_vec_bytes > 0 && need <= size_t(plan.smem_vec_bytes) && Ig.st->status == 0) {
+    if (plan.smem_vec_bytes > 0 && Ig.st->status == 0) {
       solve_in_smem<BS, kR, MatT, VecT, kDiag>(g, Ig, sh_inst, plan, rc, dsm, method);
     } else {
       solve_instance<BS, Ld::Cached, kR, MatT, VecT, kDiag>(g, sh_inst, plan, rc);

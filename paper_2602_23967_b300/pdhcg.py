@@ -52,7 +52,7 @@ class Params(C.Structure):
         ("omega_clamp", C.c_double),
         ("group_blocks", C.c_int32), ("device_timeout_ms", C.c_int32),
         ("sell_sigma", C.c_int32), ("long_row", C.c_int32), ("huge_row", C.c_int32),
-        ("pool_ctas_per_sm", C.c_int32), ("pipeline", C.c_int32),
+        ("pool_ctas_per_sm", C.c_int32), ("pipeline", C.c_int32), ("pool_threads", C.c_int32),
     ]
 
 
@@ -84,7 +84,8 @@ class Tuning(C.Structure):
                 ("group_blocks", C.c_int32), ("pool_ctas_per_sm", C.c_int32), ("pipeline", C.c_int32),
                 ("candidates", C.c_int32),
                 ("from_cache", C.c_int32), ("seconds_per_step", C.c_double),
-                ("default_seconds_per_step", C.c_double)]
+                ("default_seconds_per_step", C.c_double), ("pool_threads", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ServerStats(C.Structure):
