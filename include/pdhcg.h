@@ -297,8 +297,9 @@ int pdhcg_get_info(const pdhcg_t* prob, int32_t* n, int32_t* m, size_t* device_b
 /* CUDA device ordinal the handle's data lives on (the device current at create). */
 int pdhcg_get_device(const pdhcg_t* prob, int32_t* device);
 
-/* Profiling aid: device-timer seconds of the last pdhcg_solve / pdhcg_solve_dev
- * on this handle, as seen by one thread of the first CTA, split into 8
+/* Profiling aid: device-timer seconds of the last pdhcg_solve / pdhcg_solve_dev /
+ * pdhcg_solve_batch of this handle, as seen by one thread of the first CTA
+ * (all zero unless the library was built with PDHCG_PHASE_TIMERS=1), split into 8
  * categories: [0] Phase I (A^T y, subproblem start), [1] inner-solver row phases
  * (Q p), [2] inner-solver elementwise phases, [3] Phase II (A xbar, dual step,
  * Halpern), [4] KKT / infeasibility checks, [5] group barriers and reductions,

@@ -1767,6 +1767,7 @@ int solve_batch_impl(pdhcg_t* const* probs, int count, pdhcg_result* res, double
   bool dev_err = false;
   for (int i = 0; i < count; ++i) {
     if (hs[i].device_error) dev_err = true;
+    probs[i]->last_state = hs[i];
     if (res) fill_result(probs[i], hs[i], res + i);
     if (want_x && x_out[i]) std::memcpy(x_out[i], hx.data() + xoff[i], sizeof(double) * size_t(probs[i]->n));
     if (want_y && y_out[i] && probs[i]->m_user)

@@ -811,6 +811,8 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   }
   S.form = g.nblk > 1 ? 1 : 0;
   const int64_t K_first = S.K;
+  // the next step count that is a multiple of k_eval (a check period ends there)
+  int64_t next_check = (S.K / P.k_eval + 1) * P.k_eval;
   // device-time slice budget (single-CTA solves): thread 0 reads the clock every
   // 16 steps and shares the decision, so the whole CTA pauses together
   __shared__ int sm_pause;
@@ -836,8 +838,8 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     if (!group_reduce<BS, 4, kWT>(g, red1, 0u)) { ok = false; break; }
     PDHCG_CLK(5);
 
-    // adaptive inner tolerance (Sec. 3.3)
-    const double eps = inner_tolerance<VecT>(S, P, method, red1[1], inv_tau);
+    // adaptive inner tolerance (Sec. 3.3); the closed form has no inner solve
+    const double eps = method == PDHCG_INNER_DIAG ? 0.0 : inner_tolerance<VecT>(S, P, method, red1[1], inv_tau);
 
     // inner solve (Sec. 2.2)
     if (method == PDHCG_INNER_CG) {
@@ -937,14 +939,26 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     const double dy2 = red2[0];
     const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
     const double mvh2 = method == PDHCG_INNER_DIAG ? red1[3] : red2[2];
-    const double fpr = sqrt(S.omega * dx2 + dy2 / S.omega);
+    // the step's square roots one lane each, so a warp issues one FP64 sequence
+    // for all three: the fixed-point residual (Sec. 3.2) and the primal movement
+    // for either outcome of the restart decision
+    double fpr, sq_dx, sq_mvh;
+    {
+      const int ln = threadIdx.x & 31;
+      const double sq = sqrt(ln == 0 ? S.omega * dx2 + dy2 / S.omega : ln == 1 ? dx2 : mvh2);
+      fpr = __shfl_sync(kFull, sq, 0);
+      sq_dx = __shfl_sync(kFull, sq, 1);
+      sq_mvh = __shfl_sync(kFull, sq, 2);
+    }
     if (S.k == 0) {
       S.fpr_anchor = fpr;
       S.fpr_last = fpr;
     }
 
     bool do_restart = false;
-    const bool check = ((S.K + 1) % P.k_eval == 0) || (S.K + 1 >= P.max_iter);
+    const bool period_end = S.K + 1 == next_check;
+    if (period_end) next_check += P.k_eval;
+    const bool check = period_end || (S.K + 1 >= P.max_iter);
     if (check) {
       double cv[18];
       if (kR && I.k > 0) {
@@ -988,12 +1002,12 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       restart_copy<BS>(I, cur, vlo, vhi, clo, chi);
       if (!group_sync<BS>(g)) { ok = false; break; }
       PDHCG_CLK(6);
-      S.mv = sqrt(dx2);
+      S.mv = sq_dx;
       S.k = 0;
       S.restarts += 1;
     } else {
       S.cur ^= 1;
-      S.mv = sqrt(mvh2);
+      S.mv = sq_mvh;
       S.k += 1;
     }
     S.K += 1;
@@ -1011,11 +1025,6 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   if (g.rank == 0 && threadIdx.x == 0) store_state(I.st, S);
 }
 
-
-// Solve one instance with every iteration vector held in shared memory.  The
-// iterate state (current x, y and the Halpern anchors) is copied in when the
-// solve resumes and copied back when it stops or pauses, so the global buffers
-// stay the state of record between launches.
 // Copy an instance descriptor into the CTA's shared copy (all threads call).
 template <int BS, class MatT, class VecT>
 __device__ __forceinline__ void copy_inst(Inst<MatT, VecT>& dst, const Inst<MatT, VecT>& src) {
