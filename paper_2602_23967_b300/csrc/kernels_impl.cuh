@@ -59,6 +59,22 @@ int pool_blocks_per_sm(size_t smem_vec_bytes, int bs) {
 }
 
 template <class MatT, class VecT>
+void set_pool_carveout(int bs, size_t smem, int per_sm) {
+  int dev = 0, max_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const void* f[3];
+  pool_kernels<MatT, VecT>(bs, f);
+  for (const void* k : f) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || max_sm <= 0) continue;
+    const size_t need = size_t(per_sm) * (smem + fa.sharedSizeBytes + 1024);
+    const int pct = int(std::min<size_t>(100, (need * 100 + size_t(max_sm) - 1) / size_t(max_sm)));
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  }
+}
+
+template <class MatT, class VecT>
 size_t pool_smem_for(int per_sm, int bs) {
   if (set_solve_attrs<MatT, VecT>(~size_t(0) >> 1) != cudaSuccess) return 0;  // the opt-in maximum
   const void* f[3];
@@ -291,6 +307,7 @@ int pipeline_blocks_per_sm() {
                                                 uint64_t, cudaStream_t);                       \
   template int pool_blocks_per_sm<MatT, VecT>(size_t, int);                                     \
   template size_t pool_smem_for<MatT, VecT>(int, int);                                          \
+  template void set_pool_carveout<MatT, VecT>(int, size_t, int);                                \
   template int group_blocks_per_sm<MatT, VecT>(size_t);                                         \
   template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
                                                      int32_t*, uint64_t, cudaStream_t);           \
