@@ -217,8 +217,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 285_549_312 + 141_981_440, "instances": 512,
-                   "sources_sha256": "0ed34b75fd5b2c5df3e159f4cc44ea65be63b15986a7acea680dc22923a507f7",
+TRAFFIC_CAPTURE = {"bytes": 1_765_971_968 + 1_222_429_696, "instances": 512,
+                   "sources_sha256": "071a00789d8ef088fc1b619ab413e195e506e5085e25bd535a4b761a12b1caaf",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")

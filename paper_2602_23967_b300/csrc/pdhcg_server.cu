@@ -2,10 +2,12 @@
 //
 // Two host threads own the device side.
 //   Admission thread: takes queued requests while a slot is free and their
-//     device footprint fits the HBM budget, and creates everything it took
-//     together with the batched creation path (one allocation, one setup
-//     launch) on its own stream, so creation and device setup of new requests
-//     overlap the slices of the running ones.  Finished handles go to a ready list.
+//     device footprint fits the HBM budget.  The small ones it took are
+//     created together with the batched creation path (one allocation, one
+//     setup launch), then one large one, and the thread looks at the queue
+//     again, so small requests never wait behind the preparation of several
+//     large ones.  Creation runs on its own stream and overlaps the slices of
+//     the running solves.  Finished handles go to a ready list.
 //   Slice thread: at each slice boundary moves ready handles into free slots,
 //     advances every live solve by one slice of 10 ms of device time
 //     (PDHCG_SLICE_US) in a single pooled launch (iterates, anchors, PID and restart state stay
@@ -194,8 +196,13 @@ static void admit_batch(pdhcg_server* S, std::vector<Request>& admit) {
   S->cv_work.notify_one();
 }
 
+// Takes queued requests while a slot and the HBM budget allow.  Small requests
+// are created together as one batch; large ones (multi-CTA groups) one per
+// round, after the small ones taken in that round, so a large request's host
+// preparation and setup never holds back small requests queued meanwhile.
 static void admit_loop(pdhcg_server* S) {
   cudaSetDevice(S->device);
+  std::deque<Request> large;  // taken from the queue, not yet created
   while (true) {
     std::vector<Request> admit;
     {
@@ -204,7 +211,7 @@ static void admit_loop(pdhcg_server* S) {
         return !S->queue.empty() && S->reserved < S->max_slots &&
                S->stats.hbm_in_use + S->queue.front().bytes <= S->budget;
       };
-      S->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || can_take(); });
+      if (large.empty()) S->cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return S->stop || can_take(); });
       if (S->stop) break;
       while (can_take()) {
         S->stats.hbm_in_use += S->queue.front().bytes;  // reserved until retirement
@@ -214,20 +221,18 @@ static void admit_loop(pdhcg_server* S) {
       }
       S->stats.queued = int32_t(S->queue.size());
     }
-    if (admit.empty()) continue;
-    // Small requests first, as one batch, then each large one on its own: a
-    // large request's host preparation and setup must not hold back the small
-    // ones admitted with it.
-    std::vector<Request> small, large;
+    std::vector<Request> small;
     for (auto& r : admit) {
       const OwnedProblem& p = r.prob;
       const int64_t work = int64_t(p.qc.size()) + 2 * int64_t(p.ac.size()) + p.n + p.m;
-      (work < kGroupWork ? small : large).push_back(std::move(r));
+      if (work < kGroupWork) small.push_back(std::move(r));
+      else large.push_back(std::move(r));
     }
     if (!small.empty()) admit_batch(S, small);
-    for (auto& r : large) {
+    if (!large.empty()) {
       std::vector<Request> one;
-      one.push_back(std::move(r));
+      one.push_back(std::move(large.front()));
+      large.pop_front();
       admit_batch(S, one);
     }
   }
