@@ -27,7 +27,10 @@ namespace pdhcg {
 using ::fma;
 using ::fmaf;
 
-struct dfloat {
+// 8-byte aligned, so that an entry moves as one 64-bit load or store (a gather
+// is one memory request, a shared-memory access one 64-bit word); every array of
+// them starts on a 16-byte (shared memory) or 256-byte (device arena) boundary.
+struct __align__(8) dfloat {
   float hi, lo;
   dfloat() = default;
   __host__ __device__ __forceinline__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}

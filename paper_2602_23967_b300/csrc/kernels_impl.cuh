@@ -6,9 +6,21 @@
 #include "solve_kernel.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace pdhcg {
 
+// Kernel attributes (dynamic shared-memory limit, carveout hint) belong to the
+// function and the process; every reader or writer of them holds this lock.
+inline std::mutex& attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+// Sets the dynamic shared-memory limit of the six solve kernels and their
+// carveout hint to the largest shared-memory share, so that occupancy queries
+// report what a launch can get; a launch then narrows the hint of the kernel it
+// issues (launch_solve).  The caller holds attr_mutex().
 template <class MatT, class VecT>
 cudaError_t set_solve_attrs(size_t extra = 0) {
   int dev = 0, optin = 0;
@@ -25,7 +37,11 @@ cudaError_t set_solve_attrs(size_t extra = 0) {
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, false>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, true>,
                         (const void*)solve_kernel<kPoolBS, MatT, VecT, false, true>})
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
+    if (e == cudaSuccess) {
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(want));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
+    }
   return e;
 }
 
@@ -45,6 +61,7 @@ void pool_kernels(int bs, const void* (&f)[3]) {
 
 template <class MatT, class VecT>
 int pool_blocks_per_sm(size_t smem_vec_bytes, int bs) {
+  std::lock_guard<std::mutex> lock(attr_mutex());
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
   const void* f[3];
   pool_kernels<MatT, VecT>(bs, f);
@@ -58,24 +75,26 @@ int pool_blocks_per_sm(size_t smem_vec_bytes, int bs) {
   return nb;
 }
 
-template <class MatT, class VecT>
-void set_pool_carveout(int bs, size_t smem, int per_sm) {
+// Shared-memory carveout hint of kernel k: just what per_sm resident CTAs with
+// smem bytes of dynamic shared memory each need; the rest of the SM's
+// L1/shared storage stays L1, which caches the matrix streams and gathers.
+// The hint belongs to the function, and one function serves pool launches
+// (vectors in shared memory) and group launches (almost none), so every launch
+// sets it right before it is issued (launch_solve, under attr_mutex()).
+inline void set_carveout(const void* k, size_t smem, int per_sm) {
   int dev = 0, max_sm = 0;
-  cudaGetDevice(&dev);
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
   cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const void* f[3];
-  pool_kernels<MatT, VecT>(bs, f);
-  for (const void* k : f) {
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || max_sm <= 0) continue;
-    const size_t need = size_t(per_sm) * (smem + fa.sharedSizeBytes + 1024);
-    const int pct = int(std::min<size_t>(100, (need * 100 + size_t(max_sm) - 1) / size_t(max_sm)));
-    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || max_sm <= 0) return;
+  const size_t need = size_t(std::max(per_sm, 1)) * (smem + fa.sharedSizeBytes + 1024);
+  const int pct = int(std::min<size_t>(100, (need * 100 + size_t(max_sm) - 1) / size_t(max_sm)));
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
 template <class MatT, class VecT>
 size_t pool_smem_for(int per_sm, int bs) {
+  std::lock_guard<std::mutex> lock(attr_mutex());
   if (set_solve_attrs<MatT, VecT>(~size_t(0) >> 1) != cudaSuccess) return 0;  // the opt-in maximum
   const void* f[3];
   pool_kernels<MatT, VecT>(bs, f);
@@ -91,6 +110,7 @@ size_t pool_smem_for(int per_sm, int bs) {
 template <class MatT, class VecT>
 int group_blocks_per_sm(size_t smem_vec_bytes) {
   int nb = 0, nr = 0;
+  std::lock_guard<std::mutex> lock(attr_mutex());
   if (set_solve_attrs<MatT, VecT>(smem_vec_bytes) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS,
                                                     smem_vec_bytes) != cudaSuccess ||
@@ -107,6 +127,7 @@ cudaError_t kernel_limits(KernelLimits* out) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(attr_mutex());
   e = set_solve_attrs<MatT, VecT>();
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<kGroupBS, MatT, VecT, false>, kGroupBS, 0);
@@ -141,33 +162,30 @@ cudaError_t launch_solve(const Inst<MatT, VecT>* d_insts, const LaunchPlan& plan
   const Inst<MatT, VecT>* di = d_insts;
   // dynamic shared memory: the vectors of pool instances (a cooperative launch
   // with pool CTAs beside its groups gives it to every CTA; groups ignore it)
-  const size_t extra = size_t(plan.smem_vec_bytes);
-  cudaError_t e = set_solve_attrs<MatT, VecT>(extra);
+  const size_t smem = size_t(plan.smem_vec_bytes);
+  std::lock_guard<std::mutex> lock(attr_mutex());  // set the attributes and launch as one
+  cudaError_t e = set_solve_attrs<MatT, VecT>(smem);
   if (e != cudaSuccess) return e;
-  const size_t smem = extra;
   const bool r = plan.structured != 0;
-  if (plan.group_blocks == 0 && plan.pool_bs == kGroupBS) {  // wide pool CTAs
-    if (r)
-      solve_kernel<kGroupBS, MatT, VecT, true><<<grid, kGroupBS, smem, s>>>(di, p);
-    else if (plan.diag_only)
-      solve_kernel<kGroupBS, MatT, VecT, false, true><<<grid, kGroupBS, smem, s>>>(di, p);
-    else
-      solve_kernel<kGroupBS, MatT, VecT, false><<<grid, kGroupBS, smem, s>>>(di, p);
-    return cudaGetLastError();
-  }
-  if (plan.group_blocks == 0) {
-    if (r)
-      solve_kernel<kPoolBS, MatT, VecT, true><<<grid, kPoolBS, smem, s>>>(di, p);
-    else if (plan.diag_only)
-      solve_kernel<kPoolBS, MatT, VecT, false, true><<<grid, kPoolBS, smem, s>>>(di, p);
-    else
-      solve_kernel<kPoolBS, MatT, VecT, false><<<grid, kPoolBS, smem, s>>>(di, p);
-    return cudaGetLastError();
-  }
+  const bool coop = plan.group_blocks != 0;
+  const int bs = coop || plan.pool_bs == kGroupBS ? kGroupBS : kPoolBS;
+  const void* fn;
+  if (bs == kGroupBS)
+    fn = r ? (const void*)solve_kernel<kGroupBS, MatT, VecT, true>
+           : (!coop && plan.diag_only) ? (const void*)solve_kernel<kGroupBS, MatT, VecT, false, true>
+                                       : (const void*)solve_kernel<kGroupBS, MatT, VecT, false>;
+  else
+    fn = r ? (const void*)solve_kernel<kPoolBS, MatT, VecT, true>
+           : plan.diag_only ? (const void*)solve_kernel<kPoolBS, MatT, VecT, false, true>
+                            : (const void*)solve_kernel<kPoolBS, MatT, VecT, false>;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the CTAs per SM this grid needs resident (all of them, for a cooperative launch)
+  set_carveout(fn, smem, (grid + std::max(sms, 1) - 1) / std::max(sms, 1));
   void* args[] = {&di, &p};
-  return cudaLaunchCooperativeKernel(r ? (const void*)solve_kernel<kGroupBS, MatT, VecT, true>
-                                       : (const void*)solve_kernel<kGroupBS, MatT, VecT, false>,
-                                     dim3(grid), dim3(kGroupBS), args, smem, s);
+  if (coop) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGroupBS), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(bs), args, smem, s);
 }
 
 template <class MatT, class VecT>
@@ -307,7 +325,6 @@ int pipeline_blocks_per_sm() {
                                                 uint64_t, cudaStream_t);                       \
   template int pool_blocks_per_sm<MatT, VecT>(size_t, int);                                     \
   template size_t pool_smem_for<MatT, VecT>(int, int);                                          \
-  template void set_pool_carveout<MatT, VecT>(int, size_t, int);                                \
   template int group_blocks_per_sm<MatT, VecT>(size_t);                                         \
   template cudaError_t launch_setup_pool<MatT, VecT>(const SetupArgs<MatT, VecT>*, int, int*,   \
                                                      int32_t*, uint64_t, cudaStream_t);           \

@@ -48,12 +48,6 @@ int pool_blocks_per_sm(size_t smem_vec_bytes, int bs);
 template <class MatT, class VecT>
 size_t pool_smem_for(int per_sm, int bs);
 
-// Shared-memory carveout of the pool kernels of width bs: just what per_sm
-// CTAs with smem bytes of vectors need, the rest of the SM's L1/shared
-// storage left to L1 (which caches the matrix streams).
-template <class MatT, class VecT>
-void set_pool_carveout(int bs, size_t smem, int per_sm);
-
 // Resident CTAs per SM of the group-size solve kernel (both variants) with
 // smem_vec_bytes of dynamic shared memory per CTA: the bound of a cooperative
 // launch that mixes multi-CTA groups with pool CTAs.

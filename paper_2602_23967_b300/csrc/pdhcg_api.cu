@@ -1424,7 +1424,6 @@ int launch_batch(pdhcg_problem* const* probs, int count, std::vector<Inst<M, V>>
     pool.pool_bs = bs;
     pool.smem_vec_bytes = int64_t(std::min(need, pool_smem_for<M, V>(per_sm, bs)));
     per_sm = std::min(per_sm, std::max(1, pool_blocks_per_sm<M, V>(size_t(pool.smem_vec_bytes), bs)));
-    set_pool_carveout<M, V>(bs, size_t(pool.smem_vec_bytes), per_sm);
     const cudaError_t e = launch_solve<M, V>(di, pool, std::max(1, std::min(npool, per_sm * sms)), s);
     if (e != cudaSuccess) {
       if (ng > 0) (void)cudaStreamSynchronize(split->group_stream);
