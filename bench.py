@@ -217,8 +217,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 1_765_971_968 + 1_222_429_696, "instances": 512,
-                   "sources_sha256": "071a00789d8ef088fc1b619ab413e195e506e5085e25bd535a4b761a12b1caaf",
+TRAFFIC_CAPTURE = {"bytes": 1_800_744_448 + 1_253_647_872, "instances": 512,
+                   "sources_sha256": "8a05ca147c95f6e7e06dec815eea41879950f274e6d9b5765859bb7ed393e1cc",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
@@ -337,7 +337,53 @@ def large_instance_leg(args, stream, peak_gbs):
                         f"{r['iterations']} PDHG steps ({r['inner_iterations']} BB steps)",
             "form": forms.get(r["form"], r["form"]),
             "us_per_step": ms * 1e3 / r["iterations"], "algorithmic_bytes": alg,
-            "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak_gbs, "autotune": tune}
+            "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak_gbs, "autotune": tune,
+            "calibration": gather_calibration(qp.Q, stream)}
+
+
+def gather_calibration(Q, stream, reps=20):
+    """Library reference points on the same Q (2e7 nonzeros at uniformly random
+    columns), timed with CUDA events: torch.index_select of an 8-byte entry per
+    nonzero from an n-entry table (the random-gather rate of the device when the
+    table sits in L2, plus the index and output streams) and the cuSPARSE SpMV
+    behind torch.mv on a CSR tensor, FP32 and FP64.  Not part of the solver."""
+    import warnings
+
+    import torch
+    dev = torch.device("cuda")
+    crow = torch.from_numpy(Q.indptr.astype(np.int32)).to(dev)
+    col = torch.from_numpy(Q.indices.astype(np.int32)).to(dev)
+    val = torch.from_numpy(Q.data).to(dev)
+    n, nnz = Q.shape[0], Q.nnz
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        out = {}
+        tab = torch.randn(n, dtype=torch.float64, device=dev)
+        idx = col.long()
+        us = timed(lambda: torch.index_select(tab, 0, idx))
+        out["index_select_8B_us"] = us
+        out["random_gathers_per_s"] = nnz / (us * 1e-6)
+        for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+            M = torch.sparse_csr_tensor(crow, col, val.to(dt), size=(n, n))
+            x = torch.randn(n, dtype=dt, device=dev)
+            out[f"cusparse_{name}_spmv_us"] = timed(lambda: torch.mv(M, x))
+        del tab, idx
+    out["note"] = ("reference points only: the solver's Q product is its own kernel; per PDHG step it "
+                   "runs about (1 + BB steps per PDHG step) of them")
+    return out
 
 
 def serve_trace(prm, stream, trace, qps, slots, drain_s=90.0):
