@@ -818,10 +818,30 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   __shared__ int sm_pause;
   const uint64_t t_resume = globaltimer_ns();
 
+  // The step's FP64 scalars are computed by warp 0 alone and handed to the CTA
+  // through shared memory: every warp computing them would occupy the narrow
+  // FP64 pipe eight times over.  Same operations on the same values, so the
+  // results are the bits each warp would compute.  A box is rewritten only
+  // after the group reductions that follow its reads.
+  __shared__ StepScalars<CT> sm_sc;
+  __shared__ double sm_scal[5];  // 1/tau, 1/sigma, then the step's three square roots
+
   while (ok) {
     const int cur = S.cur;
     double inv_tau, inv_sigma;
-    const StepScalars<CT> sc = step_scalars<CT>(S, P, inv_tau, inv_sigma);
+    StepScalars<CT> sc;
+    if (threadIdx.x < 32) {
+      sc = step_scalars<CT>(S, P, inv_tau, inv_sigma);
+      if (threadIdx.x == 0) {
+        sm_sc = sc;
+        sm_scal[0] = inv_tau;
+        sm_scal[1] = inv_sigma;
+      }
+    }
+    __syncthreads();
+    sc = sm_sc;
+    inv_tau = sm_scal[0];
+    inv_sigma = sm_scal[1];
 
     // Phase I (structured Q: R x first)
     if (kR && I.k > 0 && method != PDHCG_INNER_DIAG) {
@@ -943,13 +963,15 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     // for all three: the fixed-point residual (Sec. 3.2) and the primal movement
     // for either outcome of the restart decision
     double fpr, sq_dx, sq_mvh;
-    {
-      const int ln = threadIdx.x & 31;
+    if (threadIdx.x < 32) {  // warp 0, lane q: root q
+      const int ln = threadIdx.x;
       const double sq = sqrt(ln == 0 ? S.omega * dx2 + dy2 / S.omega : ln == 1 ? dx2 : mvh2);
-      fpr = __shfl_sync(kFull, sq, 0);
-      sq_dx = __shfl_sync(kFull, sq, 1);
-      sq_mvh = __shfl_sync(kFull, sq, 2);
+      if (ln < 3) sm_scal[2 + ln] = sq;
     }
+    __syncthreads();
+    fpr = sm_scal[2];
+    sq_dx = sm_scal[3];
+    sq_mvh = sm_scal[4];
     if (S.k == 0) {
       S.fpr_anchor = fpr;
       S.fpr_last = fpr;
