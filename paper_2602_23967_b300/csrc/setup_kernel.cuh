@@ -443,9 +443,14 @@ __global__ void __launch_bounds__(BS) setup_kernel(SetupArgs<MatT, VecT> a, unsi
 }
 
 // Setup of many instances in one launch: each CTA takes the next instance from a
-// queue and sets it up alone.
+// queue and sets it up alone.  Compiled for PDHCG_SETUP_POOL_MIN_BLOCKS resident
+// CTAs per SM: the setup of a small instance is a chain of dependent passes
+// (Ruiz, Lanczos), so more instances in flight per SM hide more of its latency.
+#ifndef PDHCG_SETUP_POOL_MIN_BLOCKS
+#define PDHCG_SETUP_POOL_MIN_BLOCKS 2
+#endif
 template <int BS, class MatT, class VecT>
-__global__ void __launch_bounds__(BS) setup_pool_kernel(const SetupArgs<MatT, VecT>* args, int count,
+__global__ void __launch_bounds__(BS, PDHCG_SETUP_POOL_MIN_BLOCKS) setup_pool_kernel(const SetupArgs<MatT, VecT>* args, int count,
                                                         int* next, int32_t* err, uint64_t timeout_ns) {
   __shared__ double sm_warp[2 * (BS / 32) * kSlots];
   __shared__ double sm_tot[2 * kSlots];
