@@ -57,9 +57,69 @@ struct PipeState {
   double mx[2];                // ray norms
   int32_t j, pc, bsel, brk, status, pad;
   unsigned ticket[8];          // last-CTA counters, one per kernel kind (reset by the last CTA)
+  // Scalars of the current step (PipeScalar slots), each set once by the one
+  // thread that takes the decisions and read by every CTA of the next kernels:
+  // the FP64 value and its double-float split (hi also being the FP32 value).
+  double sd[12];
+  float shi[12], slo[12];
 };
 
 static_assert(sizeof(PipeState) <= kPipeStateBytes, "pipeline state buffer too small");
+
+// The step scalars of the persistent kernel's step_scalars() (the first seven,
+// in its order), the inner solvers' step lengths, and 1/tau, 1/sigma in FP64.
+// Computing them once instead of in every thread of every CTA keeps the
+// kernels' prologues off the narrow FP64 pipe.
+enum PipeScalar : int { kPsItau, kPsIsig, kPsSig, kPsWk, kPsAk, kPsTh, kPsTh1, kPsAlpha, kPsBeta, kPsInvTau, kPsInvSigma };
+
+__device__ __forceinline__ void pipe_set(PipeState& P, int k, double v) {
+  const dfloat d(v);  // the conversion VecT(v) makes for double-float and FP32 vectors
+  P.sd[k] = v;
+  P.shi[k] = d.hi;
+  P.slo[k] = d.lo;
+}
+template <class VecT>
+__device__ __forceinline__ VecT pipe_get(const PipeState& P, int k) {
+  if constexpr (std::is_same<VecT, dfloat>::value) return dfloat(P.shi[k], P.slo[k]);
+  else if constexpr (std::is_same<VecT, float>::value) return P.shi[k];
+  else return P.sd[k];
+}
+template <class VecT>
+__device__ __forceinline__ StepScalars<VecT> pipe_step_scalars(const PipeState& P) {
+  StepScalars<VecT> sc;
+  sc.itau = pipe_get<VecT>(P, kPsItau);
+  sc.isig = pipe_get<VecT>(P, kPsIsig);
+  sc.sig = pipe_get<VecT>(P, kPsSig);
+  sc.wk = pipe_get<VecT>(P, kPsWk);
+  sc.ak = pipe_get<VecT>(P, kPsAk);
+  sc.th = pipe_get<VecT>(P, kPsTh);
+  sc.th1 = pipe_get<VecT>(P, kPsTh1);
+  return sc;
+}
+// The quotients step_scalars() takes, one by one (the same IEEE results).
+__device__ __forceinline__ void pipe_set_step(PipeState& P, const SolverState& S, const DevParams& prm) {
+  const double kp2 = double(S.k + 2);
+  pipe_set(P, kPsItau, 1.0 / S.tau);
+  pipe_set(P, kPsIsig, 1.0 / S.sigma);
+  pipe_set(P, kPsSig, S.sigma / 1.0);
+  pipe_set(P, kPsWk, double(S.k + 1) / kp2);
+  pipe_set(P, kPsAk, 1.0 / kp2);
+  pipe_set(P, kPsTh, prm.theta / 1.0);
+  pipe_set(P, kPsTh1, (1.0 + prm.theta) / 1.0);
+  P.sd[kPsInvTau] = P.sd[kPsItau];
+  P.sd[kPsInvSigma] = P.sd[kPsIsig];
+}
+// The BB step length of inner step j (j = 0: the lower bound of its range).
+__device__ __forceinline__ void pipe_set_bb_alpha(PipeState& P, const SolverState& S, int j, double ss, double sy) {
+  const double inv_tau = 1.0 / S.tau;
+  const double alpha_min = 1.0 / (S.gersh + inv_tau), alpha_max = 1.0 / inv_tau;
+  double alpha = alpha_min;
+  if (j > 0) {
+    alpha = sy > 0.0 ? ss / sy : alpha_max;
+    alpha = fmin(fmax(alpha, alpha_min), alpha_max);
+  }
+  pipe_set(P, kPsAlpha, alpha);
+}
 
 struct PipeArgs {
   const void* inst;  // the instance descriptor, Inst<MatT, VecT> (device)
@@ -217,6 +277,7 @@ PDHCG_PIPE_KERNEL pipe_init(PipeArgs a) {
     S.started = 1;
     S.cur = 0;
     S.form = 2;
+    pipe_set_step(*a.ps, S, I.prm);
   }
 }
 
@@ -229,8 +290,7 @@ PDHCG_PIPE_KERNEL pipe_phase1(PipeArgs a) {
   const RowCtx rc{sh.red};
   const SolverState& Sg = *I.st;  // read here; written only by the last CTA below
   const int method = Sg.method;
-  double inv_tau, inv_sigma;
-  const StepScalars<VecT> sc = step_scalars<VecT>(Sg, I.prm, inv_tau, inv_sigma);
+  const StepScalars<VecT> sc = pipe_step_scalars<VecT>(*a.ps);
   double v[4];
   {
     const Red<4> r = phase1<kPipeBS, Ld::Stream, false>(I, int(blockIdx.x), method, Sg.cur, sc, rc);
@@ -240,7 +300,7 @@ PDHCG_PIPE_KERNEL pipe_phase1(PipeArgs a) {
   if (!pipe_reduce<4, kWT>(v, 0u, a.part, &a.ps->ticket[1], sh) || threadIdx.x != 0) return;
   PipeState& P = *a.ps;
   SolverState S = *I.st;
-  const double eps = inner_tolerance<VecT>(S, I.prm, method, v[1], inv_tau);
+  const double eps = inner_tolerance<VecT>(S, I.prm, method, v[1], P.sd[kPsInvTau]);
   I.st->eps_in = S.eps_in;
 #pragma unroll
   for (int q = 0; q < 4; ++q) P.red1[q] = v[q];
@@ -250,6 +310,8 @@ PDHCG_PIPE_KERNEL pipe_phase1(PipeArgs a) {
   P.bsel = 0;
   P.brk = 0;
   P.beta = 0.0;
+  pipe_set(P, kPsBeta, 0.0);
+  pipe_set_bb_alpha(P, S, 0, 0.0, 0.0);
   P.rr = v[0];
   P.nr = v[0];
   P.ss = P.sy = 0.0;
@@ -266,11 +328,11 @@ PDHCG_PIPE_KERNEL pipe_cg_a(PipeArgs a) {
   const RowCtx rc{sh.red};
   const PipeState& P = *a.ps;
   const int j = P.j, pc = P.pc;
-  const double beta = P.beta;
   const VecT* pold = pc ? I.p1 : I.p0;
   VecT* pnew = pc ? I.p0 : I.p1;
-  const VecT itau = VecT(1.0 / I.st->tau);
-  double v[1] = {cg_phase_a<kPipeBS, Ld::Stream, false>(I, int(blockIdx.x), j == 0, VecT(beta), pold, pnew, itau, rc)};
+  const VecT itau = pipe_get<VecT>(P, kPsItau);
+  const VecT beta = pipe_get<VecT>(P, kPsBeta);
+  double v[1] = {cg_phase_a<kPipeBS, Ld::Stream, false>(I, int(blockIdx.x), j == 0, beta, pold, pnew, itau, rc)};
   if (!pipe_reduce<1, kWT>(v, 0u, a.part, &a.ps->ticket[2], sh) || threadIdx.x != 0) return;
   PipeState& Pw = *a.ps;
   if (!(v[0] > 0.0)) {
@@ -278,6 +340,7 @@ PDHCG_PIPE_KERNEL pipe_cg_a(PipeArgs a) {
     cudaGraphSetConditional(a.h.inner, 0u);
   } else {
     Pw.alpha = Pw.rr / v[0];
+    pipe_set(Pw, kPsAlpha, Pw.alpha);
   }
 }
 
@@ -292,10 +355,11 @@ PDHCG_PIPE_KERNEL pipe_cg_b(PipeArgs a) {
   int vlo, vhi, clo, chi;
   pipe_ranges(I, vlo, vhi, clo, chi);
   const VecT* pnew = P.pc ? I.p0 : I.p1;
-  double v[1] = {cg_phase_b<kPipeBS>(I, vlo, vhi, VecT(P.alpha), pnew)};
+  double v[1] = {cg_phase_b<kPipeBS>(I, vlo, vhi, pipe_get<VecT>(P, kPsAlpha), pnew)};
   if (!pipe_reduce<1, kWT>(v, 0u, a.part, &a.ps->ticket[3], sh) || threadIdx.x != 0) return;
   PipeState& Pw = *a.ps;
   Pw.beta = v[0] / Pw.rr;
+  pipe_set(Pw, kPsBeta, Pw.beta);
   Pw.rr = v[0];
   Pw.pc ^= 1;
   Pw.j += 1;
@@ -322,16 +386,8 @@ PDHCG_PIPE_KERNEL pipe_bb_b(PipeArgs a) {
   int vlo, vhi, clo, chi;
   pipe_ranges(I, vlo, vhi, clo, chi);
   const PipeState& P = *a.ps;
-  const SolverState& S = *I.st;
-  const double inv_tau = 1.0 / S.tau;
-  const double alpha_min = 1.0 / (S.gersh + inv_tau), alpha_max = 1.0 / inv_tau;
-  double alpha = alpha_min;
-  if (P.j > 0) {
-    alpha = P.sy > 0.0 ? P.ss / P.sy : alpha_max;
-    alpha = fmin(fmax(alpha, alpha_min), alpha_max);
-  }
   const BBBufs<MatT, VecT> b = bb_bufs(I, P.bsel);
-  bb_phase_b<kPipeBS>(I, vlo, vhi, VecT(alpha), b.xc, b.gc, b.xo);
+  bb_phase_b<kPipeBS>(I, vlo, vhi, pipe_get<VecT>(P, kPsAlpha), b.xc, b.gc, b.xo);
 }
 
 // ---- BB Phase A': gradient at the new x, BB quantities, natural residual ----
@@ -343,7 +399,7 @@ PDHCG_PIPE_KERNEL pipe_bb_a(PipeArgs a) {
   const RowCtx rc{sh.red};
   const PipeState& P = *a.ps;
   const BBBufs<MatT, VecT> b = bb_bufs(I, P.bsel);
-  const VecT itau = VecT(1.0 / I.st->tau);
+  const VecT itau = pipe_get<VecT>(P, kPsItau);
   double v[3];
   {
     // the new x is in b.xo (written by pipe_bb_b), the old one in b.xc
@@ -359,6 +415,7 @@ PDHCG_PIPE_KERNEL pipe_bb_a(PipeArgs a) {
   Pw.nr = v[2];
   Pw.bsel ^= 1;
   Pw.j += 1;
+  pipe_set_bb_alpha(Pw, *I.st, Pw.j, Pw.ss, Pw.sy);
   const bool go = !(sqrt(Pw.nr) <= Pw.eps || Pw.j >= I.prm.max_inner_iter);
   cudaGraphSetConditional(a.h.inner, go ? 1u : 0u);
 }
@@ -394,8 +451,7 @@ PDHCG_PIPE_KERNEL pipe_phase2(PipeArgs a) {
   pipe_ranges(I, vlo, vhi, clo, chi);
   const SolverState& Sg = *I.st;  // read here; written only by the last CTA below
   const int method = Sg.method;
-  double inv_tau, inv_sigma;
-  const StepScalars<VecT> sc = step_scalars<VecT>(Sg, I.prm, inv_tau, inv_sigma);
+  const StepScalars<VecT> sc = pipe_step_scalars<VecT>(*a.ps);
   double v[3];
   {
     const Red<3> r = phase2<kPipeBS, Ld::Stream>(I, int(blockIdx.x), method, Sg.cur, vlo, vhi, sc, rc);
@@ -424,6 +480,7 @@ PDHCG_PIPE_KERNEL pipe_phase2(PipeArgs a) {
     S.mv = sqrt(mvh2);
     S.k += 1;
     S.K += 1;
+    pipe_set_step(P, S, Pr);
   }
   *I.st = S;
   cudaGraphSetConditional(a.h.check, check ? 1u : 0u);
@@ -468,6 +525,7 @@ PDHCG_PIPE_KERNEL pipe_check(PipeArgs a) {
       S.k += 1;
     }
     S.K += 1;
+    pipe_set_step(P, S, I.prm);
   }
   *I.st = S;
   cudaGraphSetConditional(a.h.restart, restart ? 1u : 0u);
