@@ -825,6 +825,10 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   // after the group reductions that follow its reads.
   __shared__ StepScalars<CT> sm_sc;
   __shared__ double sm_scal[5];  // 1/tau, 1/sigma, then the step's three square roots
+  // The inner solvers' scalar decisions, taken by thread 0 the same way:
+  // [0] stop flag, [1] eps, [2] S.eps_in; the step lengths in the vector type.
+  __shared__ double sm_in[3];
+  __shared__ CT sm_in_ct[2];  // CG beta / BB alpha, CG alpha
 
   while (ok) {
     const int cur = S.cur;
@@ -859,31 +863,48 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     PDHCG_CLK(5);
 
     // adaptive inner tolerance (Sec. 3.3); the closed form has no inner solve
-    const double eps = method == PDHCG_INNER_DIAG ? 0.0 : inner_tolerance<VecT>(S, P, method, red1[1], inv_tau);
+    double eps = 0.0;
+    if (method != PDHCG_INNER_DIAG) {
+      if (threadIdx.x == 0) {
+        sm_in[1] = inner_tolerance<VecT>(S, P, method, red1[1], inv_tau);
+        sm_in[2] = S.eps_in;
+      }
+      __syncthreads();
+      eps = sm_in[1];
+      S.eps_in = sm_in[2];
+    }
 
     // inner solve (Sec. 2.2)
     if (method == PDHCG_INNER_CG) {
+      // rr, the stop test, alpha and beta: thread 0 (FP64), shared with the CTA
       double rr = red1[0], beta = 0.0;
       int j = 0, pc = 0;
       while (true) {
-        if (sqrt(rr) <= eps || j >= P.max_inner_iter) break;
+        if (threadIdx.x == 0) {
+          sm_in[0] = (sqrt(rr) <= eps || j >= P.max_inner_iter) ? 1.0 : 0.0;
+          sm_in_ct[0] = CT(beta);
+        }
+        __syncthreads();
+        if (sm_in[0] != 0.0) break;
+        const CT beta_c = sm_in_ct[0];
         const VecT* pold = pc ? I.p1 : I.p0;
         VecT* pnew = pc ? I.p0 : I.p1;
         if (kR && I.k > 0) {
-          r_phase_p<BS, LM>(I, prank, j == 0, CT(beta), pold, rc);
+          r_phase_p<BS, LM>(I, prank, j == 0, beta_c, pold, rc);
           if (!group_sync<BS>(g)) { ok = false; break; }
         }
-        double pq[1] = {cg_phase_a<BS, LM, kR>(I, prank, j == 0, CT(beta), pold, pnew, sc.itau, rc)};
+        double pq[1] = {cg_phase_a<BS, LM, kR>(I, prank, j == 0, beta_c, pold, pnew, sc.itau, rc)};
         PDHCG_CLK(1);
         if (!group_reduce<BS, 1, kWT>(g, pq, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
         if (!(pq[0] > 0.0)) break;
-        const double alpha = rr / pq[0];
-        double rn[1] = {cg_phase_b<BS>(I, vlo, vhi, CT(alpha), pnew)};
+        if (threadIdx.x == 0) sm_in_ct[1] = CT(rr / pq[0]);
+        __syncthreads();
+        double rn[1] = {cg_phase_b<BS>(I, vlo, vhi, sm_in_ct[1], pnew)};
         PDHCG_CLK(2);
         if (!group_reduce<BS, 1, kWT>(g, rn, 0u)) { ok = false; break; }
         PDHCG_CLK(5);
-        beta = rn[0] / rr;
+        if (threadIdx.x == 0) beta = rn[0] / rr;
         rr = rn[0];
         pc ^= 1;
         ++j;
@@ -893,8 +914,13 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       write_xbar<BS>(I, vlo, vhi, I.xT, cur ? I.xb1 : I.xb0, false);
       if (!group_sync<BS>(g)) { ok = false; break; }
     } else if (method == PDHCG_INNER_BB) {
-      // x and grad alternate between two buffers each: (xT, xprev) and (grad, gprev)
-      const double alpha_min = 1.0 / (S.gersh + inv_tau), alpha_max = 1.0 / inv_tau;
+      // x and grad alternate between two buffers each: (xT, xprev) and (grad, gprev).
+      // The stop test and the step length: thread 0 (FP64), shared with the CTA.
+      double alpha_min = 0.0, alpha_max = 0.0;
+      if (threadIdx.x == 0) {
+        alpha_min = 1.0 / (S.gersh + inv_tau);
+        alpha_max = 1.0 / inv_tau;
+      }
       double nr = red1[0], ss = 0.0, sy = 0.0;
       int j = 0;
       VecT* xc = I.xT;
@@ -902,13 +928,18 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       VecT* gc = I.grad;
       VecT* go = I.gprev;
       while (true) {
-        if (sqrt(nr) <= eps || j >= P.max_inner_iter) break;
-        double alpha = alpha_min;
-        if (j > 0) {
-          alpha = sy > 0.0 ? ss / sy : alpha_max;
-          alpha = fmin(fmax(alpha, alpha_min), alpha_max);
+        if (threadIdx.x == 0) {
+          sm_in[0] = (sqrt(nr) <= eps || j >= P.max_inner_iter) ? 1.0 : 0.0;
+          double alpha = alpha_min;
+          if (j > 0) {
+            alpha = sy > 0.0 ? ss / sy : alpha_max;
+            alpha = fmin(fmax(alpha, alpha_min), alpha_max);
+          }
+          sm_in_ct[0] = CT(alpha);
         }
-        bb_phase_b<BS>(I, vlo, vhi, CT(alpha), xc, gc, xo);
+        __syncthreads();
+        if (sm_in[0] != 0.0) break;
+        bb_phase_b<BS>(I, vlo, vhi, sm_in_ct[0], xc, gc, xo);
         { VecT* t = xo; xo = xc; xc = t; }
         PDHCG_CLK(2);
         if (!group_sync<BS>(g)) { ok = false; break; }
