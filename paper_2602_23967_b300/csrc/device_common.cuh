@@ -260,17 +260,22 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
     return false;
   }
   if (g.nblk == 1) {
-    // every warp reduces the warp partials in the same order (lane j <-> slot j)
-    double tot = 0.0;
-    if (lane < NV) {
+    // warp 0 reduces the warp partials in a fixed order (lane j <-> slot j) and
+    // shares the totals through shared memory: the FP64 adds run once, not in
+    // every warp (the FP64 pipe is narrow)
+    double* tot1 = g.sm_tot + (g.epoch & 1ull) * kSlots;
+    if (warp == 0 && lane < NV) {
       const bool mx = (maxmask >> lane) & 1u;
+      double tot = 0.0;
       for (int w = 0; w < W; ++w) {
         const double o = sw[w * kSlots + lane];
         tot = mx ? fmax(tot, o) : tot + o;
       }
+      tot1[lane] = tot;
     }
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = __shfl_sync(kFull, tot, j);
+    for (int j = 0; j < NV; ++j) v[j] = tot1[j];
     g.epoch++;
     return true;
   }
