@@ -14,6 +14,7 @@ import pytest
 import oracle
 from paper_2602_23967_b300 import pdhcg
 from paper_2602_23967_b300 import workloads as W
+from certificates import check_dual_ray, check_primal_ray
 
 pytestmark = pytest.mark.gpu
 
@@ -83,14 +84,15 @@ def test_dfloat_iterates_match_fp64_vectors(name, N):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_dfloat_infeasibility(seed):
-    x, y, r = solve(W.infeasible_qp(n=8, m=4, seed=seed), precision="dfloat", max_iter=200000)
+    qp = W.infeasible_qp(n=8, m=4, seed=seed)
+    x, y, r = solve(qp, precision="dfloat", max_iter=200000)
     assert r["status_name"] == "PRIMAL_INFEASIBLE"
+    check_primal_ray(qp, y)
     # Q d = 0 holds bit for bit in FP32 storage too (mirrored columns)
     qp = W.unbounded_qp(n=6, seed=seed)
     x, y, r = solve(qp, precision="dfloat", max_iter=200000)
     assert r["status_name"] == "DUAL_INFEASIBLE"
-    assert qp.c @ x < 0
-    assert np.max(np.abs(qp.Q @ x)) <= 1e-5
+    check_dual_ray(qp, x)
 
 
 def test_dfloat_batch_equals_single():

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from paper_2602_23967_b300 import pdhcg
 from paper_2602_23967_b300 import workloads as W
+from certificates import check_dual_ray, check_primal_ray
 
 pytestmark = pytest.mark.gpu
 
@@ -152,13 +153,9 @@ def test_primal_infeasible_detected(seed):
     qp = W.infeasible_qp(n=8, m=4, seed=seed)
     x, y, r, _ = gpu_solve(qp)
     assert r["status_name"] == "PRIMAL_INFEASIBLE"
-    g = qp.A.T @ y
-    # Farkas ray: p(-A^T y) + p(y) < 0 with A^T y in R (Sec. 5.1)
-    def p(z, lo, hi):
-        return sum(hi[i] * z[i] if z[i] > 0 else (lo[i] * z[i] if z[i] < 0 else 0.0)
-                   for i in range(len(z)))
-    val = p(-g, qp.lv, qp.uv) + p(y, qp.lc, qp.uc)
-    assert val < 0
+    # the whole Farkas certificate of Sec. 5.1: y in the rows' sign cone,
+    # A^T y in R, p(-A^T y) + p(y) < 0
+    check_primal_ray(qp, y)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -166,8 +163,8 @@ def test_dual_infeasible_detected(seed):
     qp = W.unbounded_qp(n=6, seed=seed)
     x, y, r, _ = gpu_solve(qp)
     assert r["status_name"] == "DUAL_INFEASIBLE"
-    assert qp.c @ x < 0
-    assert np.max(np.abs(qp.Q @ x)) <= 1e-5
+    # the whole certificate of Sec. 5.2: c^T d < 0, Q d = 0, d in Recc(X), A d in Recc(S)
+    check_dual_ray(qp, x)
 
 
 def test_edge_no_constraints_and_lp():

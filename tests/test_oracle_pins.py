@@ -485,3 +485,23 @@ def test_golden_gap_term():
     assert rg == pytest.approx(e["r_gap"], rel=1e-15)
     assert pobj == pytest.approx(e["primal_obj"], abs=1e-15)
     assert dobj == pytest.approx(e["dual_obj"], rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_certificate_checks_accept_oracle_rays_and_reject_flipped_ones(seed):
+    """The certificate checks the GPU tests apply (tests/certificates.py) accept
+    the oracle's rays, whose conditions the two tests above verify one by one,
+    and reject the same rays with the sign flipped."""
+    from certificates import check_dual_ray, check_primal_ray
+    qp = W.infeasible_qp(n=8, m=4, seed=seed)
+    _, y, r = oracle.solve(qp, oracle.default_params(max_iter=200000))
+    assert r["status_name"] == "PRIMAL_INFEASIBLE"
+    check_primal_ray(qp, y)
+    with pytest.raises(AssertionError):
+        check_primal_ray(qp, -y)
+    qp = W.unbounded_qp(n=6, seed=seed)
+    d, _, r = oracle.solve(qp, oracle.default_params(max_iter=200000))
+    assert r["status_name"] == "DUAL_INFEASIBLE"
+    check_dual_ray(qp, d)
+    with pytest.raises(AssertionError):
+        check_dual_ray(qp, -d)
