@@ -306,27 +306,33 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
   }
   // Every thread loads its CTAs' partials of all slots at once (one round trip
   // to L2), then a fixed-order tree: lanes, warps.  The same in every CTA.
+  // A warp with no CTA to load (warp * 32 >= nblk) hands in zeros, which is
+  // what its tree would produce, without running the FP64 tree.
   {
-    double t[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) t[j] = 0.0;
-    for (int b = threadIdx.x; b < g.nblk; b += BS) {
-      double o[NV];
-#pragma unroll
-      for (int j = 0; j < NV; ++j) o[j] = __ldcg(buf + (size_t)j * g.nblk + b);
-#pragma unroll
-      for (int j = 0; j < NV; ++j) t[j] = ((maxmask >> j) & 1u) ? fmax(t[j], o[j]) : t[j] + o[j];
-    }
     double* sw2 = g.sm_warp + ((g.epoch + 1ull) & 1ull) * (W * kSlots);  // free half until the next epoch
+    if (warp * 32 < g.nblk) {
+      double t[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      const bool mx = (maxmask >> j) & 1u;
+      for (int j = 0; j < NV; ++j) t[j] = 0.0;
+      for (int b = threadIdx.x; b < g.nblk; b += BS) {
+        double o[NV];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double o = __shfl_xor_sync(kFull, t[j], off);
-        t[j] = mx ? fmax(t[j], o) : t[j] + o;
+        for (int j = 0; j < NV; ++j) o[j] = __ldcg(buf + (size_t)j * g.nblk + b);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) t[j] = ((maxmask >> j) & 1u) ? fmax(t[j], o[j]) : t[j] + o[j];
       }
-      if (lane == 0) sw2[warp * kSlots + j] = t[j];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const bool mx = (maxmask >> j) & 1u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const double o = __shfl_xor_sync(kFull, t[j], off);
+          t[j] = mx ? fmax(t[j], o) : t[j] + o;
+        }
+        if (lane == 0) sw2[warp * kSlots + j] = t[j];
+      }
+    } else if (lane < NV) {
+      sw2[warp * kSlots + lane] = 0.0;
     }
     __syncthreads();
     if (warp == 0 && lane < NV) {
