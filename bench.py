@@ -217,8 +217,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 1_800_744_448 + 1_253_647_872, "instances": 512,
-                   "sources_sha256": "8a05ca147c95f6e7e06dec815eea41879950f274e6d9b5765859bb7ed393e1cc",
+TRAFFIC_CAPTURE = {"bytes": 1_158_003_968 + 911_395_584, "instances": 512,
+                   "sources_sha256": "153135a5d400de5e666c93a924e14c4d8124919025254a88424ed31b52db3bac",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
