@@ -355,6 +355,11 @@ __device__ __forceinline__ bool group_reduce(Group<BS>& g, double (&v)[NV], unsi
 // Plain group barrier (no values).
 template <int BS>
 __device__ __forceinline__ bool group_sync(Group<BS>& g) {
+  if (g.nblk == 1) {  // one CTA: a block barrier (the epoch still advances)
+    __syncthreads();
+    g.epoch++;
+    return true;
+  }
   double v[1] = {0.0};
   return group_reduce<BS, 1>(g, v, 0u);
 }

@@ -859,7 +859,15 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       for (int q = 0; q < 4; ++q) red1[q] = r.v[q];
     }
     PDHCG_CLK(0);
-    if (!group_reduce<BS, 4, kWT>(g, red1, 0u)) { ok = false; break; }
+    if (method == PDHCG_INNER_DIAG) {
+      // The closed form uses Phase I's sums (the movement norms, slots 2 and 3)
+      // only after Phase II: they ride in Phase II's reduction, and Phase I
+      // ends with a plain barrier (xbar must be complete).  Same sums, same order.
+      if (!group_sync<BS>(g)) { ok = false; break; }
+    } else if (!group_reduce<BS, 4, kWT>(g, red1, 0u)) {
+      ok = false;
+      break;
+    }
     PDHCG_CLK(5);
 
     // adaptive inner tolerance (Sec. 3.3); the closed form has no inner solve
@@ -973,7 +981,8 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
 
     // Phase II.  Slot 3 carries a group's pause decision for time slices: rank
     // 0's clock decides, and the max-reduction hands every CTA the same value.
-    double red2[4];
+    // (closed form: slots 4 and 5 carry Phase I's unreduced movement sums)
+    double red2[6];
     {
       const Red<3> r = phase2<BS, LM>(I, prank, method, cur, vlo, vhi, sc, rc);
       red2[0] = r.v[0];
@@ -983,13 +992,15 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
                  globaltimer_ns() - t_resume >= plan.slice_ns)
                     ? 1.0
                     : 0.0;
+      red2[4] = method == PDHCG_INNER_DIAG ? red1[2] : 0.0;
+      red2[5] = method == PDHCG_INNER_DIAG ? red1[3] : 0.0;
     }
     PDHCG_CLK(3);
-    if (!group_reduce<BS, 4, kWT>(g, red2, 1u << 3)) { ok = false; break; }
+    if (!group_reduce<BS, 6, kWT>(g, red2, 1u << 3)) { ok = false; break; }
     PDHCG_CLK(5);
     const double dy2 = red2[0];
-    const double dx2 = method == PDHCG_INNER_DIAG ? red1[2] : red2[1];
-    const double mvh2 = method == PDHCG_INNER_DIAG ? red1[3] : red2[2];
+    const double dx2 = method == PDHCG_INNER_DIAG ? red2[4] : red2[1];
+    const double mvh2 = method == PDHCG_INNER_DIAG ? red2[5] : red2[2];
     // the step's square roots one lane each, so a warp issues one FP64 sequence
     // for all three: the fixed-point residual (Sec. 3.2) and the primal movement
     // for either outcome of the restart decision
