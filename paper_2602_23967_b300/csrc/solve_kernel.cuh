@@ -181,17 +181,17 @@ struct StepScalars {
 };
 
 // The step's scalars 1/tau, 1/sigma, sigma, (k+1)/(k+2), 1/(k+2), theta,
-// 1 + theta: lane q computes scalar q as one quotient and converts it to the
+// 1 + theta (k: the Halpern index of the step): lane q computes scalar q as one quotient and converts it to the
 // vector type, so the warp issues one FP64 division and one conversion for all
 // seven (the FP64 pipe is narrow); the values are the same as computing each on
 // its own.  Every lane then takes them by shuffle.  Called by whole warps.
 template <class CT>
-__device__ __forceinline__ StepScalars<CT> step_scalars(const SolverState& S, const DevParams& P, double& inv_tau,
-                                                       double& inv_sigma) {
+__device__ __forceinline__ StepScalars<CT> step_scalars(const SolverState& S, const DevParams& P, int64_t k,
+                                                       double& inv_tau, double& inv_sigma) {
   StepScalars<CT> sc;
   const int ln = threadIdx.x & 31;
-  const double kp2 = double(S.k + 2);
-  const double num = ln == 2 ? S.sigma : ln == 3 ? double(S.k + 1) : ln == 5 ? P.theta : ln == 6 ? 1.0 + P.theta : 1.0;
+  const double kp2 = double(k + 2);
+  const double num = ln == 2 ? S.sigma : ln == 3 ? double(k + 1) : ln == 5 ? P.theta : ln == 6 ? 1.0 + P.theta : 1.0;
   const double den = ln == 0 ? S.tau : ln == 1 ? S.sigma : (ln == 3 || ln == 4) ? kp2 : 1.0;
   const double q = num / den;
   const CT qc = CT(q);
@@ -825,6 +825,12 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
   // after the group reductions that follow its reads.
   __shared__ StepScalars<CT> sm_sc;
   __shared__ double sm_scal[5];  // 1/tau, 1/sigma, then the step's three square roots
+  // The next step's scalars, computed ahead by the last warp after its share of
+  // Phase II (it takes the fewest slices), valid when no check ends the step
+  // (only a check can restart, which changes k, tau and sigma otherwise).
+  __shared__ StepScalars<CT> sm_sc_next;
+  __shared__ double sm_scal_next[2];
+  bool next_ready = false;
   // The inner solvers' scalar decisions, taken by thread 0 the same way:
   // [0] stop flag, [1] eps, [2] S.eps_in; the step lengths in the vector type.
   __shared__ double sm_in[3];
@@ -834,18 +840,24 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
     const int cur = S.cur;
     double inv_tau, inv_sigma;
     StepScalars<CT> sc;
-    if (threadIdx.x < 32) {
-      sc = step_scalars<CT>(S, P, inv_tau, inv_sigma);
-      if (threadIdx.x == 0) {
-        sm_sc = sc;
-        sm_scal[0] = inv_tau;
-        sm_scal[1] = inv_sigma;
+    if (next_ready) {  // published before the barriers that ended the last step
+      sc = sm_sc_next;
+      inv_tau = sm_scal_next[0];
+      inv_sigma = sm_scal_next[1];
+    } else {
+      if (threadIdx.x < 32) {
+        sc = step_scalars<CT>(S, P, S.k, inv_tau, inv_sigma);
+        if (threadIdx.x == 0) {
+          sm_sc = sc;
+          sm_scal[0] = inv_tau;
+          sm_scal[1] = inv_sigma;
+        }
       }
+      __syncthreads();
+      sc = sm_sc;
+      inv_tau = sm_scal[0];
+      inv_sigma = sm_scal[1];
     }
-    __syncthreads();
-    sc = sm_sc;
-    inv_tau = sm_scal[0];
-    inv_sigma = sm_scal[1];
 
     // Phase I (structured Q: R x first)
     if (kR && I.k > 0 && method != PDHCG_INNER_DIAG) {
@@ -995,34 +1007,50 @@ __device__ PDHCG_PHASE_ATTR void solve_instance(Group<BS>& g, const Inst<MatT, V
       red2[4] = method == PDHCG_INNER_DIAG ? red1[2] : 0.0;
       red2[5] = method == PDHCG_INNER_DIAG ? red1[3] : 0.0;
     }
+    // the next step's scalars for k + 1 (used if this step ends without a
+    // check); the reduction below orders these writes before their reads
+    if (threadIdx.x >= BS - 32) {
+      double it, is;
+      const StepScalars<CT> nx = step_scalars<CT>(S, P, S.k + 1, it, is);
+      if (threadIdx.x == BS - 32) {
+        sm_sc_next = nx;
+        sm_scal_next[0] = it;
+        sm_scal_next[1] = is;
+      }
+    }
     PDHCG_CLK(3);
     if (!group_reduce<BS, 6, kWT>(g, red2, 1u << 3)) { ok = false; break; }
     PDHCG_CLK(5);
     const double dy2 = red2[0];
     const double dx2 = method == PDHCG_INNER_DIAG ? red2[4] : red2[1];
     const double mvh2 = method == PDHCG_INNER_DIAG ? red2[5] : red2[2];
-    // the step's square roots one lane each, so a warp issues one FP64 sequence
-    // for all three: the fixed-point residual (Sec. 3.2) and the primal movement
-    // for either outcome of the restart decision
-    double fpr, sq_dx, sq_mvh;
-    if (threadIdx.x < 32) {  // warp 0, lane q: root q
-      const int ln = threadIdx.x;
-      const double sq = sqrt(ln == 0 ? S.omega * dx2 + dy2 / S.omega : ln == 1 ? dx2 : mvh2);
-      if (ln < 3) sm_scal[2 + ln] = sq;
-    }
-    __syncthreads();
-    fpr = sm_scal[2];
-    sq_dx = sm_scal[3];
-    sq_mvh = sm_scal[4];
-    if (S.k == 0) {
-      S.fpr_anchor = fpr;
-      S.fpr_last = fpr;
-    }
-
     bool do_restart = false;
     const bool period_end = S.K + 1 == next_check;
     if (period_end) next_check += P.k_eval;
     const bool check = period_end || (S.K + 1 >= P.max_iter);
+    next_ready = !check;
+
+    // the step's square roots one lane each, so a warp issues one FP64 sequence
+    // for all three: the fixed-point residual (Sec. 3.2) and the primal movement
+    // for either outcome of the restart decision.  The closed form needs them
+    // only where the restart logic reads them (the first step of a round, a
+    // check): the movement feeds the inner tolerance, which it does not have.
+    double fpr = 0.0, sq_dx = 0.0, sq_mvh = 0.0;
+    if (method != PDHCG_INNER_DIAG || S.k == 0 || check) {
+      if (threadIdx.x < 32) {  // warp 0, lane q: root q
+        const int ln = threadIdx.x;
+        const double sq = sqrt(ln == 0 ? S.omega * dx2 + dy2 / S.omega : ln == 1 ? dx2 : mvh2);
+        if (ln < 3) sm_scal[2 + ln] = sq;
+      }
+      __syncthreads();
+      fpr = sm_scal[2];
+      sq_dx = sm_scal[3];
+      sq_mvh = sm_scal[4];
+    }
+    if (S.k == 0) {
+      S.fpr_anchor = fpr;
+      S.fpr_last = fpr;
+    }
     if (check) {
       double cv[18];
       if (kR && I.k > 0) {
