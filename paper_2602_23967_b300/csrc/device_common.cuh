@@ -457,7 +457,9 @@ template <Ld LM, class Acc, class X>
 __device__ __forceinline__ void slice_dot(const X& x, int s, int lane, Acc* sums) {
   if constexpr (X::NG > 0) {
     if (!x.on) return;
-    const int64_t b = ldm64<LM>(x.S.ptr + s), e = ldm64<LM>(x.S.ptr + s + 1);
+    // pool CTAs may hold the slice offsets in shared memory: a generic load
+    constexpr Ld LP = LM == Ld::Cached ? Ld::Generic : LM;
+    const int64_t b = ldm64<LP>(x.S.ptr + s), e = ldm64<LP>(x.S.ptr + s + 1);
     const int W = int((e - b) >> 5);
     const int* cp = x.S.col + b + lane;
     const auto* vp = x.S.val + b + lane;

@@ -141,11 +141,15 @@ struct Inst {
 };
 
 // Shared-memory bytes the vectors of an (n, m) instance take when a pool CTA
-// keeps them on chip: 9 n-vectors (+4 for CG / BB), 6 m-vectors, bound codes.
+// keeps them on chip: 9 n-vectors (+4 for CG / BB), 6 m-vectors, bound codes,
+// and the SELL slice offsets of the row spaces (at most n/32 + 1 slices each;
+// A^T's and A's, and Q's with an inner solver).
 inline __host__ __device__ size_t smem_vector_bytes(int n, int m, int method, size_t vec_bytes) {
-  const size_t nv = 9 + ((method == 2 || method == 3) ? 4 : 0);
+  const bool inner = method == 2 || method == 3;
+  const size_t nv = 9 + (inner ? 4 : 0);
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return nv * al(size_t(n) * vec_bytes) + 6 * al(size_t(m) * vec_bytes) + al(size_t(n)) + al(size_t(m));
+  const size_t ptrs = (inner ? 2 : 1) * al((size_t(n) / 32 + 2) * 8) + al((size_t(m) / 32 + 2) * 8);
+  return nv * al(size_t(n) * vec_bytes) + 6 * al(size_t(m) * vec_bytes) + al(size_t(n)) + al(size_t(m)) + ptrs;
 }
 
 // How one launch of the solve kernel maps CTAs to instances.

@@ -1156,6 +1156,14 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
     return q;
   };
   const bool inner = method == PDHCG_INNER_CG || method == PDHCG_INNER_BB;
+  // First the SELL slice offsets of the row spaces: each slice's walk starts
+  // with two of them, at the head of its chain of dependent loads.
+  auto place_ptr = [&](const int64_t* p, int nslices) -> const int64_t* {
+    return p ? place(p, nslices + 1) : p;
+  };
+  const int64_t* pAT = place_ptr(Ig.ATs.ptr, Ig.vsp.nslices);
+  const int64_t* pQ = inner && Ig.has_q ? place_ptr(Ig.Qs.ptr, Ig.vsp.nslices) : Ig.Qs.ptr;
+  const int64_t* pA = place_ptr(Ig.As.ptr, Ig.csp.nslices);
   VecT *e0 = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr;
   VecT *xT = Ig.xT, *yT = Ig.yT;
   VecT* yb0 = place(Ig.yb0, m);
@@ -1196,6 +1204,13 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
   const VecT* ycg = cur ? Ig.yb1 : Ig.yb0;
   // copies into the shared-memory slots only (a vector left in global memory
   // is already in place)
+  auto copy_ptr = [&](const int64_t* dst, const int64_t* src, int nslices) {
+    if (dst != src)
+      for (int i = threadIdx.x; i <= nslices; i += BS) const_cast<int64_t*>(dst)[i] = src[i];
+  };
+  copy_ptr(pAT, Ig.ATs.ptr, Ig.vsp.nslices);
+  copy_ptr(pQ, Ig.Qs.ptr, Ig.vsp.nslices);
+  copy_ptr(pA, Ig.As.ptr, Ig.csp.nslices);
   for (int i = threadIdx.x; i < n; i += BS) {
     if (c != Ig.c) c[i] = Ig.c[i];
     if (lv != Ig.lv) lv[i] = Ig.lv[i];
@@ -1221,6 +1236,7 @@ __device__ PDHCG_PHASE_ATTR void solve_in_smem(Group<BS>& g, const Inst<MatT, Ve
     I.xb0 = xb0; I.xb1 = xb1; I.xT = xT; I.xa = xa; I.xbar = xbar;
     I.c = c; I.lv = lv; I.uv = uv; I.qdiag = qd; I.vtype = vt;
     I.yb0 = yb0; I.yb1 = yb1; I.yT = yT; I.ya = ya; I.lc = lc; I.uc = uc; I.ctype = ct;
+    I.ATs.ptr = pAT; I.Qs.ptr = pQ; I.As.ptr = pA;
     if (method == PDHCG_INNER_CG) {
       I.r = e0; I.p0 = e1; I.p1 = e2; I.q = e3;
     } else if (method == PDHCG_INNER_BB) {
