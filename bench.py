@@ -217,8 +217,8 @@ def cpu_oracle_sample(qps, sample, time_budget_s=25.0):
 # DRAM traffic of the batched solve kernel from one ncu capture on 512 instances
 # (dram__bytes_read.sum + dram__bytes_write.sum), per instance; valid only for the
 # kernel sources it was taken on (hash below), else the roofline reports null.
-TRAFFIC_CAPTURE = {"bytes": 1_158_003_968 + 911_395_584, "instances": 512,
-                   "sources_sha256": "153135a5d400de5e666c93a924e14c4d8124919025254a88424ed31b52db3bac",
+TRAFFIC_CAPTURE = {"bytes": 1_848_600_320 + 1_397_771_520, "instances": 512,
+                   "sources_sha256": "15bbaee1c95199a85b19b9658ebd977f69aeef56e7b08a80db8e95cca51dbcaf",
                    "summary": "profiles/solve_kernel_mpc_batch512_dram.md"}
 KERNEL_SOURCES = ("solve_kernel.cuh", "device_common.cuh", "dfloat.cuh", "launch.h", "kernels_impl.cuh",
                   "pdhcg_internal.h", "kernels_dfloat.cu")
