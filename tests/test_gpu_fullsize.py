@@ -9,7 +9,9 @@ configurations the benchmark uses.
   iterates after 3 PDHG steps (BB inner solver, auto multi-CTA group) equal the
   oracle's to 1e-10 relative, with the same number of inner steps; after 64
   steps the double-float and mixed modes (the same FP32 matrix values) agree
-  to 1e-8.
+  to 1e-8; in the benchmark's configuration (double-float, pipeline form, 64
+  steps) the device's residuals equal the oracle's evaluation of its point,
+  and the trajectory follows the oracle's.
 * The factor-model portfolio QP (n = 1e5 + 1e3 variables, the 1e5-entry budget
   row): FP64 iterates after 20 steps equal the oracle's to 1e-10, and the
   double-float solve at 1e-6 matches the oracle's objective to 1e-6.
@@ -88,6 +90,29 @@ def test_large_sparse_double_float_matches_mixed_full_size(large_sparse):
     assert rd["inner_iterations"] == rm["inner_iterations"]
     assert np.max(np.abs(xd - xm)) <= 1e-8 * (1 + np.max(np.abs(xm)))
     assert np.max(np.abs(yd - ym)) <= 1e-8 * (1 + np.max(np.abs(ym)))
+
+
+def test_large_sparse_bench_configuration_full_size(large_sparse):
+    # The large-instance leg of bench.py: double-float, the automatic form (the
+    # pipeline graph at this size), 64 PDHG steps ending at a check.
+    # (a) The residuals and objective the device reports (FP64-accurate checks,
+    #     Sec. 4.2) equal the oracle's independent FP64 evaluation of the
+    #     returned point.
+    # (b) The trajectory is the oracle's: after the same 64 steps (same step
+    #     size), objective and residuals agree to 1e-4 (FP32 matrix values,
+    #     double-float vectors against FP64 throughout).
+    qp = large_sparse
+    N = 64
+    x, y, r, eta = solve_n(qp, N, precision="dfloat", eps_tol=1e-12)
+    assert r["status_name"] == "ITERATION_LIMIT" and r["iterations"] == N, r
+    assert r["form"] == 2, r["form"]  # the pipeline graph
+    rp, rd, rg, pobj, _ = kkt_of(qp, x, y)
+    for dev, host in ((r["r_primal"], rp), (r["r_dual"], rd), (r["r_gap"], rg), (r["primal_obj"], pobj)):
+        assert abs(dev - host) <= 1e-9 * (1 + abs(host)), (dev, host)
+    _, _, ro = oracle.solve(qp, oracle.default_params(max_iter=N, eta_override=eta))
+    assert ro["iterations"] == N
+    for key in ("r_primal", "r_dual", "r_gap", "primal_obj"):
+        assert abs(r[key] - ro[key]) <= 1e-4 * (1 + abs(ro[key])), (key, r[key], ro[key])
 
 
 def test_factor_portfolio_full_size():
