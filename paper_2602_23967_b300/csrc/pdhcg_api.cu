@@ -585,8 +585,14 @@ int choose_group_blocks(const pdhcg_problem* P, int maxblk) {
 // entries one PDHG step touches, inner products counted once) run on one pool
 // CTA each; larger ones on a multi-CTA group of about one CTA per
 // kWorkPerGroupCta, at most kMaxBatchGroup.
-constexpr int64_t kWorkPerGroupCta = 65536;
-constexpr int kMaxBatchGroup = 32;
+#ifndef PDHCG_WORK_PER_GROUP_CTA
+#define PDHCG_WORK_PER_GROUP_CTA 65536
+#endif
+constexpr int64_t kWorkPerGroupCta = PDHCG_WORK_PER_GROUP_CTA;
+#ifndef PDHCG_MAX_BATCH_GROUP
+#define PDHCG_MAX_BATCH_GROUP 32
+#endif
+constexpr int kMaxBatchGroup = PDHCG_MAX_BATCH_GROUP;
 
 int batch_group_blocks(const pdhcg_problem* P) {
   const int64_t work = (P->method != PDHCG_INNER_DIAG ? P->nnzQ + P->nnzR : 0) + 2 * P->nnzA + P->n + P->m;
