@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=120, help="arrivals per serving trace")
     ap.add_argument("--serve-plain", type=int, default=16, help="requests the plain solver times per trace")
     ap.add_argument("--serve-slots", type=int, default=2 * 148, help="concurrent solves of the serving loop")
+    ap.add_argument("--serve-mpc-rate", type=float, default=3000.0,
+                    help="arrival rate of a 4 s trace of MPC requests only, run with the serving traces "
+                         "(0: skip; an empty --serve-rates skips all serving)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the row layout and launch shape with pdhcg_autotune (batch: on a 512-instance "
                          "sample; large sparse QP: on the instance) before timing")
@@ -486,11 +489,20 @@ def serving_leg(args, stream):
                 if row["solves_per_s"]:
                     row["served_vs_plain"] = row["solves_per_s"] / plain
             rows.append(row)
+    mpc_only = None
+    if args.serve_mpc_rate > 0:
+        # the serving loop's capacity on small requests: a 4 s trace of MPC QPs only
+        trace = W.serving_trace(rate_per_s=args.serve_mpc_rate, duration_s=4.0, seed=7, mix=(1.0, 0.0, 0.0))
+        qps = [W.build_request(k, sd, n) for _, k, sd, n in trace]
+        prm = pdhcg.default_params(precision=args.precision, eps_tol=EPS, time_limit_s=60.0)
+        mpc_only = {"arrival_rate_per_s": args.serve_mpc_rate, "eps": EPS, "duration_s": 4.0}
+        mpc_only.update(serve_trace(prm, stream, trace, qps, args.serve_slots))
+        mpc_only.pop("by_kind", None)
     return {"mix": "70 % MPC (T~U{10..50}), 25 % random QPs n~U{1e3..1e5} (~10 nnz/row, 2 % primal "
                    "infeasible), 5 % factor-model QPs n=1e5", "hbm_budget_gb": 100, "max_slots": args.serve_slots,
             "slice": "10 ms of device time per slice; MPC-sized requests on pool CTAs, larger ones on "
                      "multi-CTA groups in a cooperative launch of their own",
-            "traces": rows}
+            "traces": rows, "mpc_only": mpc_only}
 
 
 def whole_solve_leg(args, stream):
