@@ -230,3 +230,18 @@ def test_autotune_selection_rule(shim):
     assert pick([-1.0, 2.0, 1.5]) == 2              # the defaults failed: the fastest that ran
     assert pick([-1.0, float("inf")]) == -1         # nothing ran
     assert pick([0.7]) == 0
+
+
+@pytest.mark.parametrize("nrows", [1, 31, 32, 33, 1000, 4097])
+def test_slice_count_within_the_shared_memory_bound(shim, nrows):
+    """A pool CTA keeps each row space's nslices + 1 slice offsets in shared
+    memory, budgeted as n/32 + 2 entries (smem_vector_bytes): the packing never
+    makes more slices than that, whatever the layout or the share of long rows."""
+    rng = np.random.default_rng(nrows)
+    lengths = rng.integers(0, 12, size=nrows)
+    lengths[rng.random(nrows) < 0.05] = 100  # some long rows (warp-per-row, not in slices)
+    M = random_rows(rng, nrows, 200, lengths)
+    for layout in (None, (1, 64, 2048), (8192, 16, 64)):
+        lay = pack(shim, [M], layout)
+        assert lay["nslices"] + 1 <= nrows // 32 + 2, (layout, lay["nslices"])
+        assert len(lay["ptr"][0]) == lay["nslices"] + 1
