@@ -15,6 +15,7 @@ import pytest
 import oracle
 from paper_2602_23967_b300 import pdhcg
 from paper_2602_23967_b300 import workloads as W
+from certificates import check_dual_ray, check_primal_ray
 
 pytestmark = pytest.mark.gpu
 
@@ -73,10 +74,11 @@ def test_pipeline_infeasibility(seed):
     x, y, r, _ = solve(qp)
     assert r["status_name"] == "PRIMAL_INFEASIBLE"
     assert np.max(np.abs(y)) == pytest.approx(1.0)
+    check_primal_ray(qp, y)   # the whole certificate of Sec. 5.1
     qp = W.unbounded_qp(n=6, seed=seed)
     x, y, r, _ = solve(qp)
     assert r["status_name"] == "DUAL_INFEASIBLE"
-    assert qp.c @ x < 0 and np.max(np.abs(qp.Q @ x)) <= 1e-5
+    check_dual_ray(qp, x)     # the whole certificate of Sec. 5.2
 
 
 def test_pipeline_limits_and_warm_start():
